@@ -1,0 +1,628 @@
+// amg_oracle.cpp -- plain, slow, FP64 CPU oracle of the matching-based AMG
+// preconditioned CG of D'Ambra, Durastante and Filippone, "AMG preconditioners
+// for linear solvers towards extreme scale" (Sections 3.1-3.3, 5).
+//
+// TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU
+// baseline leg of the benchmark may build, load or call this file. The CUDA
+// library never links, includes or calls it, and it shares no code with it.
+//
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -shared -fPIC (no FMA contraction:
+// every multiply and add below is rounded on its own, in the order written).
+//
+// Functions and what pins them (tests under tests/test_oracle_*.py):
+//   edge weights (Eq. 3)            -- closed form 7/6 on the Laplacian, hand
+//                                      example fixture, range (0,2) for SPD
+//   greedy matching on the strict   -- equals the independent locally-dominant
+//   edge order (Section 3.2)           rounds; valid, maximal, >= 1/2 of the
+//                                      brute-force optimum on tiny graphs
+//   aggregates + prolongator (Eq. 4) -- partition, orthonormal columns, P w_c = w
+//   pairwise Galerkin product        -- dense P^T A P (numpy) on small inputs
+//   level loop + stop rule           -- paper's hierarchy table: 80^3 -> 5 levels,
+//                                      ratio 8.00, coarsest 125; opc 1.141
+//   l1-Jacobi (Eq. 5-6, nb = 1)      -- two-level constant K = 5.6220 (Table 1)
+//   V-cycle (Eq. 2)                  -- dense error-propagation product; SPD
+//   PCG                              -- dense Cholesky solve of A
+// Nothing here is "parity unpinned".
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- CSR ------
+struct Csr {
+    int n = 0;
+    std::vector<int32_t> ptr;   // n + 1
+    std::vector<int32_t> col;   // nnz, ascending in each row
+    std::vector<double> val;    // nnz
+    int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+// Position of entry (i, j) in row i, or -1 when it is not stored.
+int64_t find_entry(const Csr& A, int i, int j) {
+    int64_t lo = A.ptr[i], hi = A.ptr[i + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (A.col[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    return (lo < A.ptr[i + 1] && A.col[lo] == j) ? lo : -1;
+}
+
+double diag_of(const Csr& A, int i) {
+    int64_t k = find_entry(A, i, i);
+    return k < 0 ? 0.0 : A.val[k];
+}
+
+// Input checks: square CSR with sorted unique columns, finite values, a
+// positive stored diagonal (A s.p.d., Section 3.1) and a symmetric pattern.
+// Returns 0 when valid, a negative code otherwise (-1 shape, -2 not SPD).
+int validate(const Csr& A) {
+    if (A.n < 0 || (int)A.ptr.size() != A.n + 1 || A.ptr[0] != 0) return -1;
+    for (int i = 0; i < A.n; ++i) {
+        if (A.ptr[i + 1] < A.ptr[i]) return -1;
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            if (A.col[k] < 0 || A.col[k] >= A.n) return -1;
+            if (k > A.ptr[i] && A.col[k] <= A.col[k - 1]) return -1;
+            if (!std::isfinite(A.val[k])) return -2;
+            if (find_entry(A, A.col[k], i) < 0) return -1;
+        }
+        if (!(diag_of(A, i) > 0.0)) return -2;
+    }
+    return 0;
+}
+
+// ------------------------------------------------------- Eq. 3 weights -----
+// c_ij = 1 - 2 a_ij w_i w_j / (a_ii w_i^2 + a_jj w_j^2), evaluated for the
+// unordered pair {lo, hi} from the upper entry a_{lo,hi}, operation by
+// operation in this order.
+double edge_weight(double a_lohi, double a_lolo, double a_hihi, double w_lo, double w_hi) {
+    double den = (a_lolo * w_lo) * w_lo + (a_hihi * w_hi) * w_hi;
+    double num = ((2.0 * a_lohi) * w_lo) * w_hi;
+    return 1.0 - num / den;
+}
+
+struct Edge {
+    double c;
+    int lo, hi;
+};
+
+// Strict total order on edges: larger weight first, then smaller lower end,
+// then smaller upper end (the index tiebreak).
+bool edge_before(const Edge& a, const Edge& b) {
+    if (a.c != b.c) return a.c > b.c;
+    if (a.lo != b.lo) return a.lo < b.lo;
+    return a.hi < b.hi;
+}
+
+// Edge set of G (Section 3.2): unordered pairs {i, j}, i != j, whose upper
+// entry a_{lo,hi} is a stored nonzero.
+std::vector<Edge> edge_list(const Csr& A, const std::vector<double>& w) {
+    std::vector<Edge> E;
+    for (int i = 0; i < A.n; ++i) {
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            int j = A.col[k];
+            if (j <= i || A.val[k] == 0.0) continue;
+            E.push_back({edge_weight(A.val[k], diag_of(A, i), diag_of(A, j), w[i], w[j]), i, j});
+        }
+    }
+    return E;
+}
+
+// ------------------------------------------------ matching (Section 3.2) ---
+// Greedy matching on the strict edge order: scan the edges from best to worst
+// and keep an edge when both ends are still free. mate[v] = partner or -1.
+std::vector<int32_t> match_greedy(const Csr& A, const std::vector<double>& w) {
+    std::vector<Edge> E = edge_list(A, w);
+    std::sort(E.begin(), E.end(), edge_before);
+    std::vector<int32_t> mate(A.n, -1);
+    for (const Edge& e : E) {
+        if (mate[e.lo] < 0 && mate[e.hi] < 0) {
+            mate[e.lo] = e.hi;
+            mate[e.hi] = e.lo;
+        }
+    }
+    return mate;
+}
+
+// Locally-dominant matching by rounds (the half-approximate algorithm the
+// paper uses through MatchBox-P): in each round every free vertex points at
+// its best free neighbour; mutual pointers are locally dominant edges and are
+// matched. Stops when no free vertex has a free neighbour. Written without
+// reference to match_greedy so that the two can check each other.
+std::vector<int32_t> match_ld_rounds(const Csr& A, const std::vector<double>& w, int* rounds_out) {
+    const int n = A.n;
+    std::vector<Edge> E = edge_list(A, w);
+    std::vector<std::vector<int>> inc(n);    // incident edge ids
+    for (int e = 0; e < (int)E.size(); ++e) {
+        inc[E[e].lo].push_back(e);
+        inc[E[e].hi].push_back(e);
+    }
+    std::vector<int32_t> mate(n, -1);
+    std::vector<char> alive(n, 1);           // free and still has a free neighbour
+    std::vector<int> cand(n, -1);
+    int rounds = 0;
+    for (;;) {
+        bool any = false;
+        for (int v = 0; v < n; ++v) {
+            cand[v] = -1;
+            if (!alive[v]) continue;
+            int best = -1;
+            for (int e : inc[v]) {
+                int u = E[e].lo == v ? E[e].hi : E[e].lo;
+                if (mate[u] >= 0 || !alive[u]) continue;
+                if (best < 0 || edge_before(E[e], E[best])) best = e;
+            }
+            if (best < 0) { alive[v] = 0; continue; }
+            cand[v] = E[best].lo == v ? E[best].hi : E[best].lo;
+            any = true;
+        }
+        if (!any) break;
+        ++rounds;
+        for (int v = 0; v < n; ++v) {
+            int u = cand[v];
+            if (u > v && cand[u] == v) {
+                mate[v] = u; mate[u] = v;
+                alive[v] = alive[u] = 0;
+            }
+        }
+    }
+    if (rounds_out) *rounds_out = rounds;
+    return mate;
+}
+
+// ---------------------------------- aggregates and prolongator (Eq. 4) -----
+struct Pairwise {
+    int nc = 0;
+    std::vector<int32_t> mate;   // matching that produced it
+    std::vector<int32_t> agg;    // fine index -> aggregate
+    std::vector<double> p;       // the single nonzero of row i of P
+    std::vector<double> wc;      // w restricted to the coarse space
+    int rounds = 0;
+};
+
+// Aggregates are the matched pairs and the unmatched singletons, numbered in
+// increasing order of their smallest member. For a pair the column of P is
+// the orthonormal projection of w on the pair, w_e = (w_i, w_j)/|(w_i, w_j)|,
+// and the coarse smooth vector entry is |(w_i, w_j)|; a singleton column is
+// w_s/|w_s| and its coarse entry |w_s|.
+Pairwise aggregate(const std::vector<int32_t>& mate, const std::vector<double>& w) {
+    const int n = (int)mate.size();
+    Pairwise R;
+    R.mate = mate;
+    R.agg.assign(n, -1);
+    R.p.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        int j = mate[i];
+        if (j >= 0 && j < i) continue;        // numbered with its smaller member
+        int q = R.nc++;
+        if (j < 0) {
+            R.agg[i] = q;
+            R.p[i] = w[i] > 0.0 ? 1.0 : -1.0;
+            R.wc.push_back(std::fabs(w[i]));
+        } else {
+            double s = std::sqrt(w[i] * w[i] + w[j] * w[j]);
+            R.agg[i] = q; R.agg[j] = q;
+            R.p[i] = w[i] / s;
+            R.p[j] = w[j] / s;
+            R.wc.push_back(s);
+        }
+    }
+    return R;
+}
+
+// ------------------------------------ Galerkin product (Section 3.1) -------
+// A_c = P^T A P for a P with one nonzero per row. Coarse row q is built from
+// its members in ascending order, each member's entries in ascending column
+// order; the term (p_i a_ij) p_j is added to the running sum of coarse column
+// agg(j) from left to right, the first term starting the sum. Columns of the
+// coarse row are emitted in ascending order.
+Csr galerkin_onenz(const Csr& A, const std::vector<int32_t>& agg, const std::vector<double>& p, int nc) {
+    std::vector<std::vector<int>> members(nc);
+    for (int i = 0; i < A.n; ++i) members[agg[i]].push_back(i);   // ascending i
+    Csr C;
+    C.n = nc;
+    C.ptr.assign(nc + 1, 0);
+    std::vector<double> acc(nc, 0.0);
+    std::vector<char> seen(nc, 0);
+    std::vector<int> touched;
+    for (int q = 0; q < nc; ++q) {
+        touched.clear();
+        for (int i : members[q]) {
+            for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                int j = A.col[k];
+                int Q = agg[j];
+                double t = (p[i] * A.val[k]) * p[j];
+                if (!seen[Q]) { seen[Q] = 1; acc[Q] = t; touched.push_back(Q); }
+                else acc[Q] = acc[Q] + t;
+            }
+        }
+        std::sort(touched.begin(), touched.end());
+        for (int Q : touched) {
+            C.col.push_back(Q);
+            C.val.push_back(acc[Q]);
+            seen[Q] = 0;
+        }
+        C.ptr[q + 1] = (int32_t)C.col.size();
+    }
+    return C;
+}
+
+// ------------------------------------------------------------ hierarchy -----
+struct Level {
+    Csr A;
+    std::vector<double> w;        // smooth vector on this level
+    std::vector<double> minv;     // l1-Jacobi inverse diagonal
+    // prolongator to the next level (absent on the coarsest): P = product of
+    // the pairwise prolongators of the sweeps, still one nonzero per row
+    std::vector<int32_t> agg;
+    std::vector<double> p;
+    std::vector<Pairwise> sweeps;
+    std::vector<int64_t> sweep_nnz;   // nnz of the coarse matrix after each sweep
+};
+
+struct Hierarchy {
+    std::vector<Level> lev;
+    int nc = 0;                    // coarsest size
+    std::vector<double> L;         // dense Cholesky factor, column-major nc x nc
+    int pre = 1, post = 1;
+    double omega = 1.0;
+    int use_ld = 0;
+};
+
+// l1-Jacobi (Eq. 5-6 with blocks of size one): M_ii = a_ii + sum_{j != i} |a_ij|.
+std::vector<double> l1_jacobi_inverse(const Csr& A) {
+    std::vector<double> m(A.n);
+    for (int i = 0; i < A.n; ++i) {
+        double s = 0.0, d = 0.0;
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            if (A.col[k] == i) d = A.val[k];
+            else s = s + std::fabs(A.val[k]);
+        }
+        m[i] = 1.0 / (d + s);
+    }
+    return m;
+}
+
+// Textbook dense Cholesky A = L L^T of the lower triangle, column-major.
+// Returns false if a pivot is not positive.
+bool dense_cholesky(const Csr& A, std::vector<double>& L) {
+    const int n = A.n;
+    std::vector<double> D((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (A.col[k] <= i) D[(size_t)A.col[k] * n + i] = A.val[k];   // (i, col), i >= col
+    L.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = D[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s = s - L[(size_t)k * n + j] * L[(size_t)k * n + j];
+        if (!(s > 0.0)) return false;
+        double ljj = std::sqrt(s);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = D[(size_t)j * n + i];
+            for (int k = 0; k < j; ++k) t = t - L[(size_t)k * n + i] * L[(size_t)k * n + j];
+            L[(size_t)j * n + i] = t / ljj;
+        }
+    }
+    return true;
+}
+
+void cholesky_solve(const std::vector<double>& L, int n, const double* b, double* x) {
+    std::vector<double> y(b, b + n);
+    for (int i = 0; i < n; ++i) {                      // L y = b
+        double t = y[i];
+        for (int k = 0; k < i; ++k) t = t - L[(size_t)k * n + i] * y[k];
+        y[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {                 // L^T x = y
+        double t = y[i];
+        for (int k = i + 1; k < n; ++k) t = t - L[(size_t)i * n + k] * y[k];
+        y[i] = t / L[(size_t)i * n + i];
+    }
+    std::copy(y.begin(), y.end(), x);
+}
+
+// Level loop (Sections 3.2 and 5): each level applies `sweeps` pairwise
+// matching steps, each on the Galerkin matrix and the restricted smooth vector
+// of the previous step; the level prolongator is the product of the pairwise
+// ones and the next level matrix is the last pairwise Galerkin matrix. A sweep
+// that matches nothing ends the level early. Coarsening stops as soon as the
+// new level has at most max_coarse rows, when a level brings no reduction, or
+// at max_levels levels; the last level is solved by dense Cholesky.
+int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps, int max_coarse,
+          int max_levels) {
+    H.lev.clear();
+    H.lev.push_back(Level{});
+    H.lev[0].A = A0;
+    H.lev[0].w = w0;
+    for (;;) {
+        Level& cur = H.lev.back();
+        const int l = (int)H.lev.size() - 1;
+        if (cur.A.n <= max_coarse || l + 1 >= max_levels) break;
+        Csr A = cur.A;
+        std::vector<double> w = cur.w;
+        std::vector<int32_t> agg(cur.A.n);
+        std::vector<double> p(cur.A.n, 1.0);
+        for (int i = 0; i < cur.A.n; ++i) agg[i] = i;
+        for (int s = 0; s < sweeps; ++s) {
+            int rounds = 0;
+            std::vector<int32_t> mate = H.use_ld ? match_ld_rounds(A, w, &rounds) : match_greedy(A, w);
+            Pairwise pw = aggregate(mate, w);
+            pw.rounds = rounds;
+            if (pw.nc == A.n) break;
+            Csr C = galerkin_onenz(A, pw.agg, pw.p, pw.nc);
+            for (int i = 0; i < cur.A.n; ++i) {       // compose: P <- P P_s
+                p[i] = p[i] * pw.p[agg[i]];
+                agg[i] = pw.agg[agg[i]];
+            }
+            cur.sweep_nnz.push_back(C.nnz());
+            A = std::move(C);
+            w = pw.wc;
+            cur.sweeps.push_back(std::move(pw));
+        }
+        if (A.n == cur.A.n) break;                  // no reduction: this level is the coarsest
+        cur.agg = std::move(agg);
+        cur.p = std::move(p);
+        Level next;
+        next.A = std::move(A);
+        next.w = std::move(w);
+        H.lev.push_back(std::move(next));
+    }
+    for (auto& L : H.lev) L.minv = l1_jacobi_inverse(L.A);
+    const Csr& Ac = H.lev.back().A;
+    H.nc = Ac.n;
+    if (!dense_cholesky(Ac, H.L)) return -2;
+    return 0;
+}
+
+// ------------------------------------------------------------- V-cycle -----
+void spmv(const Csr& A, const double* x, double* y) {
+    for (int i = 0; i < A.n; ++i) {
+        double s = 0.0;
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) s = s + A.val[k] * x[A.col[k]];
+        y[i] = s;
+    }
+}
+
+// x := x + omega M^{-1} (b - A x), M the l1-Jacobi diagonal.
+void smooth(const Level& L, double omega, const double* b, double* x) {
+    std::vector<double> r(L.A.n);
+    spmv(L.A, x, r.data());
+    for (int i = 0; i < L.A.n; ++i) x[i] = x[i] + (omega * L.minv[i]) * (b[i] - r[i]);
+}
+
+// B_l b for the V-cycle of Eq. 2: pre-smoothing from a zero guess, coarse
+// correction with the restricted residual, post-smoothing; the coarsest level
+// is solved exactly.
+void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
+    const Level& L = H.lev[l];
+    const int n = L.A.n;
+    if (l == (int)H.lev.size() - 1) { cholesky_solve(H.L, H.nc, b, x); return; }
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    for (int s = 0; s < H.pre; ++s) smooth(L, H.omega, b, x);
+    std::vector<double> r(n);
+    spmv(L.A, x, r.data());
+    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    const int nc = H.lev[l + 1].A.n;
+    std::vector<double> bc(nc, 0.0), ec(nc);
+    for (int i = 0; i < n; ++i) bc[L.agg[i]] = bc[L.agg[i]] + L.p[i] * r[i];     // P^T r, members ascending
+    vcycle(H, l + 1, bc.data(), ec.data());
+    for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
+    for (int s = 0; s < H.post; ++s) smooth(L, H.omega, b, x);
+}
+
+double dot(const double* a, const double* b, int n) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = s + a[i] * b[i];
+    return s;
+}
+
+// Preconditioned CG with the V-cycle (the paper's outer FCG reduces to PCG for
+// a fixed s.p.d. preconditioner). Iterations count products A p. Convergence
+// on ||r|| <= rtol ||b|| with the recursive residual; at that point the true
+// residual b - A x is formed and, if it is not below rtol, the iteration
+// restarts from it. Returns 0 converged, 1 not converged, -6 breakdown.
+int pcg(const Hierarchy& H, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+        double* true_relres) {
+    const Level& L0 = H.lev[0];
+    const int n = L0.A.n;
+    std::vector<double> r(n), z(n), p(n), q(n);
+    double nb = std::sqrt(dot(b, b, n));
+    *iters = 0;
+    if (nb == 0.0) {
+        for (int i = 0; i < n; ++i) x[i] = 0.0;
+        *relres = 0.0; *true_relres = 0.0;
+        return 0;
+    }
+    spmv(L0.A, x, r.data());
+    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    double rr = std::sqrt(dot(r.data(), r.data(), n));
+    int status = 1;
+    bool restart = true;
+    double rho = 0.0;
+    int it = 0;
+    if (rr / nb <= rtol) status = 0;
+    while (status != 0 && it < maxit) {
+        if (restart) {
+            vcycle(H, 0, r.data(), z.data());
+            p = z;
+            rho = dot(r.data(), z.data(), n);
+            restart = false;
+        }
+        spmv(L0.A, p.data(), q.data());
+        ++it;
+        double pq = dot(p.data(), q.data(), n);
+        if (!(pq > 0.0) || !std::isfinite(rho)) { status = -6; break; }
+        double alpha = rho / pq;
+        for (int i = 0; i < n; ++i) {
+            x[i] = x[i] + alpha * p[i];
+            r[i] = r[i] - alpha * q[i];
+        }
+        rr = std::sqrt(dot(r.data(), r.data(), n));
+        if (rr / nb <= rtol) {
+            spmv(L0.A, x, q.data());                // true residual check
+            for (int i = 0; i < n; ++i) q[i] = b[i] - q[i];
+            double tr = std::sqrt(dot(q.data(), q.data(), n));
+            if (tr / nb <= rtol) { status = 0; break; }
+            r = q;
+            rr = tr;
+            restart = true;
+            continue;
+        }
+        vcycle(H, 0, r.data(), z.data());
+        double rho_new = dot(r.data(), z.data(), n);
+        double beta = rho_new / rho;
+        for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rho = rho_new;
+    }
+    *iters = it;
+    *relres = rr / nb;
+    spmv(L0.A, x, q.data());
+    for (int i = 0; i < n; ++i) q[i] = b[i] - q[i];
+    *true_relres = std::sqrt(dot(q.data(), q.data(), n)) / nb;
+    return status;
+}
+
+Csr make_csr(int n, const int32_t* ptr, const int32_t* col, const double* val) {
+    Csr A;
+    A.n = n;
+    A.ptr.assign(ptr, ptr + n + 1);
+    int64_t nnz = ptr[n];
+    A.col.assign(col, col + nnz);
+    A.val.assign(val, val + nnz);
+    return A;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI --------
+extern "C" {
+
+// Edge weights for every stored entry (i, j), i != j, from the upper entry of
+// the pair (Eq. 3); diagonal entries and pairs whose upper entry is zero get
+// -infinity. Returns 0 or a validation error.
+int orc_weights(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, double* c) {
+    Csr A = make_csr(n, ptr, col, val);
+    if (int e = validate(A)) return e;
+    for (int i = 0; i < n; ++i) {
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            int j = A.col[k];
+            int lo = std::min(i, j), hi = std::max(i, j);
+            double a = A.val[find_entry(A, lo, hi)];
+            c[k] = (i == j || a == 0.0) ? -std::numeric_limits<double>::infinity()
+                                        : edge_weight(a, diag_of(A, lo), diag_of(A, hi), w[lo], w[hi]);
+        }
+    }
+    return 0;
+}
+
+int orc_match_greedy(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w,
+                     int32_t* mate) {
+    Csr A = make_csr(n, ptr, col, val);
+    if (int e = validate(A)) return e;
+    std::vector<double> wv(w, w + n);
+    std::vector<int32_t> m = match_greedy(A, wv);
+    std::copy(m.begin(), m.end(), mate);
+    return 0;
+}
+
+int orc_match_ld(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w,
+                 int32_t* mate, int* rounds) {
+    Csr A = make_csr(n, ptr, col, val);
+    if (int e = validate(A)) return e;
+    std::vector<double> wv(w, w + n);
+    std::vector<int32_t> m = match_ld_rounds(A, wv, rounds);
+    std::copy(m.begin(), m.end(), mate);
+    return 0;
+}
+
+// Builds the hierarchy. use_ld != 0 uses the locally-dominant rounds for the
+// matching (same result, also records the round counts). Returns a handle or
+// null; *status receives 0 or a negative code.
+void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
+                int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, int* status) {
+    Csr A = make_csr(n, ptr, col, val);
+    int e = validate(A);
+    for (int i = 0; e == 0 && i < n; ++i)
+        if (!std::isfinite(w[i]) || w[i] == 0.0) e = -3;
+    if (e) { *status = e; return nullptr; }
+    Hierarchy* H = new Hierarchy;
+    H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld;
+    e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels);
+    *status = e;
+    if (e) { delete H; return nullptr; }
+    return H;
+}
+
+void orc_free(void* h) { delete static_cast<Hierarchy*>(h); }
+
+int orc_num_levels(void* h) { return (int)static_cast<Hierarchy*>(h)->lev.size(); }
+
+void orc_level_dims(void* h, int l, int* n, int64_t* nnz) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    *n = L.A.n;
+    *nnz = L.A.nnz();
+}
+
+void orc_level_csr(void* h, int l, int32_t* ptr, int32_t* col, double* val) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    std::copy(L.A.ptr.begin(), L.A.ptr.end(), ptr);
+    std::copy(L.A.col.begin(), L.A.col.end(), col);
+    std::copy(L.A.val.begin(), L.A.val.end(), val);
+}
+
+void orc_level_vectors(void* h, int l, double* w, double* minv) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    std::copy(L.w.begin(), L.w.end(), w);
+    std::copy(L.minv.begin(), L.minv.end(), minv);
+}
+
+// Level prolongator (one nonzero per row): agg[i], p[i]. Not for the coarsest.
+void orc_level_prolongator(void* h, int l, int32_t* agg, double* p) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    std::copy(L.agg.begin(), L.agg.end(), agg);
+    std::copy(L.p.begin(), L.p.end(), p);
+}
+
+int orc_level_num_sweeps(void* h, int l) { return (int)static_cast<Hierarchy*>(h)->lev[l].sweeps.size(); }
+
+// Sweep s of level l: fine size n_s, coarse size, coarse nnz and LD rounds.
+void orc_sweep_dims(void* h, int l, int s, int* n, int* nc, int64_t* nnzc, int* rounds) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    const Pairwise& pw = L.sweeps[s];
+    *n = (int)pw.mate.size();
+    *nc = pw.nc;
+    *nnzc = L.sweep_nnz[s];
+    *rounds = pw.rounds;
+}
+
+void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* p, double* wc) {
+    const Pairwise& pw = static_cast<Hierarchy*>(h)->lev[l].sweeps[s];
+    std::copy(pw.mate.begin(), pw.mate.end(), mate);
+    std::copy(pw.agg.begin(), pw.agg.end(), agg);
+    std::copy(pw.p.begin(), pw.p.end(), p);
+    std::copy(pw.wc.begin(), pw.wc.end(), wc);
+}
+
+void orc_coarse_factor(void* h, double* L) {
+    const Hierarchy* H = static_cast<Hierarchy*>(h);
+    std::copy(H->L.begin(), H->L.end(), L);
+}
+
+// z = B r on level 0 (one V-cycle).
+void orc_vcycle(void* h, const double* r, double* z) { vcycle(*static_cast<Hierarchy*>(h), 0, r, z); }
+
+// z = B_l r on level l.
+void orc_vcycle_level(void* h, int l, const double* r, double* z) {
+    vcycle(*static_cast<Hierarchy*>(h), l, r, z);
+}
+
+int orc_pcg(void* h, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+            double* true_relres) {
+    return pcg(*static_cast<Hierarchy*>(h), b, x, rtol, maxit, iters, relres, true_relres);
+}
+
+}  // extern "C"
