@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the matching-AMG preconditioned CG on one GB300.
+
+Workload (default): 3D Poisson, 7-point stencil on a 256^3 grid (16.8M
+unknowns, 117M nonzeros), FP64 CSR, w = 1, 3 matching sweeps per level,
+l1-Jacobi 1+1, dense Cholesky on the coarsest level, b = A x* with
+x* ~ U[-1, 1] (seed 1), x0 = 0, PCG to rel-res 1e-6.
+
+One step = amg_setup (the whole hierarchy build) + amg_solve + amg_free with
+A, w and b already resident in HBM. The metric is time to solution (ms per
+step, lower is better). Inputs (1.4 GB) are larger than L2, so no flush is
+needed between steps.
+
+Prints one JSON line. ``--impl reference`` times the CPU oracle instead (a
+bounded sample of the same workload, scaled to the full size by unknowns).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AMG-PCG time to rel-res 1e-6 (full setup + single-RHS solve)"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--rtol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-grid", type=int, default=128)
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.remove(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(grid):
+    from paper_2006_16147_gb300 import workloads as W
+    A = W.poisson3d(grid)
+    b, _ = W.rhs_uniform(A, 1)
+    return A, b
+
+
+def _oracle_sample(grid, rtol):
+    """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance."""
+    import oracle
+    from paper_2006_16147_gb300 import workloads as W
+    A = W.poisson3d(grid)
+    b, _ = W.rhs_uniform(A, 1)
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(A)
+    t1 = time.perf_counter()
+    x, info = H.pcg(b, rtol=rtol)
+    t2 = time.perf_counter()
+    return dict(setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"], n=A.n)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    grid = min(args.grid, 64)
+    n_full = args.grid ** 3
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = _oracle_sample(grid, args.rtol)
+        if k >= args.warmup:
+            times.append((r["setup_s"] + r["solve_s"]) * 1e3 * n_full / r["n"])
+    v = statistics.mean(times)
+    sample = (f"oracle setup + PCG to {args.rtol:g} on the {grid}^3 instance of the same workload "
+              f"({r['iterations']} iterations), scaled by unknowns x{n_full / r['n']:.0f}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve", "grid": args.grid,
+                       "rtol": args.rtol},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2006_16147_gb300 import amg
+    amg.lib()
+
+    A, b = _workload(args.grid)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_ptr, d_col, d_val = t(A.row_ptr), t(A.col), t(A.val)
+    d_w = torch.ones(A.n, dtype=torch.float64, device=dev)
+    d_b = t(b)
+    d_x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = amg.AMG_FP32_VCYCLE if args.precision == "fp32" else amg.AMG_FP64
+
+    def step(profile=0, keep=False):
+        d_x.zero_()
+        h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, stream=stream.cuda_stream)
+        info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
+        if keep:
+            return h, info
+        h.close()
+        return None, info
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+
+    # ---- timed region: K steps, CUDA events on the library's stream
+    infos = []
+    hinfos = []
+    barrier()
+    launches0 = amg.amg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kstats = {}
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for k in range(args.steps):
+            h, info = step(profile=1, keep=True)
+            infos.append(info)
+            hinfos.append(amg.amg_hierarchy_info(h))
+            for name, (sc, kms, by) in amg.amg_kernel_stats(h).items():
+                s = kstats.setdefault(name, [0, 0.0, 0.0])
+                s[0] += sc
+                s[1] += kms
+                s[2] += by
+            h.close()
+        ev1.record(stream)
+        barrier()
+    launches = amg.amg_launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = clk.summary()
+
+    # residual check of the last solution (independent of the library)
+    xs = d_x.cpu().numpy()
+    rel = float(np.linalg.norm(b - A.scipy() @ xs) / np.linalg.norm(b))
+
+    # ---- roofline of the dominant solve kernel (largest summed time)
+    peak, peak_kind = _peaks()
+    solve_k = {k: v for k, v in kstats.items() if not k.startswith("setup_")}
+    dom = max(solve_k, key=lambda k: solve_k[k][1])
+    nl, ms_tot, by_tot = solve_k[dom]
+    per_launch_ms = ms_tot / nl
+    achieved = (by_tot / nl) / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": by_tot / nl, "ms_per_launch": per_launch_ms, "launches": nl // args.steps}
+    kernel_table = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": round(v[1] / args.steps, 4),
+                        "GBps": round(v[2] / max(v[1], 1e-12) / 1e6, 1) if v[2] else None}
+                    for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the host-buffer entry points (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+              for k, v in dict(ptr=A.row_ptr, col=A.col, val=A.val, w=np.ones(A.n), b=b).items()}
+        xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
+        e2e_steps = max(1, min(3, args.steps))
+        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec)
+        amg_h.close()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            xh[:] = 0.0
+            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec)
+            amg.amg_solve_host(hh, hp["b"], xh, rtol=args.rtol, maxit=1000)
+            hh.close()
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        h2d = A.row_ptr.nbytes + A.col.nbytes + A.val.nbytes + 8 * A.n * 3
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * A.n)}
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        g = min(args.cpu_sample_grid, args.grid)
+        r = _oracle_sample(g, args.rtol)
+        scale = A.n / r["n"]
+        cpu = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": (f"oracle setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s ({r['iterations']} it) "
+                          f"on the {g}^3 instance of the same workload, scaled x{scale:.0f} by unknowns")}
+
+    if rank == 0:
+        it = [i["iterations"] for i in infos]
+        hi = hinfos[-1]
+        line = {
+            "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle",
+            "data": "synthetic",
+            "config": {"workload": f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve", "grid": args.grid,
+                       "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
+                       "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",
+                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single"},
+            "iterations": it[-1], "true_relres": infos[-1]["true_relres"], "numpy_relres": rel,
+            "setup_ms": round(statistics.mean(h["setup_ms"] for h in hinfos), 3),
+            "solve_ms": round(statistics.mean(i["solve_ms"] for i in infos), 3),
+            "levels": hi["n"], "opc": round(hi["opc"], 4), "solves_per_s": round(world * 1e3 / ms, 3),
+            "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches),
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * amg.h -- C ABI of the GB300 matching-aggregation AMG + PCG library.
+ *
+ * Method: D'Ambra, Durastante, Filippone, "AMG preconditioners for linear
+ * solvers towards extreme scale". The library solves A x = b (Eq. 1) for a
+ * symmetric positive definite sparse A (Section 3.1) with conjugate gradients
+ * preconditioned by one V-cycle (Eq. 2) over a hierarchy built by coarsening
+ * based on compatible weighted matching (Section 3.2): edge weights from A and
+ * a smooth vector w (Eq. 3), a locally-dominant half-approximate matching with
+ * an index tiebreak, pairwise aggregates and the tentative prolongator (Eq. 4)
+ * repeated `sweeps` times per level, Galerkin products A_{l+1} = P^T A_l P,
+ * l1-Jacobi smoothing (Eq. 5-6 with blocks of one row) and a dense Cholesky
+ * solve on the coarsest level.
+ *
+ * Conventions shared by every call:
+ *  - Indices are int32, values float64. CSR: row_ptr[n+1], col[nnz] strictly
+ *    ascending within each row, val[nnz]. The pattern must be structurally
+ *    symmetric with a stored, positive diagonal.
+ *  - Array arguments of amg_setup / amg_solve / amg_vcycle are DEVICE pointers
+ *    (cudaMalloc'd or torch tensors on the current device) read and written in
+ *    stream order on the stream given in amg_options. The *_host variants take
+ *    host pointers and copy through device memory inside the call.
+ *  - The caller owns every array it passes; the library copies what it keeps
+ *    and never retains a caller pointer after a call returns.
+ *  - A hierarchy owns all of its device memory and is released by amg_free.
+ *    One call at a time per hierarchy (calls on one handle are serialised).
+ *  - No exception or abort crosses the ABI: every failure is an amg_status;
+ *    amg_last_error() returns a message for the calling thread. Partial
+ *    allocations are freed on failure.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_hierarchy amg_hierarchy;
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_NOT_CONVERGED = 1,   /* maxit reached; x holds the last iterate, info filled */
+    AMG_ERR_ARG = -1,        /* null pointer, bad size, malformed CSR */
+    AMG_ERR_NOT_SPD = -2,    /* diagonal missing or <= 0, non-finite value, failed Cholesky pivot */
+    AMG_ERR_BAD_W = -3,      /* smooth vector entry zero or non-finite */
+    AMG_ERR_OOM = -4,        /* device allocation failed */
+    AMG_ERR_CUDA = -5,       /* any other CUDA runtime error */
+    AMG_ERR_BREAKDOWN = -6,  /* CG breakdown: p^T A p <= 0 or non-finite scalar */
+    AMG_ERR_TIMEOUT = -7,    /* a bounded device-side loop gave up */
+    AMG_ERR_TOO_LARGE = -8,  /* coarsest level too large for the dense solve, or size limits */
+    AMG_ERR_BUDGET = -9      /* request exceeds the configured device-memory budget */
+} amg_status;
+
+enum { AMG_FP64 = 0, AMG_FP32_VCYCLE = 1 };
+
+/* Sparse matrix in CSR form (see conventions). */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+} amg_csr;
+
+/* Options; amg_options_default fills the defaults noted in brackets. */
+typedef struct {
+    int sweeps;        /* [3] pairwise matching steps per level; aggregates up to 2^sweeps (Section 3.2) */
+    int max_coarse;    /* [200] stop when a level has at most this many rows (Section 5) */
+    int max_levels;    /* [32] hierarchy depth limit, including the coarsest level */
+    int pre, post;     /* [1, 1] l1-Jacobi sweeps before and after the coarse correction (Eq. 2) */
+    double omega;      /* [1.0] smoother damping */
+    int precision;     /* [AMG_FP64] or AMG_FP32_VCYCLE: V-cycle in float inside FP64 CG */
+    int max_dense;     /* [4096] largest coarsest level accepted for the dense Cholesky solve */
+    int keep_sweeps;   /* [0] keep every sweep's matching and aggregates for amg_export_sweep */
+    int profile;       /* [0] time every kernel / setup phase with CUDA events (amg_kernel_stats) */
+    void* stream;      /* [NULL] cudaStream_t for every device operation; NULL = legacy default */
+} amg_options;
+
+/* Per-solve report. */
+typedef struct {
+    int iterations;      /* products A p (PCG iterations) */
+    int restarts;        /* restarts after a failed true-residual check */
+    double relres;       /* recursive ||r|| / ||b|| at exit */
+    double true_relres;  /* ||b - A x|| / ||b|| at exit, computed in FP64 */
+    double solve_ms;     /* wall time of the call on its stream */
+} amg_solve_info;
+
+#define AMG_MAX_LEVELS 32
+#define AMG_MAX_SWEEPS 8
+
+/* Hierarchy report (Section 5: operator complexity, coarsening ratio). */
+typedef struct {
+    int num_levels;                                  /* nl, including the coarsest */
+    int64_t n[AMG_MAX_LEVELS];                       /* rows per level */
+    int64_t nnz[AMG_MAX_LEVELS];                     /* stored entries per level */
+    int sweeps_done[AMG_MAX_LEVELS];                 /* matching sweeps applied on each level */
+    int rounds[AMG_MAX_LEVELS][AMG_MAX_SWEEPS];      /* locally-dominant rounds per sweep */
+    double opc;                                      /* sum nnz(A_l) / nnz(A_0) */
+    double avg_coarsening_ratio;                     /* mean of n_l / n_{l+1} over the nl-1 steps */
+    double setup_ms;                                 /* wall time of amg_setup */
+    size_t device_bytes;                             /* device memory held by the hierarchy */
+} amg_hier_info;
+
+void amg_options_default(amg_options* opt);
+
+/*
+ * Builds the hierarchy (Sections 3.1-3.3) from A and the smooth vector w
+ * (length n; the paper's experiments use w = 1). Device pointers.
+ * Errors: AMG_ERR_ARG (null/malformed), AMG_ERR_NOT_SPD, AMG_ERR_BAD_W,
+ * AMG_ERR_OOM, AMG_ERR_TOO_LARGE (coarsest level above max_dense),
+ * AMG_ERR_TIMEOUT, AMG_ERR_CUDA. *out is NULL on failure.
+ */
+amg_status amg_setup(const amg_csr* A, const double* w, const amg_options* opt, amg_hierarchy** out);
+
+/* As amg_setup with host arrays (A's three arrays and w). */
+amg_status amg_setup_host(const amg_csr* A, const double* w, const amg_options* opt, amg_hierarchy** out);
+
+/*
+ * PCG on A x = b preconditioned by one V-cycle (Eq. 2) per iteration, to
+ * ||b - A x|| <= rtol ||b|| (Section 5: rtol = 1e-6). Device pointers of
+ * length n: b is read, x holds the initial guess on entry and the solution on
+ * return. b = 0 returns x = 0 after zero iterations. Returns AMG_OK,
+ * AMG_NOT_CONVERGED (x and info still filled) or an error. info may be NULL.
+ */
+amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info);
+
+/* As amg_solve with host arrays b and x (copies inside the call). */
+amg_status amg_solve_host(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
+                          amg_solve_info* info);
+
+/* One application of the preconditioner, z = B r (Eq. 2), device pointers of length n. */
+amg_status amg_vcycle(amg_hierarchy* h, const double* r, double* z);
+
+/* Fills *out (see amg_hier_info). */
+amg_status amg_hierarchy_info(const amg_hierarchy* h, amg_hier_info* out);
+
+/*
+ * Copies level `level` to HOST arrays; any pointer may be NULL to skip it.
+ * row_ptr[n+1], col[nnz], val[nnz]: A_l. w[n]: smooth vector on level l.
+ * minv[n]: l1-Jacobi inverse diagonal. agg[n], p[n]: the level prolongator
+ * (one nonzero p[i] in column agg[i] of row i; not available on the coarsest).
+ */
+amg_status amg_export_level(const amg_hierarchy* h, int level, int32_t* row_ptr, int32_t* col, double* val,
+                            double* w, double* minv, int32_t* agg, double* p);
+
+/*
+ * Copies matching sweep `sweep` of level `level` to HOST arrays (requires
+ * keep_sweeps). n = rows of the matrix the sweep matched; mate[n] (partner or
+ * -1), agg[n], p[n] (Eq. 4), wc[nc] (coarse smooth vector). Any may be NULL.
+ */
+amg_status amg_sweep_dims(const amg_hierarchy* h, int level, int sweep, int32_t* n, int32_t* nc, int64_t* nnz_c);
+amg_status amg_export_sweep(const amg_hierarchy* h, int level, int sweep, int32_t* mate, int32_t* agg, double* p,
+                            double* wc);
+
+/* Dense Cholesky factor L (lower, column-major nc x nc, HOST) of the coarsest level. */
+amg_status amg_coarse_factor(const amg_hierarchy* h, double* L);
+
+/*
+ * Per-kernel timing of hierarchy h (requires options.profile): entry `idx`
+ * (0 <= idx < count returned by amg_kernel_stats_count) gives the kernel or
+ * setup-phase name, the number of timed scopes, their summed CUDA-event time
+ * on the hierarchy's stream in ms, and the summed algorithmic bytes (every
+ * array the kernel must read or write, counted once). Host outputs; any may
+ * be NULL. amg_kernel_stats_reset zeroes the counters.
+ */
+int amg_kernel_stats_count(void);
+amg_status amg_kernel_stats(amg_hierarchy* h, int idx, const char** name, int64_t* scopes, double* total_ms,
+                            double* bytes);
+amg_status amg_kernel_stats_reset(amg_hierarchy* h);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t amg_launch_count(void);
+
+/* Releases every device allocation of h. NULL is accepted. */
+void amg_free(amg_hierarchy* h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_H */

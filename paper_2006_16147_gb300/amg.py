@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the C ABI in include/amg.h (argument marshalling only).
+
+Every computation runs in libamg.so's CUDA kernels. There is no CPU fallback:
+if the library has not been built, ``lib()`` raises.
+
+Device arrays are torch CUDA tensors (contiguous, int32 / float64); the
+``*_host`` calls take numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamg.so")
+
+AMG_OK = 0
+AMG_NOT_CONVERGED = 1
+AMG_FP64 = 0
+AMG_FP32_VCYCLE = 1
+MAX_LEVELS = 32
+MAX_SWEEPS = 8
+
+STATUS_NAMES = {
+    0: "AMG_OK", 1: "AMG_NOT_CONVERGED", -1: "AMG_ERR_ARG", -2: "AMG_ERR_NOT_SPD", -3: "AMG_ERR_BAD_W",
+    -4: "AMG_ERR_OOM", -5: "AMG_ERR_CUDA", -6: "AMG_ERR_BREAKDOWN", -7: "AMG_ERR_TIMEOUT",
+    -8: "AMG_ERR_TOO_LARGE", -9: "AMG_ERR_BUDGET",
+}
+
+EXPORTED = [
+    "amg_options_default", "amg_setup", "amg_setup_host", "amg_solve", "amg_solve_host", "amg_vcycle",
+    "amg_hierarchy_info", "amg_export_level", "amg_sweep_dims", "amg_export_sweep", "amg_coarse_factor",
+    "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
+    "amg_launch_count",
+]
+
+
+class amg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class amg_options(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
+                ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class amg_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("relres", ctypes.c_double),
+                ("true_relres", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class amg_hier_info(ctypes.Structure):
+    _fields_ = [("num_levels", ctypes.c_int), ("n", ctypes.c_int64 * MAX_LEVELS),
+                ("nnz", ctypes.c_int64 * MAX_LEVELS), ("sweeps_done", ctypes.c_int * MAX_LEVELS),
+                ("rounds", (ctypes.c_int * MAX_SWEEPS) * MAX_LEVELS), ("opc", ctypes.c_double),
+                ("avg_coarsening_ratio", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libamg.so; raise if it is missing (build it with build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        L.amg_options_default.argtypes = [ctypes.POINTER(amg_options)]
+        L.amg_options_default.restype = None
+        for name in ("amg_setup", "amg_setup_host"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.POINTER(amg_csr), _vp, ctypes.POINTER(amg_options), ctypes.POINTER(_vp)]
+            f.restype = ctypes.c_int
+        for name in ("amg_solve", "amg_solve_host"):
+            f = getattr(L, name)
+            f.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(amg_solve_info)]
+            f.restype = ctypes.c_int
+        L.amg_vcycle.argtypes = [_vp, _vp, _vp]
+        L.amg_vcycle.restype = ctypes.c_int
+        L.amg_hierarchy_info.argtypes = [_vp, ctypes.POINTER(amg_hier_info)]
+        L.amg_hierarchy_info.restype = ctypes.c_int
+        L.amg_export_level.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.amg_export_level.restype = ctypes.c_int
+        L.amg_sweep_dims.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _i64p]
+        L.amg_sweep_dims.restype = ctypes.c_int
+        L.amg_export_sweep.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.amg_export_sweep.restype = ctypes.c_int
+        L.amg_coarse_factor.argtypes = [_vp, _vp]
+        L.amg_coarse_factor.restype = ctypes.c_int
+        L.amg_free.argtypes = [_vp]
+        L.amg_free.restype = None
+        L.amg_last_error.argtypes = []
+        L.amg_last_error.restype = ctypes.c_char_p
+        L.amg_kernel_stats_count.argtypes = []
+        L.amg_kernel_stats_count.restype = ctypes.c_int
+        L.amg_kernel_stats.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), _i64p,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.amg_kernel_stats.restype = ctypes.c_int
+        L.amg_kernel_stats_reset.argtypes = [_vp]
+        L.amg_kernel_stats_reset.restype = ctypes.c_int
+        L.amg_launch_count.argtypes = []
+        L.amg_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status < 0:
+        raise AmgError(status, lib().amg_last_error().decode())
+    return status
+
+
+def amg_options_default(**overrides) -> amg_options:
+    o = amg_options()
+    lib().amg_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "stream":
+            v = ctypes.c_void_p(v)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Hierarchy:
+    """Owns an amg_hierarchy*; freed by close() or garbage collection."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("hierarchy was freed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().amg_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def amg_setup(row_ptr, col, val, w, host: bool = False, **opts) -> Hierarchy:
+    """Builds the hierarchy from a CSR matrix and smooth vector w.
+
+    Device tensors (torch, cuda) unless host=True (numpy). Options as in amg_options.
+    """
+    n = int(row_ptr.shape[0] - 1)
+    A = amg_csr(n, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    if "stream" not in opts and not host:
+        opts["stream"] = _current_stream()
+    o = amg_options_default(**opts)
+    h = ctypes.c_void_p()
+    f = lib().amg_setup_host if host else lib().amg_setup
+    _check(f(ctypes.byref(A), _ptr(w), ctypes.byref(o), ctypes.byref(h)))
+    return Hierarchy(h.value, n)
+
+
+def amg_setup_host(row_ptr, col, val, w, **opts) -> Hierarchy:
+    return amg_setup(row_ptr, col, val, w, host=True, **opts)
+
+
+def _info_dict(inf, status):
+    return dict(status=status, iterations=inf.iterations, restarts=inf.restarts, relres=inf.relres,
+                true_relres=inf.true_relres, solve_ms=inf.solve_ms)
+
+
+def amg_solve(h: Hierarchy, b, x, rtol: float = 1e-6, maxit: int = 1000) -> dict:
+    """PCG with the V-cycle preconditioner; x holds x0 on entry (device tensors)."""
+    inf = amg_solve_info()
+    st = _check(lib().amg_solve(h.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(inf)))
+    return _info_dict(inf, st)
+
+
+def amg_solve_host(h: Hierarchy, b: np.ndarray, x: np.ndarray, rtol: float = 1e-6, maxit: int = 1000) -> dict:
+    inf = amg_solve_info()
+    st = _check(lib().amg_solve_host(h.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(inf)))
+    return _info_dict(inf, st)
+
+
+def amg_vcycle(h: Hierarchy, r, z) -> None:
+    _check(lib().amg_vcycle(h.handle, _ptr(r), _ptr(z)))
+
+
+def amg_hierarchy_info(h: Hierarchy) -> dict:
+    inf = amg_hier_info()
+    _check(lib().amg_hierarchy_info(h.handle, ctypes.byref(inf)))
+    nl = inf.num_levels
+    return dict(num_levels=nl, n=[inf.n[i] for i in range(nl)], nnz=[inf.nnz[i] for i in range(nl)],
+                sweeps_done=[inf.sweeps_done[i] for i in range(nl)],
+                rounds=[[inf.rounds[i][s] for s in range(inf.sweeps_done[i])] for i in range(nl)],
+                opc=inf.opc, avg_coarsening_ratio=inf.avg_coarsening_ratio, setup_ms=inf.setup_ms,
+                device_bytes=inf.device_bytes)
+
+
+def amg_export_level(h: Hierarchy, level: int) -> dict:
+    info = amg_hierarchy_info(h)
+    n, nnz = info["n"][level], info["nnz"][level]
+    last = level == info["num_levels"] - 1
+    out = dict(n=n, nnz=nnz, row_ptr=np.empty(n + 1, np.int32), col=np.empty(nnz, np.int32),
+               val=np.empty(nnz), w=np.empty(n), minv=np.empty(n),
+               agg=None if last else np.empty(n, np.int32), p=None if last else np.empty(n))
+    _check(lib().amg_export_level(h.handle, level, _ptr(out["row_ptr"]), _ptr(out["col"]), _ptr(out["val"]),
+                                  _ptr(out["w"]), _ptr(out["minv"]), _ptr(out["agg"]), _ptr(out["p"])))
+    return out
+
+
+def amg_export_sweep(h: Hierarchy, level: int, sweep: int) -> dict:
+    n, nc, nnzc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().amg_sweep_dims(h.handle, level, sweep, ctypes.byref(n), ctypes.byref(nc), ctypes.byref(nnzc)))
+    out = dict(n=n.value, nc=nc.value, nnz_c=nnzc.value, mate=np.empty(n.value, np.int32),
+               agg=np.empty(n.value, np.int32), p=np.empty(n.value), wc=np.empty(nc.value))
+    _check(lib().amg_export_sweep(h.handle, level, sweep, _ptr(out["mate"]), _ptr(out["agg"]), _ptr(out["p"]),
+                                  _ptr(out["wc"])))
+    return out
+
+
+def amg_coarse_factor(h: Hierarchy) -> np.ndarray:
+    info = amg_hierarchy_info(h)
+    nc = info["n"][-1]
+    L = np.empty(nc * nc)
+    _check(lib().amg_coarse_factor(h.handle, _ptr(L)))
+    return L.reshape(nc, nc).T.copy()
+
+
+def amg_free(h: Hierarchy) -> None:
+    h.close()
+
+
+def amg_kernel_stats(h: Hierarchy) -> dict:
+    """{name: (timed scopes, total ms, algorithmic bytes)} for scopes that ran (needs profile=1)."""
+    out = {}
+    for idx in range(lib().amg_kernel_stats_count()):
+        name = ctypes.c_char_p()
+        sc = ctypes.c_int64()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        _check(lib().amg_kernel_stats(h.handle, idx, ctypes.byref(name), ctypes.byref(sc), ctypes.byref(ms),
+                                      ctypes.byref(by)))
+        if sc.value:
+            out[name.value.decode()] = (sc.value, ms.value, by.value)
+    return out
+
+
+def amg_kernel_stats_reset(h: Hierarchy) -> None:
+    _check(lib().amg_kernel_stats_reset(h.handle))
+
+
+def amg_launch_count() -> int:
+    return int(lib().amg_launch_count())

@@ -1,0 +1,196 @@
+// amg_internal.cuh -- types and helpers shared by the library's translation
+// units (setup, solve, api). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+#include "prof.cuh"
+
+namespace amg {
+
+// ------------------------------------------------------------ errors -------
+struct Error {
+    amg_status status;
+    std::string msg;
+};
+
+void set_last_error(const std::string& m);
+
+#define AMG_THROW(st, ...)                                                  \
+    do {                                                                    \
+        char _b[512];                                                       \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                              \
+        throw ::amg::Error{(st), std::string(_b)};                          \
+    } while (0)
+
+#define CUDA_CHECK(expr)                                                                  \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            amg_status _s = (_e == cudaErrorMemoryAllocation) ? AMG_ERR_OOM : AMG_ERR_CUDA; \
+            AMG_THROW(_s, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+        }                                                                                 \
+    } while (0)
+
+#define KERNEL_CHECK()                                     \
+    do {                                                   \
+        ::amg::launch_counter().fetch_add(1, std::memory_order_relaxed); \
+        CUDA_CHECK(cudaGetLastError());                    \
+    } while (0)
+
+// ------------------------------------------------------ device memory ------
+// Owner of a set of device allocations, released together.
+struct DevArena {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    template <typename T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        CUDA_CHECK(cudaMalloc(&p, count * sizeof(T)));
+        ptrs.push_back(p);
+        bytes += count * sizeof(T);
+        return static_cast<T*>(p);
+    }
+    void release(void* p) {
+        for (size_t i = 0; i < ptrs.size(); ++i)
+            if (ptrs[i] == p) {
+                cudaFree(p);
+                ptrs[i] = ptrs.back();
+                ptrs.pop_back();
+                return;
+            }
+    }
+    void free_all() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+        bytes = 0;
+    }
+    ~DevArena() { free_all(); }
+};
+
+// ------------------------------------------------------------ formats ------
+struct DevCsr {
+    int n = 0;
+    int nnz = 0;
+    int* ptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+};
+
+// SELL-32 (sliced ELLPACK, slice height 32, no row sorting): slice s holds
+// rows 32s..32s+31; its entries start at sptr[s] and are stored column-major
+// inside the slice (entry k of lane r at sptr[s] + 32k + r). Short rows are
+// padded with (col = row, val = 0).
+constexpr int SELL_C = 32;
+struct DevSell {
+    int n = 0;
+    int nslices = 0;
+    int64_t padded = 0;
+    int* sptr = nullptr;   // nslices + 1, in entries
+    int* col = nullptr;
+    double* val = nullptr;
+    float* val32 = nullptr;
+};
+
+struct SweepRecord {
+    int n = 0, nc = 0;
+    int64_t nnz_c = 0;
+    int rounds = 0;
+    int* mate = nullptr;
+    int* agg = nullptr;
+    double* p = nullptr;
+    double* wc = nullptr;
+};
+
+struct Level {
+    DevCsr A;
+    DevSell S;
+    double* w = nullptr;        // smooth vector on this level
+    double* minv = nullptr;     // l1-Jacobi inverse diagonal
+    float* minv32 = nullptr;
+    // prolongator to the next level (one nonzero per row) and its transpose
+    int* agg = nullptr;
+    double* p = nullptr;
+    float* p32 = nullptr;
+    int* pt_ptr = nullptr;      // n_{l+1} + 1
+    int* pt_idx = nullptr;      // n_l, members of each aggregate ascending
+    int sweeps_done = 0;
+    int rounds[AMG_MAX_SWEEPS] = {0};
+    std::vector<SweepRecord> sweeps;
+    // V-cycle work vectors (FP64 and FP32 copies)
+    double *b = nullptr, *x = nullptr, *r = nullptr, *y = nullptr, *t = nullptr, *u = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *y32 = nullptr, *t32 = nullptr, *u32 = nullptr;
+};
+
+// Device-resident scalars of one PCG solve.
+struct PcgScalars {
+    double rho;       // r . z
+    double rho_new;
+    double alpha, beta;
+    double pq;        // p . A p
+    double rr;        // ||r||^2
+    double bb;        // ||b||^2
+    int breakdown;
+    int pad;
+};
+
+struct Reducer {
+    double* partial = nullptr;   // one slot per block
+    unsigned* ticket = nullptr;  // last-block counter
+    int blocks = 0;
+};
+
+}  // namespace amg
+
+struct amg_hierarchy {
+    amg_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    amg::DevArena mem;
+    std::vector<amg::Level> lev;
+    int nc = 0;                 // coarsest size
+    double* coarse_L = nullptr;  // dense Cholesky factor (column-major)
+    double* coarse_inv = nullptr;// dense inverse A_L^{-1} (row-major)
+    // PCG workspace (level 0 sized)
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *t = nullptr;
+    amg::PcgScalars* sc = nullptr;      // device
+    amg::PcgScalars* sc_host = nullptr; // pinned mirror
+    amg::Reducer red;
+    double setup_ms = 0.0;
+    amg::Profiler prof;
+    std::mutex lock;
+};
+
+namespace amg {
+
+// ------------------------------------------------------- launch sizes ------
+inline int blocks_for(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// Exclusive prefix sum of int32 counts (out may alias in). Returns the total
+// through *total_dev (device) and, if total_host is non-null, synchronously
+// to the host.
+void scan_exclusive(const int* in, int* out, int n, int* total_dev, cudaStream_t st, int* scratch_blocks);
+size_t scan_scratch_ints(int n);
+
+// Setup and solve entry points used by the api translation unit.
+void setup_hierarchy(amg_hierarchy* h, const amg_csr* A, const double* w);
+void prepare_solve(amg_hierarchy* h);
+amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info);
+void vcycle_apply(amg_hierarchy* h, const double* r, double* z);
+
+}  // namespace amg

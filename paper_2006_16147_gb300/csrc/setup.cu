@@ -1,0 +1,790 @@
+// setup.cu -- hierarchy construction on the device: coarsening based on
+// compatible weighted matching (Section 3.2), Galerkin products (Section 3.1),
+// l1-Jacobi smoother setup (Section 3.3, Eq. 5-6 with one-row blocks) and the
+// dense Cholesky factor of the coarsest level.
+//
+// The matching and the operators it produces must not depend on rounding
+// choices: weights (Eq. 3), the pair normalisation (Eq. 4) and the Galerkin
+// sums use explicitly rounded operations (__dmul_rn, __dadd_rn, ...), never a
+// fused multiply-add, in a fixed order that is part of the definition.
+#include <chrono>
+#include <cmath>
+
+#include "amg_internal.cuh"
+#include "device_util.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr int TPB = 256;
+
+// ------------------------------------------------------------- checks ------
+enum : int { F_SHAPE = 1, F_NOT_SPD = 2, F_BAD_W = 4 };
+
+__device__ __forceinline__ int find_in_row(const int* __restrict__ ptr, const int* __restrict__ col, int row, int j) {
+    int lo = ptr[row], hi = ptr[row + 1];
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < j) lo = mid + 1; else hi = mid;
+    }
+    return (lo < ptr[row + 1] && col[lo] == j) ? lo : -1;
+}
+
+// Row pointers first: monotone, starting at 0, ending at nnz.
+__global__ void k_check_ptr(int n, int nnz, const int* __restrict__ ptr, int* flags) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n; i += (long long)gridDim.x * blockDim.x) {
+        int a = ptr[i];
+        bool bad = (a < 0 || a > nnz) || (i == 0 && a != 0) || (i == n && a != nnz) || (i < n && ptr[i + 1] < a);
+        if (bad) atomicOr(flags, F_SHAPE);
+    }
+}
+
+// Columns sorted and in range, finite values, positive stored diagonal,
+// symmetric pattern; w finite and nonzero. Writes the diagonal.
+__global__ void k_check_rows(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ w, double* __restrict__ diag,
+                             int* flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int f = 0;
+        double d = 0.0;
+        int prev = -1;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            int j = col[k];
+            if (j < 0 || j >= n || j <= prev) { f |= F_SHAPE; break; }
+            prev = j;
+            double v = val[k];
+            if (!isfinite(v)) f |= F_NOT_SPD;
+            if (j == i) d = v;
+            else if (find_in_row(ptr, col, j, i) < 0) f |= F_SHAPE;
+        }
+        if (!(d > 0.0)) f |= F_NOT_SPD;
+        double wi = w[i];
+        if (!isfinite(wi) || wi == 0.0) f |= F_BAD_W;
+        diag[i] = d;
+        if (f) atomicOr(flags, f);
+    }
+}
+
+__global__ void k_diag(int n, const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
+                       double* __restrict__ diag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int k = find_in_row(ptr, col, i, i);
+        diag[i] = k >= 0 ? val[k] : 0.0;
+    }
+}
+
+// --------------------------------------------------- Eq. 3 edge weights ----
+// c_ij = 1 - 2 a_ij w_i w_j / (a_ii w_i^2 + a_jj w_j^2) for the pair {lo, hi}
+// from the upper entry a_{lo,hi}; written at both stored positions of the
+// pair. Diagonal entries and pairs whose upper entry is 0 are not edges and
+// get -inf.
+__global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ val, const double* __restrict__ diag,
+                          const double* __restrict__ w, double* __restrict__ c) {
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double wi = w[i], di = diag[i];
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            const int j = col[k];
+            if (j < i) continue;                 // written by the thread of row j
+            if (j == i) { c[k] = NEG_INF; continue; }
+            const double a = val[k];
+            double cw = NEG_INF;
+            if (a != 0.0) {
+                const double wj = w[j];
+                double den = __dadd_rn(__dmul_rn(__dmul_rn(di, wi), wi), __dmul_rn(__dmul_rn(diag[j], wj), wj));
+                double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wi), wj);
+                cw = __dsub_rn(1.0, __ddiv_rn(num, den));
+            }
+            c[k] = cw;
+            const int mirror = find_in_row(ptr, col, j, i);
+            if (mirror >= 0) c[mirror] = cw;
+        }
+    }
+}
+
+// ------------------------------------- locally-dominant matching rounds ----
+// mate[v]: -1 free, -2 free without free neighbours, >= 0 partner.
+// cand[v]: best free neighbour of a free v under the strict edge order
+// (weight descending, lower end ascending, upper end ascending).
+__device__ __forceinline__ bool key_better(double c1, int lo1, int hi1, double c2, int lo2, int hi2) {
+    if (c1 != c2) return c1 > c2;
+    if (lo1 != lo2) return lo1 < lo2;
+    return hi1 < hi2;
+}
+
+__device__ __forceinline__ int best_free(int v, const int* __restrict__ ptr, const int* __restrict__ col,
+                                         const double* __restrict__ c, const int* mate) {
+    int best = -1, blo = 0, bhi = 0;
+    double bc = 0.0;
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
+        const double cw = c[k];
+        if (cw == NEG_INF) continue;
+        const int u = col[k];
+        if (mate[u] != -1) continue;
+        const int lo = min(u, v), hi = max(u, v);
+        if (best < 0 || key_better(cw, lo, hi, bc, blo, bhi)) {
+            best = u; bc = cw; blo = lo; bhi = hi;
+        }
+    }
+    return best;
+}
+
+__global__ void k_ld_init(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ c, int* cand, int* mate) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int b = best_free(v, ptr, col, c, mate);
+        cand[v] = b;
+        if (b < 0) mate[v] = -2;   // isolated: nobody reads it
+    }
+}
+
+// Round, part 1: mutual candidates are locally dominant edges; match them.
+// list == nullptr means every vertex. Zeroes the next round's list counter.
+__global__ void k_ld_match(int n, const int* __restrict__ list, const int* __restrict__ list_cnt, const int* cand,
+                           int* mate, int* mlist, int* mcnt, int* zero_next, int* rounds) {
+    const int cnt = list ? min(*list_cnt, n) : n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *zero_next = 0;
+        if (cnt > 0) *rounds += 1;
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int v = list ? list[t] : t;
+        bool take = false;
+        int lo = 0, hi = 0;
+        if (mate[v] == -1) {
+            const int u = cand[v];
+            if (u >= 0 && cand[u] == v) {
+                lo = min(u, v); hi = max(u, v);
+                if (atomicCAS(&mate[lo], -1, hi) == -1) {
+                    mate[hi] = lo;
+                    take = true;
+                }
+            }
+        }
+        warp_append(take, lo, mlist, mcnt, n);
+        warp_append(take, hi, mlist, mcnt, n);
+    }
+}
+
+// Round, part 2: free vertices whose candidate was just matched pick a new
+// one; they form the next round's list. Zeroes the next round's match counter.
+__global__ void k_ld_update(int n, const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ c,
+                            int* cand, int* mate, const int* __restrict__ mlist, const int* __restrict__ mcnt,
+                            int* next_list, int* next_cnt, int* zero_next_m) {
+    const int cnt = min(*mcnt, n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *zero_next_m = 0;
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+        const int m = mlist[t];
+        for (int k = ptr[m]; k < ptr[m + 1]; ++k) {
+            bool take = false;
+            int x = col[k];
+            if (c[k] != NEG_INF && mate[x] == -1 && cand[x] == m) {
+                const int b = best_free(x, ptr, col, c, mate);
+                cand[x] = b;
+                if (b < 0) mate[x] = -2;
+                else take = true;
+            }
+            warp_append(take, x, next_list, next_cnt, n);
+        }
+    }
+}
+
+// ------------------------------------------ aggregates + Eq. 4 prolongator --
+__global__ void k_head_flags(int n, const int* __restrict__ mate, int* __restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int m = mate[i];
+        flag[i] = (m < 0 || m > i) ? 1 : 0;
+    }
+}
+
+// Aggregate q = number of heads (smallest members) before it. Pair columns
+// are w restricted to the pair and normalised; singletons sign(w_s).
+__global__ void k_aggregate(int n, const int* __restrict__ mate, const int* __restrict__ qid,
+                            const double* __restrict__ w, int* __restrict__ agg, double* __restrict__ p,
+                            double* __restrict__ wc, int* __restrict__ heads, int* __restrict__ mate_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int j = mate[i];
+        if (mate_out) mate_out[i] = j < 0 ? -1 : j;
+        if (j >= 0 && j < i) continue;
+        const int q = qid[i];
+        const double wi = w[i];
+        heads[q] = i;
+        if (j < 0) {
+            agg[i] = q;
+            p[i] = wi > 0.0 ? 1.0 : -1.0;
+            wc[q] = fabs(wi);
+        } else {
+            const double wj = w[j];
+            const double s = __dsqrt_rn(__dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj)));
+            agg[i] = q;
+            agg[j] = q;
+            p[i] = __ddiv_rn(wi, s);
+            p[j] = __ddiv_rn(wj, s);
+            wc[q] = s;
+        }
+    }
+}
+
+// --------------------------------------- pairwise Galerkin product ---------
+// Coarse row q has members h = heads[q] and, for a pair, mate[h] > h.
+__global__ void k_rap_bound(int nc, const int* __restrict__ heads, const int* __restrict__ mate,
+                            const int* __restrict__ ptr, int* __restrict__ ub) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int h = heads[q];
+        const int m = mate[h];
+        int u = ptr[h + 1] - ptr[h];
+        if (m > h) u += ptr[m + 1] - ptr[m];
+        ub[q] = u;
+    }
+}
+
+// Expands coarse row q into scratch (coarse column, term) in member order
+// then column order, sorts the segment stably by coarse column and sums each
+// run left to right starting from its first term. cnt[q] = distinct columns.
+__global__ void k_rap_rows(int nc, const int* __restrict__ heads, const int* __restrict__ mate,
+                           const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
+                           const int* __restrict__ agg, const double* __restrict__ p, const int* __restrict__ off,
+                           int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int h = heads[q];
+        const int m = mate[h];
+        int* K = skey + off[q];
+        double* V = sval + off[q];
+        int len = 0;
+        for (int s = 0; s < 2; ++s) {
+            const int i = s == 0 ? h : m;
+            if (s == 1 && m <= h) break;
+            const double pi = p[i];
+            for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+                const int j = col[k];
+                K[len] = agg[j];
+                V[len] = __dmul_rn(__dmul_rn(pi, val[k]), p[j]);
+                ++len;
+            }
+        }
+        for (int a = 1; a < len; ++a) {              // stable insertion sort by key
+            const int key = K[a];
+            const double v = V[a];
+            int b = a - 1;
+            while (b >= 0 && K[b] > key) {
+                K[b + 1] = K[b];
+                V[b + 1] = V[b];
+                --b;
+            }
+            K[b + 1] = key;
+            V[b + 1] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < len;) {
+            const int key = K[a];
+            double s = V[a];
+            int e = a + 1;
+            while (e < len && K[e] == key) { s = __dadd_rn(s, V[e]); ++e; }
+            K[u] = key;
+            V[u] = s;
+            ++u;
+            a = e;
+        }
+        cnt[q] = u;
+    }
+}
+
+__global__ void k_rap_copy(int nc, const int* __restrict__ off, const int* __restrict__ cptr,
+                           const int* __restrict__ skey, const double* __restrict__ sval, int* __restrict__ ccol,
+                           double* __restrict__ cval) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int s = off[q], d = cptr[q], e = cptr[q + 1];
+        for (int k = 0; k < e - d; ++k) {
+            ccol[d + k] = skey[s + k];
+            cval[d + k] = sval[s + k];
+        }
+    }
+}
+
+// P_l <- P_l P_s: agg_l = agg_s o agg_l, p_l = p_l * p_s(agg_l).
+__global__ void k_compose(int n, int* __restrict__ agg_l, double* __restrict__ p_l, const int* __restrict__ agg_s,
+                          const double* __restrict__ p_s) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int a = agg_l[i];
+        p_l[i] = __dmul_rn(p_l[i], p_s[a]);
+        agg_l[i] = agg_s[a];
+    }
+}
+
+// ------------------------------------------------------- P^T member lists --
+__global__ void k_member_count(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) atomicAdd(&cnt[agg[i]], 1);
+}
+
+__global__ void k_member_fill(int n, const int* __restrict__ agg, const int* __restrict__ pt_ptr, int* cursor,
+                              int* __restrict__ idx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int q = agg[i];
+        idx[pt_ptr[q] + atomicAdd(&cursor[q], 1)] = i;
+    }
+}
+
+__global__ void k_member_sort(int nc, const int* __restrict__ pt_ptr, int* __restrict__ idx) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int b = pt_ptr[q], e = pt_ptr[q + 1];
+        for (int a = b + 1; a < e; ++a) {
+            const int v = idx[a];
+            int c = a - 1;
+            while (c >= b && idx[c] > v) { idx[c + 1] = idx[c]; --c; }
+            idx[c + 1] = v;
+        }
+    }
+}
+
+// ----------------------------------------------- l1-Jacobi (Eq. 5-6) -------
+// M_ii = a_ii + sum_{j != i} |a_ij| (row order), stored as its inverse.
+__global__ void k_l1_jacobi(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                            const double* __restrict__ val, double* __restrict__ minv, float* __restrict__ minv32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0, d = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            if (col[k] == i) d = val[k];
+            else s = __dadd_rn(s, fabs(val[k]));
+        }
+        const double m = __ddiv_rn(1.0, __dadd_rn(d, s));
+        minv[i] = m;
+        if (minv32) minv32[i] = (float)m;
+    }
+}
+
+__global__ void k_to_float(long long n, const double* __restrict__ a, float* __restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------ SELL-32 ------
+// width[s] = longest row of slice s.
+__global__ void k_sell_width(int n, int nslices, const int* __restrict__ ptr, int* __restrict__ width) {
+    const int lane = threadIdx.x & 31;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t >> 5);
+        const int i = (int)t;
+        const int len = i < n ? ptr[i + 1] - ptr[i] : 0;
+        const int m = warp_max_int(len);
+        if (lane == 0) width[s] = m;
+    }
+}
+
+__global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ col,
+                            const double* __restrict__ val, const int* __restrict__ sptr, int* __restrict__ scol,
+                            double* __restrict__ sval) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t >> 5), lane = (int)(t & 31);
+        const int i = (int)t;
+        const int width = sptr[s + 1] - sptr[s];
+        long long pos = (long long)sptr[s] * 32 + lane;
+        int len = 0, b = 0;
+        if (i < n) { b = ptr[i]; len = ptr[i + 1] - b; }
+        const int pad = i < n ? i : 0;
+        for (int k = 0; k < width; ++k, pos += 32) {
+            if (k < len) { scol[pos] = col[b + k]; sval[pos] = val[b + k]; }
+            else { scol[pos] = pad; sval[pos] = 0.0; }
+        }
+    }
+}
+
+// ----------------------------------------------- coarsest: dense Cholesky --
+__global__ void k_dense_lower(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                              const double* __restrict__ val, double* __restrict__ D) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] <= i) D[(size_t)col[k] * n + i] = val[k];
+}
+
+// Left-looking column Cholesky A = L L^T in one block; column-major,
+// sequential sums in k (the textbook order). flag = 1 on a non-positive pivot.
+__global__ void k_cholesky(int n, const double* __restrict__ D, double* __restrict__ L, int* flag) {
+    __shared__ double ljj_s;
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double s = D[(size_t)j * n + j];
+            for (int k = 0; k < j; ++k) {
+                const double l = L[(size_t)k * n + j];
+                s = __dsub_rn(s, __dmul_rn(l, l));
+            }
+            if (!(s > 0.0)) { *flag = 1; s = 1.0; }
+            ljj_s = __dsqrt_rn(s);
+            L[(size_t)j * n + j] = ljj_s;
+        }
+        __syncthreads();
+        const double ljj = ljj_s;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double t = D[(size_t)j * n + i];
+            for (int k = 0; k < j; ++k) t = __dsub_rn(t, __dmul_rn(L[(size_t)k * n + i], L[(size_t)k * n + j]));
+            L[(size_t)j * n + i] = __ddiv_rn(t, ljj);
+        }
+        __syncthreads();
+    }
+}
+
+// Y = L^{-1} (column-major, lower), one column per thread.
+__global__ void k_lower_inverse(int n, const double* __restrict__ L, double* __restrict__ Y) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int i = 0; i < c; ++i) Y[(size_t)c * n + i] = 0.0;
+    Y[(size_t)c * n + c] = 1.0 / L[(size_t)c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+        double t = 0.0;
+        for (int k = c; k < i; ++k) t = fma(L[(size_t)k * n + i], Y[(size_t)c * n + k], t);
+        Y[(size_t)c * n + i] = -t / L[(size_t)i * n + i];
+    }
+}
+
+// Ainv = Y^T Y (row-major).
+__global__ void k_gram(int n, const double* __restrict__ Y, double* __restrict__ Ainv) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n) return;
+    const int i = (int)(t / n), j = (int)(t % n);
+    double s = 0.0;
+    for (int k = max(i, j); k < n; ++k) s = fma(Y[(size_t)i * n + k], Y[(size_t)j * n + k], s);
+    Ainv[(size_t)i * n + j] = s;
+}
+
+// ------------------------------------------------------------ host side ----
+struct Scratch {
+    DevArena mem;
+    double* diag = nullptr;
+    double* c = nullptr;
+    int *mate = nullptr, *cand = nullptr, *list0 = nullptr, *list1 = nullptr, *mlist = nullptr;
+    int* cnt = nullptr;       // [0,1] list counters, [2,3] match counters, [4] rounds, [5] flags, [6..7] totals
+    int* flag = nullptr;      // n
+    int* qid = nullptr;       // n
+    int* heads = nullptr;     // n
+    int* ub = nullptr;        // n + 1
+    int* off = nullptr;       // n + 1
+    int* skey = nullptr;      // nnz
+    double* sval = nullptr;   // nnz
+    int* scan_tmp = nullptr;
+    int* host = nullptr;      // pinned
+    ~Scratch() {
+        if (host) cudaFreeHost(host);
+    }
+};
+
+int grid_for(const amg_hierarchy* h, long long n) { return blocks_for(n, TPB, h->num_sms * 16); }
+
+int read_int(const int* dev, int* host, cudaStream_t st) {
+    CUDA_CHECK(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return *host;
+}
+
+// Locally-dominant matching by frontier rounds. Returns the number of rounds.
+int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
+    cudaStream_t st = h->stream;
+    const int n = A.n;
+    CUDA_CHECK(cudaMemsetAsync(S.mate, 0xff, sizeof(int) * n, st));   // all -1
+    CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 5, st));
+    k_ld_init<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.cand, S.mate);
+    KERNEL_CHECK();
+    int* lists[2] = {S.list0, S.list1};
+    int* lcnt = S.cnt;          // two slots
+    int* mcnt = S.cnt + 2;      // two slots
+    const int grid = h->num_sms * 8;
+    const int batch = 16;
+    const long long max_rounds = (long long)n + 4;
+    long long r = 0;
+    for (;;) {
+        for (int b = 0; b < batch; ++b, ++r) {
+            const int cur = (int)(r & 1), nxt = (int)((r + 1) & 1);
+            k_ld_match<<<grid, TPB, 0, st>>>(n, r == 0 ? nullptr : lists[cur], &lcnt[cur], S.cand, S.mate, S.mlist,
+                                             &mcnt[cur], &lcnt[nxt], S.cnt + 4);
+            KERNEL_CHECK();
+            k_ld_update<<<grid, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.cand, S.mate, S.mlist, &mcnt[cur], lists[nxt],
+                                              &lcnt[nxt], &mcnt[nxt]);
+            KERNEL_CHECK();
+        }
+        if (read_int(&lcnt[r & 1], S.host, st) == 0) break;
+        if (r > max_rounds) AMG_THROW(AMG_ERR_TIMEOUT, "matching did not settle after %lld rounds", r);
+    }
+    return read_int(S.cnt + 4, S.host, st);
+}
+
+struct SweepOut {
+    int nc;
+    int* agg;
+    double* p;
+    double* wc;
+};
+
+// Pairwise Galerkin product C = P^T A P (one nonzero per row of P).
+DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const SweepOut& sw, DevArena& owner) {
+    cudaStream_t st = h->stream;
+    const int nc = sw.nc;
+    k_rap_bound<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, S.ub);
+    KERNEL_CHECK();
+    scan_exclusive(S.ub, S.off, nc, S.cnt + 6, st, S.scan_tmp);
+    k_rap_rows<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
+                                                S.skey, S.sval, S.ub);
+    KERNEL_CHECK();
+    DevCsr C;
+    C.n = nc;
+    C.ptr = owner.alloc<int>(nc + 1);
+    scan_exclusive(S.ub, C.ptr, nc, C.ptr + nc, st, S.scan_tmp);
+    C.nnz = read_int(C.ptr + nc, S.host, st);
+    C.col = owner.alloc<int>(C.nnz);
+    C.val = owner.alloc<double>(C.nnz);
+    k_rap_copy<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val);
+    KERNEL_CHECK();
+    return C;
+}
+
+void build_sell(amg_hierarchy* h, Level& L, Scratch& S, bool fp32) {
+    cudaStream_t st = h->stream;
+    DevSell& E = L.S;
+    E.n = L.A.n;
+    E.nslices = (L.A.n + SELL_C - 1) / SELL_C;
+    E.sptr = h->mem.alloc<int>(E.nslices + 1);
+    k_sell_width<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(L.A.n, E.nslices, L.A.ptr,
+                                                                                             S.ub);
+    KERNEL_CHECK();
+    scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
+    E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
+    E.col = h->mem.alloc<int>(E.padded);
+    E.val = h->mem.alloc<double>(E.padded);
+    k_sell_fill<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
+        L.A.n, E.nslices, L.A.ptr, L.A.col, L.A.val, E.sptr, E.col, E.val);
+    KERNEL_CHECK();
+    if (fp32) {
+        E.val32 = h->mem.alloc<float>(E.padded);
+        k_to_float<<<blocks_for(E.padded, TPB, h->num_sms * 16), TPB, 0, st>>>(E.padded, E.val, E.val32);
+        KERNEL_CHECK();
+    }
+}
+
+void build_members(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
+    cudaStream_t st = h->stream;
+    const int n = L.A.n;
+    L.pt_ptr = h->mem.alloc<int>(nc + 1);
+    L.pt_idx = h->mem.alloc<int>(n);
+    CUDA_CHECK(cudaMemsetAsync(S.ub, 0, sizeof(int) * (nc + 1), st));
+    k_member_count<<<grid_for(h, n), TPB, 0, st>>>(n, L.agg, S.ub);
+    KERNEL_CHECK();
+    scan_exclusive(S.ub, L.pt_ptr, nc, L.pt_ptr + nc, st, S.scan_tmp);
+    CUDA_CHECK(cudaMemsetAsync(S.ub, 0, sizeof(int) * (nc + 1), st));
+    k_member_fill<<<grid_for(h, n), TPB, 0, st>>>(n, L.agg, L.pt_ptr, S.ub, L.pt_idx);
+    KERNEL_CHECK();
+    k_member_sort<<<grid_for(h, nc), TPB, 0, st>>>(nc, L.pt_ptr, L.pt_idx);
+    KERNEL_CHECK();
+}
+
+}  // namespace
+
+void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->stream;
+    const amg_options& o = h->opt;
+    const int n0 = Ain->n, nnz0 = Ain->nnz;
+
+    Scratch S;
+    CUDA_CHECK(cudaHostAlloc(&S.host, 64, cudaHostAllocDefault));
+    S.diag = S.mem.alloc<double>(n0);
+    S.c = S.mem.alloc<double>(nnz0);
+    S.mate = S.mem.alloc<int>(n0);
+    S.cand = S.mem.alloc<int>(n0);
+    S.list0 = S.mem.alloc<int>(n0);
+    S.list1 = S.mem.alloc<int>(n0);
+    S.mlist = S.mem.alloc<int>(n0);
+    S.cnt = S.mem.alloc<int>(16);
+    S.flag = S.mem.alloc<int>(n0 + 1);
+    S.qid = S.mem.alloc<int>(n0 + 1);
+    S.heads = S.mem.alloc<int>(n0 + 1);
+    S.ub = S.mem.alloc<int>(n0 + 2);
+    S.off = S.mem.alloc<int>(n0 + 2);
+    S.skey = S.mem.alloc<int>(nnz0);
+    S.sval = S.mem.alloc<double>(nnz0);
+    S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
+
+    // ---- level 0: private copy of A and w, validated
+    h->lev.clear();
+    h->lev.emplace_back();
+    {
+        Level& L0 = h->lev[0];
+        L0.A.n = n0;
+        L0.A.nnz = nnz0;
+        L0.A.ptr = h->mem.alloc<int>(n0 + 1);
+        L0.A.col = h->mem.alloc<int>(nnz0);
+        L0.A.val = h->mem.alloc<double>(nnz0);
+        L0.w = h->mem.alloc<double>(n0);
+        CUDA_CHECK(cudaMemcpyAsync(L0.A.ptr, Ain->row_ptr, sizeof(int) * (n0 + 1), cudaMemcpyDefault, st));
+        CUDA_CHECK(cudaMemcpyAsync(L0.A.col, Ain->col, sizeof(int) * (size_t)nnz0, cudaMemcpyDefault, st));
+        CUDA_CHECK(cudaMemcpyAsync(L0.A.val, Ain->val, sizeof(double) * (size_t)nnz0, cudaMemcpyDefault, st));
+        CUDA_CHECK(cudaMemcpyAsync(L0.w, w_in, sizeof(double) * n0, cudaMemcpyDefault, st));
+        Scope sc_(&h->prof, st, S_VALIDATE, 16.0 * nnz0 + 16.0 * n0);
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
+        k_check_ptr<<<grid_for(h, n0 + 1), TPB, 0, st>>>(n0, nnz0, L0.A.ptr, S.cnt + 5);
+        KERNEL_CHECK();
+        int f = read_int(S.cnt + 5, S.host, st);
+        if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "row_ptr is not a valid CSR row pointer");
+        k_check_rows<<<grid_for(h, n0), TPB, 0, st>>>(n0, L0.A.ptr, L0.A.col, L0.A.val, L0.w, S.diag, S.cnt + 5);
+        KERNEL_CHECK();
+        f = read_int(S.cnt + 5, S.host, st);
+        if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "CSR columns unsorted, out of range, or pattern not symmetric");
+        if (f & F_NOT_SPD) AMG_THROW(AMG_ERR_NOT_SPD, "non-finite value or diagonal entry missing or <= 0");
+        if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "smooth vector w has a zero or non-finite entry");
+    }
+
+    // ---- level loop (Section 3.2 coarsening, Section 5 stop rule)
+    for (;;) {
+        const int l = (int)h->lev.size() - 1;
+        if (h->lev[l].A.n <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
+        const int nl = h->lev[l].A.n;
+        DevCsr A = h->lev[l].A;
+        double* w = h->lev[l].w;
+        int* agg_l = h->mem.alloc<int>(nl);
+        double* p_l = h->mem.alloc<double>(nl);
+        std::vector<SweepRecord> recs;
+        int sweeps_done = 0;
+        int rounds[AMG_MAX_SWEEPS] = {0};
+        for (int s = 0; s < o.sweeps && s < AMG_MAX_SWEEPS; ++s) {
+            const int n = A.n;
+            {
+                Scope sc_(&h->prof, st, S_WEIGHTS, 20.0 * A.nnz + 24.0 * n);
+                k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag);
+                KERNEL_CHECK();
+                k_weights<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag, w, S.c);
+                KERNEL_CHECK();
+            }
+            int rr = 0;
+            {
+                Scope sc_(&h->prof, st, S_MATCH, 0.0);
+                rr = ld_match(h, S, A);
+            }
+            int nc = 0;
+            {
+                Scope sc_(&h->prof, st, S_AGGREGATE, 0.0);
+                k_head_flags<<<grid_for(h, n), TPB, 0, st>>>(n, S.mate, S.flag);
+                KERNEL_CHECK();
+                scan_exclusive(S.flag, S.qid, n, S.cnt + 6, st, S.scan_tmp);
+                nc = read_int(S.cnt + 6, S.host, st);
+            }
+            if (nc == n) break;                                   // nothing matched: end the level
+            SweepOut sw;
+            sw.nc = nc;
+            sw.agg = h->mem.alloc<int>(n);
+            sw.p = h->mem.alloc<double>(n);
+            sw.wc = h->mem.alloc<double>(nc);
+            int* mate_keep = o.keep_sweeps ? h->mem.alloc<int>(n) : nullptr;
+            {
+                Scope sc_(&h->prof, st, S_AGGREGATE, 0.0);
+                k_aggregate<<<grid_for(h, n), TPB, 0, st>>>(n, S.mate, S.qid, w, sw.agg, sw.p, sw.wc, S.heads,
+                                                            mate_keep);
+                KERNEL_CHECK();
+            }
+            DevCsr C;
+            {
+                Scope sc_(&h->prof, st, S_GALERKIN, 12.0 * A.nnz + 12.0 * n);
+                C = galerkin_pairwise(h, S, A, sw, h->mem);
+            }
+            Scope sc_compose(&h->prof, st, S_COMPOSE, 24.0 * nl);
+            if (s == 0) {
+                CUDA_CHECK(cudaMemcpyAsync(agg_l, sw.agg, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+                CUDA_CHECK(cudaMemcpyAsync(p_l, sw.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            } else {
+                k_compose<<<grid_for(h, nl), TPB, 0, st>>>(nl, agg_l, p_l, sw.agg, sw.p);
+                KERNEL_CHECK();
+            }
+            rounds[s] = rr;
+            if (o.keep_sweeps) {
+                SweepRecord R;
+                R.n = n; R.nc = nc; R.nnz_c = C.nnz; R.rounds = rr;
+                R.mate = mate_keep; R.agg = sw.agg; R.p = sw.p; R.wc = sw.wc;
+                recs.push_back(R);
+            } else {
+                CUDA_CHECK(cudaStreamSynchronize(st));
+                h->mem.release(sw.agg);
+                h->mem.release(sw.p);
+            }
+            // the previous intermediate matrix and smooth vector are no longer needed
+            if (A.ptr != h->lev[l].A.ptr) {
+                CUDA_CHECK(cudaStreamSynchronize(st));
+                h->mem.release(A.ptr); h->mem.release(A.col); h->mem.release(A.val);
+                if (!o.keep_sweeps) h->mem.release(w);
+            }
+            A = C;
+            w = sw.wc;
+            ++sweeps_done;
+        }
+        if (sweeps_done == 0 || A.n == nl) {          // no reduction: level l is the coarsest
+            h->mem.release(agg_l);
+            h->mem.release(p_l);
+            break;
+        }
+        Level& cur = h->lev[l];
+        cur.agg = agg_l;
+        cur.p = p_l;
+        cur.sweeps_done = sweeps_done;
+        for (int s = 0; s < AMG_MAX_SWEEPS; ++s) cur.rounds[s] = rounds[s];
+        cur.sweeps = std::move(recs);
+        Level next;
+        next.A = A;
+        next.w = w;
+        h->lev.push_back(std::move(next));
+    }
+
+    // ---- per-level solve data: smoother, SELL copies, member lists
+    const bool fp32 = o.precision == AMG_FP32_VCYCLE;
+    const int nlev = (int)h->lev.size();
+    for (int l = 0; l < nlev; ++l) {
+        Level& L = h->lev[l];
+        const int n = L.A.n;
+        L.minv = h->mem.alloc<double>(n);
+        if (fp32) L.minv32 = h->mem.alloc<float>(n);
+        {
+            Scope sc_(&h->prof, st, S_SMOOTHER, 12.0 * L.A.nnz + 12.0 * n);
+            k_l1_jacobi<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.minv, L.minv32);
+            KERNEL_CHECK();
+        }
+        Scope sc_(&h->prof, st, S_FORMAT, 24.0 * L.A.nnz);
+        if (l == 0 || l < nlev - 1) build_sell(h, L, S, fp32);
+        if (l == nlev - 1) break;
+        build_members(h, L, h->lev[l + 1].A.n, S);
+        if (fp32) {
+            L.p32 = h->mem.alloc<float>(n);
+            k_to_float<<<grid_for(h, n), TPB, 0, st>>>(n, L.p, L.p32);
+            KERNEL_CHECK();
+        }
+    }
+
+    // ---- coarsest level: dense Cholesky and explicit inverse
+    {
+        Level& Lc = h->lev.back();
+        const int nc = Lc.A.n;
+        if (nc > o.max_dense)
+            AMG_THROW(AMG_ERR_TOO_LARGE, "coarsest level has %d rows, above max_dense = %d", nc, o.max_dense);
+        h->nc = nc;
+        Scope sc_(&h->prof, st, S_COARSE, 0.0);
+        double* D = S.mem.alloc<double>((size_t)nc * nc);
+        double* Y = S.mem.alloc<double>((size_t)nc * nc);
+        h->coarse_L = h->mem.alloc<double>((size_t)nc * nc);
+        h->coarse_inv = h->mem.alloc<double>((size_t)nc * nc);
+        CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * nc * nc, st));
+        CUDA_CHECK(cudaMemsetAsync(h->coarse_L, 0, sizeof(double) * nc * nc, st));
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
+        k_dense_lower<<<grid_for(h, nc), TPB, 0, st>>>(nc, Lc.A.ptr, Lc.A.col, Lc.A.val, D);
+        KERNEL_CHECK();
+        k_cholesky<<<1, 1024, 0, st>>>(nc, D, h->coarse_L, S.cnt + 5);
+        KERNEL_CHECK();
+        if (read_int(S.cnt + 5, S.host, st)) AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
+        k_lower_inverse<<<(nc + 127) / 128, 128, 0, st>>>(nc, h->coarse_L, Y);
+        KERNEL_CHECK();
+        k_gram<<<(int)(((long long)nc * nc + 255) / 256), 256, 0, st>>>(nc, Y, h->coarse_inv);
+        KERNEL_CHECK();
+    }
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    h->prof.flush();
+    h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace amg

@@ -1,0 +1,613 @@
+// solve.cu -- V-cycle (Eq. 2) with l1-Jacobi smoothing and preconditioned CG.
+//
+// Every level holds its matrix in SELL-32: one warp per 32-row slice, one
+// lane per row, entries of a slice stored column-major so that each step of
+// the row loop is one fully coalesced 128-byte (float) / 256-byte (double)
+// load of values and a 128-byte load of column indices.
+//
+// V-cycle for level l < L (input b_l, zero initial guess):
+//   pre-smooth + residual (fused):  x = omega M^-1 b;  r = b - A x
+//   restriction:                    b_{l+1} = P^T r   (member lists, no atomics)
+//   coarse correction:              e = B_{l+1} b_{l+1}
+//   prolongation + post-smooth (fused): y = x + P e;  y += omega M^-1 (b - A y)
+// where the neighbours' x, resp. x + P e, are recomputed inside the row loop
+// instead of being stored and re-read. On level 0 the post-smoothing kernel
+// also forms the dot product r . z needed by CG.
+#include <chrono>
+#include <cmath>
+
+#include "amg_internal.cuh"
+#include "device_util.cuh"
+
+namespace amg {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int WARPS = TPB / 32;
+
+enum FinMode : int { FIN_NORMS = 0, FIN_PQ = 1, FIN_RR = 2, FIN_RHO_INIT = 3, FIN_RHO_UPDATE = 4, FIN_NONE = 5 };
+
+__device__ void finish(int mode, double a, double b, PcgScalars* sc) {
+    switch (mode) {
+        case FIN_NORMS: sc->rr = a; sc->bb = b; break;
+        case FIN_PQ: {
+            sc->pq = a;
+            const double alpha = sc->rho / a;
+            sc->alpha = alpha;
+            if (!(a > 0.0) || !isfinite(alpha)) sc->breakdown = 1;
+            break;
+        }
+        case FIN_RR: sc->rr = a; break;
+        case FIN_RHO_INIT: sc->rho = a; if (!isfinite(a)) sc->breakdown = 1; break;
+        case FIN_RHO_UPDATE: {
+            const double beta = a / sc->rho;
+            sc->rho_new = a;
+            sc->beta = beta;
+            sc->rho = a;
+            if (!isfinite(beta)) sc->breakdown = 1;
+            break;
+        }
+        default: break;
+    }
+}
+
+// Block partial sums, then the last block to arrive combines all partials in
+// a fixed order (deterministic for a fixed grid) and runs the finisher.
+__device__ __forceinline__ void reduce_and_finish(double a, double b, Reducer red, PcgScalars* sc, int mode) {
+    __shared__ bool last;
+    a = block_sum(a);
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        red.partial[2 * blockIdx.x] = a;
+        red.partial[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        last = atomicAdd(red.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double sa = 0.0, sb = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+        sa += __ldcg(&red.partial[2 * k]);
+        sb += __ldcg(&red.partial[2 * k + 1]);
+    }
+    sa = block_sum(sa);
+    sb = block_sum(sb);
+    if (threadIdx.x == 0) {
+        finish(mode, sa, sb, sc);
+        *red.ticket = 0u;
+    }
+}
+
+struct SellView {
+    int n, nslices;
+    const int* __restrict__ sptr;
+    const int* __restrict__ col;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// --------------------------------------------------------- V-cycle ---------
+template <typename T, typename TB>
+__global__ void __launch_bounds__(TPB) k_pre_residual(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
+                                                      T omega, const TB* __restrict__ b, T* __restrict__ x,
+                                                      T* __restrict__ r) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        T acc = 0;
+        for (int k = 0; k < w; ++k, base += 32) {
+            const int j = ld(S.col + base);
+            const T xj = (omega * ld(minv + j)) * (T)ld(b + j);
+            acc = fma(ld(val + base), xj, acc);
+        }
+        const int i = s * 32 + lane;
+        if (i < S.n) {
+            const T bi = (T)b[i];
+            x[i] = (omega * minv[i]) * bi;
+            r[i] = bi - acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_restrict(int nc, const int* __restrict__ pt_ptr, const int* __restrict__ pt_idx,
+                                                  const T* __restrict__ p, const T* __restrict__ r, T* __restrict__ bc) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        T s = 0;
+        for (int k = pt_ptr[q]; k < pt_ptr[q + 1]; ++k) {
+            const int i = pt_idx[k];
+            s = fma(ld(p + i), ld(r + i), s);
+        }
+        bc[q] = s;
+    }
+}
+
+// y = x + P e, then y += omega M^-1 (b - A y). With DOT, also r . z on level
+// 0 (r = b, z = out), finished into the CG scalars.
+template <typename T, typename TB, typename TO, bool DOT>
+__global__ void __launch_bounds__(TPB) k_post(SellView S, const T* __restrict__ val, const T* __restrict__ minv, T omega,
+                                              const int* __restrict__ agg, const T* __restrict__ p,
+                                              const T* __restrict__ e, const TB* __restrict__ b,
+                                              const T* __restrict__ x, TO* __restrict__ out, Reducer red,
+                                              PcgScalars* sc, int mode) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    double dot = 0.0;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        T acc = 0;
+        for (int k = 0; k < w; ++k, base += 32) {
+            const int j = ld(S.col + base);
+            const T yj = fma(ld(p + j), ld(e + ld(agg + j)), ld(x + j));
+            acc = fma(ld(val + base), yj, acc);
+        }
+        const int i = s * 32 + lane;
+        if (i < S.n) {
+            const T yi = fma(p[i], e[agg[i]], x[i]);
+            const T bi = (T)b[i];
+            const T o = fma(omega * minv[i], bi - acc, yi);
+            out[i] = (TO)o;
+            if (DOT) dot = fma((double)b[i], (double)(TO)o, dot);
+        }
+    }
+    if (DOT) reduce_and_finish(dot, 0.0, red, sc, mode);
+}
+
+// Extra pre-smoothing sweep from (x, r = b - A x):
+//   x' = x + omega M^-1 r,  r' = b - A x'  (x' of neighbours recomputed).
+template <typename T, typename TB>
+__global__ void __launch_bounds__(TPB) k_pre_step(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
+                                                  T omega, const TB* __restrict__ b, const T* __restrict__ xin,
+                                                  const T* __restrict__ rin, T* __restrict__ xout,
+                                                  T* __restrict__ rout) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        T acc = 0;
+        for (int k = 0; k < w; ++k, base += 32) {
+            const int j = ld(S.col + base);
+            const T xj = fma(omega * ld(minv + j), ld(rin + j), ld(xin + j));
+            acc = fma(ld(val + base), xj, acc);
+        }
+        const int i = s * 32 + lane;
+        if (i < S.n) {
+            xout[i] = fma(omega * minv[i], rin[i], xin[i]);
+            rout[i] = (T)b[i] - acc;
+        }
+    }
+}
+
+// Extra post-smoothing sweep: y' = y + omega M^-1 (b - A y).
+template <typename T, typename TB, typename TO>
+__global__ void __launch_bounds__(TPB) k_smooth(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
+                                                T omega, const TB* __restrict__ b, const T* __restrict__ yin,
+                                                TO* __restrict__ yout) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        T acc = 0;
+        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(yin + ld(S.col + base)), acc);
+        const int i = s * 32 + lane;
+        if (i < S.n) yout[i] = (TO)fma(omega * minv[i], (T)b[i] - acc, yin[i]);
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                             Reducer red, PcgScalars* sc, int mode) {
+    double d = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d = fma(a[i], b[i], d);
+    reduce_and_finish(d, 0.0, red, sc, mode);
+}
+
+// x = A_L^{-1} b on the coarsest level, in FP64 whatever T is.
+template <typename T, typename TO>
+__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b, TO* __restrict__ x) {
+    extern __shared__ double bs[];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) bs[j] = (double)b[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n; i += gridDim.x * warps) {
+        double s = 0.0;
+        const double* row = Ainv + (size_t)i * n;
+        for (int j = lane; j < n; j += 32) s = fma(row[j], bs[j], s);
+        s = warp_sum(s);
+        if (lane == 0) x[i] = (TO)s;
+    }
+}
+
+// ------------------------------------------------------------- PCG ---------
+// r = b - A x; ||r||^2 and ||b||^2.
+__global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __restrict__ val,
+                                                  const double* __restrict__ x, const double* __restrict__ b,
+                                                  double* __restrict__ r, Reducer red, PcgScalars* sc) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    double rr = 0.0, bb = 0.0;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        double acc = 0.0;
+        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(x + ld(S.col + base)), acc);
+        const int i = s * 32 + lane;
+        if (i < S.n) {
+            const double bi = b[i];
+            const double ri = bi - acc;
+            r[i] = ri;
+            rr = fma(ri, ri, rr);
+            bb = fma(bi, bi, bb);
+        }
+    }
+    reduce_and_finish(rr, bb, red, sc, FIN_NORMS);
+}
+
+// q = A p; p . q; alpha = rho / p.q.
+__global__ void __launch_bounds__(TPB) k_spmv_dot(SellView S, const double* __restrict__ val,
+                                                  const double* __restrict__ p, double* __restrict__ q, Reducer red,
+                                                  PcgScalars* sc) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * WARPS;
+    double pq = 0.0;
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
+        const int w = S.sptr[s + 1] - S.sptr[s];
+        long long base = (long long)S.sptr[s] * 32 + lane;
+        double acc = 0.0;
+        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(p + ld(S.col + base)), acc);
+        const int i = s * 32 + lane;
+        if (i < S.n) {
+            q[i] = acc;
+            pq = fma(p[i], acc, pq);
+        }
+    }
+    reduce_and_finish(pq, 0.0, red, sc, FIN_PQ);
+}
+
+// x += alpha p; r -= alpha q; ||r||^2.
+__global__ void __launch_bounds__(TPB) k_update_xr(int n, const double* __restrict__ p, const double* __restrict__ q,
+                                                   double* __restrict__ x, double* __restrict__ r, Reducer red,
+                                                   PcgScalars* sc) {
+    const double alpha = sc->alpha;
+    double rr = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+    }
+    reduce_and_finish(rr, 0.0, red, sc, FIN_RR);
+}
+
+// p = z + beta p.
+__global__ void __launch_bounds__(TPB) k_update_p(int n, const double* __restrict__ z, double* __restrict__ p,
+                                                  const PcgScalars* sc) {
+    const double beta = sc->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = fma(beta, p[i], z[i]);
+}
+
+// ------------------------------------------------------------ host ---------
+// Algorithmic bytes of one launch: every array the kernel must touch, read
+// or written once (index 4 B, value V B, the level-0 input/output in FP64);
+// matrix entries counted without SELL padding.
+double by_pre(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 3.0 * V); }
+double by_pre_step(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 5.0 * V); }
+double by_restrict(int n, int nc, int V) { return (double)n * (4 + 2.0 * V) + (double)nc * (4 + V); }
+double by_post(const Level& L, int nc, int V, int Vb, int Vo) {
+    return (double)L.A.nnz * (V + 4) + (double)L.A.n * (3.0 * V + 4 + Vb + Vo) + (double)nc * V;
+}
+double by_smooth(const Level& L, int V, int Vb, int Vo) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (2.0 * V + Vb + Vo); }
+double by_coarse(int nc, int Vi, int Vo) { return 8.0 * nc * nc + (double)nc * (Vi + Vo); }
+
+SellView view(const Level& L) { return SellView{L.S.n, L.S.nslices, L.S.sptr, L.S.col}; }
+
+int sell_grid(const amg_hierarchy* h, int nslices) {
+    int g = (nslices + WARPS - 1) / WARPS;
+    int cap = h->num_sms * 8;
+    return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+int vec_grid(const amg_hierarchy* h, long long n) { return blocks_for(n, TPB, h->num_sms * 8); }
+
+// Fixed grid of every reducing kernel (deterministic partial order).
+int red_grid(const amg_hierarchy* h) { return h->red.blocks; }
+
+void coarse_solve_launch(amg_hierarchy* h, const void* b, void* x, bool fp32_in, bool fp64_out) {
+    const int n = h->nc;
+    const int threads = 256;
+    int grid = (n + (threads / 32) - 1) / (threads / 32);
+    if (grid > h->num_sms * 2) grid = h->num_sms * 2;
+    const size_t sh = sizeof(double) * (size_t)n;
+    Scope sc_(&h->prof, h->stream, K_COARSE, by_coarse(n, fp32_in ? 4 : 8, fp64_out ? 8 : 4));
+    if (!fp32_in)
+        k_coarse_solve<double, double><<<grid, threads, sh, h->stream>>>(n, h->coarse_inv, (const double*)b, (double*)x);
+    else if (fp64_out)
+        k_coarse_solve<float, double><<<grid, threads, sh, h->stream>>>(n, h->coarse_inv, (const float*)b, (double*)x);
+    else
+        k_coarse_solve<float, float><<<grid, threads, sh, h->stream>>>(n, h->coarse_inv, (const float*)b, (float*)x);
+    KERNEL_CHECK();
+}
+
+// z = B r on level 0. With rz_mode != FIN_NONE, also finishes r . z.
+template <typename T>
+void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
+    cudaStream_t st = h->stream;
+    const int L = (int)h->lev.size() - 1;
+    const bool f32 = sizeof(T) == 4;
+    const T omega = (T)h->opt.omega;
+    const int n0 = h->lev[0].A.n;
+    if (L == 0) {
+        coarse_solve_launch(h, r, z, false, true);
+        if (rz_mode != FIN_NONE) {
+            Scope sc_(&h->prof, st, K_DOT, 16.0 * n0);
+            k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, h->red, h->sc, rz_mode);
+            KERNEL_CHECK();
+        }
+        return;
+    }
+    auto val = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.S.val32 : (const T*)Lv.S.val; };
+    auto minv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv; };
+    auto pv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.p32 : (const T*)Lv.p; };
+    auto vec = [&](Level& Lv, int which) -> T* {
+        if (f32) {
+            float* v[6] = {Lv.b32, Lv.x32, Lv.r32, Lv.y32, Lv.t32, Lv.u32};
+            return (T*)v[which];
+        }
+        double* v[6] = {Lv.b, Lv.x, Lv.r, Lv.y, Lv.t, Lv.u};
+        return (T*)v[which];
+    };
+    enum { VB = 0, VX = 1, VR = 2, VY = 3, VT = 4, VU = 5 };
+    const int V = sizeof(T);
+    const int pre = h->opt.pre < 1 ? 1 : h->opt.pre;
+    const int post = h->opt.post < 1 ? 1 : h->opt.post;
+    std::vector<T*> xcur(L + 1), out(L + 1), spare(L + 1);
+
+    // downward: level 0 reads the FP64 r directly
+    for (int l = 0; l < L; ++l) {
+        Level& Lv = h->lev[l];
+        const SellView S = view(Lv);
+        const int g = sell_grid(h, S.nslices);
+        T *xa = vec(Lv, VX), *ra = vec(Lv, VR), *xb = vec(Lv, VT), *rb = vec(Lv, VU);
+        const int Vb = l == 0 ? 8 : V;
+        {
+            Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, Vb));
+            if (l == 0) k_pre_residual<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra);
+            else k_pre_residual<T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra);
+            KERNEL_CHECK();
+        }
+        for (int k = 1; k < pre; ++k) {
+            Scope sc_(&h->prof, st, K_PRE_STEP, by_pre_step(Lv, V, Vb));
+            if (l == 0) k_pre_step<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra, xb, rb);
+            else k_pre_step<T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra, xb, rb);
+            KERNEL_CHECK();
+            std::swap(xa, xb);
+            std::swap(ra, rb);
+        }
+        xcur[l] = xa;
+        spare[l] = (xa == vec(Lv, VX)) ? vec(Lv, VT) : vec(Lv, VX);
+        const int nc = h->lev[l + 1].A.n;
+        Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(Lv.A.n, nc, V));
+        k_restrict<T><<<vec_grid(h, nc), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, pv(Lv), ra, vec(h->lev[l + 1], VB));
+        KERNEL_CHECK();
+    }
+    // coarsest: FP64 dense solve
+    out[L] = vec(h->lev[L], VX);
+    coarse_solve_launch(h, vec(h->lev[L], VB), out[L], f32, !f32);
+    // upward
+    for (int l = L - 1; l >= 0; --l) {
+        Level& Lv = h->lev[l];
+        const SellView S = view(Lv);
+        const int g = sell_grid(h, S.nslices);
+        const T* e = out[l + 1];
+        const int nc = h->lev[l + 1].A.n;
+        if (l > 0) {
+            T *ya = vec(Lv, VY), *yb = spare[l];
+            {
+                Scope sc_(&h->prof, st, K_POST, by_post(Lv, nc, V, V, V));
+                k_post<T, T, T, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, vec(Lv, VB),
+                                                          xcur[l], ya, h->red, h->sc, FIN_NONE);
+                KERNEL_CHECK();
+            }
+            for (int k = 1; k < post; ++k) {
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
+                k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), ya, yb);
+                KERNEL_CHECK();
+                std::swap(ya, yb);
+            }
+            out[l] = ya;
+            continue;
+        }
+        if (post == 1) {
+            Scope sc_(&h->prof, st, K_POST_L0, by_post(Lv, nc, V, 8, 8));
+            if (rz_mode != FIN_NONE)
+                k_post<T, double, double, true><<<red_grid(h), TPB, 0, st>>>(
+                    S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r, xcur[0], z, h->red, h->sc, rz_mode);
+            else
+                k_post<T, double, double, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r,
+                                                                   xcur[0], z, h->red, h->sc, FIN_NONE);
+            KERNEL_CHECK();
+        } else {
+            T *ya = vec(Lv, VY), *yb = spare[0];
+            {
+                Scope sc_(&h->prof, st, K_POST_L0, by_post(Lv, nc, V, 8, V));
+                k_post<T, double, T, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r,
+                                                              xcur[0], ya, h->red, h->sc, FIN_NONE);
+                KERNEL_CHECK();
+            }
+            for (int k = 1; k < post - 1; ++k) {
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, V));
+                k_smooth<T, double, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, ya, yb);
+                KERNEL_CHECK();
+                std::swap(ya, yb);
+            }
+            {
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, 8));
+                k_smooth<T, double, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, ya, z);
+                KERNEL_CHECK();
+            }
+            if (rz_mode != FIN_NONE) {
+                Scope sc_(&h->prof, st, K_DOT, 16.0 * n0);
+                k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, h->red, h->sc, rz_mode);
+                KERNEL_CHECK();
+            }
+        }
+    }
+}
+
+void vcycle_dispatch(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
+    if (h->opt.precision == AMG_FP32_VCYCLE) vcycle_typed<float>(h, r, z, rz_mode);
+    else vcycle_typed<double>(h, r, z, rz_mode);
+}
+
+void read_scalars(amg_hierarchy* h) {
+    CUDA_CHECK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+}
+
+}  // namespace
+
+void prepare_solve(amg_hierarchy* h) {
+    const bool f32 = h->opt.precision == AMG_FP32_VCYCLE;
+    const bool extra = h->opt.pre > 1 || h->opt.post > 1;
+    for (auto& L : h->lev) {
+        const int n = L.A.n;
+        if (f32) {
+            L.b32 = h->mem.alloc<float>(n);
+            L.x32 = h->mem.alloc<float>(n);
+            L.r32 = h->mem.alloc<float>(n);
+            L.y32 = h->mem.alloc<float>(n);
+            if (extra) { L.t32 = h->mem.alloc<float>(n); L.u32 = h->mem.alloc<float>(n); }
+        } else {
+            L.b = h->mem.alloc<double>(n);
+            L.x = h->mem.alloc<double>(n);
+            L.r = h->mem.alloc<double>(n);
+            L.y = h->mem.alloc<double>(n);
+            if (extra) { L.t = h->mem.alloc<double>(n); L.u = h->mem.alloc<double>(n); }
+        }
+    }
+    const int n0 = h->lev[0].A.n;
+    h->r = h->mem.alloc<double>(n0);
+    h->z = h->mem.alloc<double>(n0);
+    h->p = h->mem.alloc<double>(n0);
+    h->q = h->mem.alloc<double>(n0);
+    h->t = h->mem.alloc<double>(n0);
+    h->sc = h->mem.alloc<PcgScalars>(1);
+    CUDA_CHECK(cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->stream));
+    if (!h->sc_host) CUDA_CHECK(cudaHostAlloc(&h->sc_host, sizeof(PcgScalars), cudaHostAllocDefault));
+    h->red.blocks = h->num_sms * 4;
+    h->red.partial = h->mem.alloc<double>(2 * (size_t)h->red.blocks);
+    h->red.ticket = h->mem.alloc<unsigned>(1);
+    CUDA_CHECK(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+}
+
+void vcycle_apply(amg_hierarchy* h, const double* r, double* z) {
+    vcycle_dispatch(h, r, z, FIN_NONE);
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    h->prof.flush();
+}
+
+amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->stream;
+    Level& L0 = h->lev[0];
+    const int n = L0.A.n;
+    const SellView S = view(L0);
+    const double* A = L0.S.val;
+    PcgScalars* hs = h->sc_host;
+
+    const double nnz = (double)L0.A.nnz;
+    const double by_res = 12.0 * nnz + 24.0 * n, by_spmv = 12.0 * nnz + 16.0 * n;
+    CUDA_CHECK(cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), st));
+    {
+        Scope sc_(&h->prof, st, K_RESIDUAL, by_res);
+        k_residual<<<red_grid(h), TPB, 0, st>>>(S, A, x, b, h->r, h->red, h->sc);
+        KERNEL_CHECK();
+    }
+    read_scalars(h);
+    const double nb = std::sqrt(hs->bb);
+    amg_solve_info inf{};
+    amg_status status = AMG_NOT_CONVERGED;
+    if (nb == 0.0) {
+        CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+        CUDA_CHECK(cudaStreamSynchronize(st));
+        inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (info) *info = inf;
+        return AMG_OK;
+    }
+    double rel = std::sqrt(hs->rr) / nb;
+    double true_rel = rel;
+    bool have_true = true;          // r currently equals b - A x exactly
+    int it = 0;
+    bool restart = true;
+    if (rel <= rtol) status = AMG_OK;
+    while (status != AMG_OK && it < maxit) {
+        if (restart) {
+            vcycle_dispatch(h, h->r, h->z, FIN_RHO_INIT);
+            CUDA_CHECK(cudaMemcpyAsync(h->p, h->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            restart = false;
+        }
+        {
+            Scope sc_(&h->prof, st, K_SPMV_DOT, by_spmv);
+            k_spmv_dot<<<red_grid(h), TPB, 0, st>>>(S, A, h->p, h->q, h->red, h->sc);
+            KERNEL_CHECK();
+        }
+        {
+            Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n);
+            k_update_xr<<<red_grid(h), TPB, 0, st>>>(n, h->p, h->q, x, h->r, h->red, h->sc);
+            KERNEL_CHECK();
+        }
+        ++it;
+        read_scalars(h);
+        if (hs->breakdown) { status = AMG_ERR_BREAKDOWN; break; }
+        rel = std::sqrt(hs->rr) / nb;
+        have_true = false;
+        if (rel <= rtol) {
+            {
+                Scope sc_(&h->prof, st, K_RESIDUAL, by_res);
+                k_residual<<<red_grid(h), TPB, 0, st>>>(S, A, x, b, h->t, h->red, h->sc);
+                KERNEL_CHECK();
+            }
+            read_scalars(h);
+            true_rel = std::sqrt(hs->rr) / nb;
+            have_true = true;
+            if (true_rel <= rtol) { status = AMG_OK; break; }
+            CUDA_CHECK(cudaMemcpyAsync(h->r, h->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            rel = true_rel;
+            restart = true;
+            ++inf.restarts;
+            continue;
+        }
+        vcycle_dispatch(h, h->r, h->z, FIN_RHO_UPDATE);
+        Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
+        k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
+        KERNEL_CHECK();
+    }
+    if (!have_true) {
+        {
+            Scope sc_(&h->prof, st, K_RESIDUAL, by_res);
+            k_residual<<<red_grid(h), TPB, 0, st>>>(S, A, x, b, h->t, h->red, h->sc);
+            KERNEL_CHECK();
+        }
+        read_scalars(h);
+        true_rel = std::sqrt(hs->rr) / nb;
+    }
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    h->prof.flush();
+    inf.iterations = it;
+    inf.relres = rel;
+    inf.true_relres = true_rel;
+    inf.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return status;
+}
+
+}  // namespace amg

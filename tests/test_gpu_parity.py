@@ -1,0 +1,211 @@
+"""CUDA path vs the CPU oracle through the C ABI, on the same seeded inputs.
+
+Bars: matchings, aggregates and prolongators bit-exact at every sweep and
+level; hierarchy operators (Galerkin matrices, l1-Jacobi diagonals, smooth
+vectors, Cholesky factor) bit-exact as well (the canonical operation order is
+part of their definition, so no tolerance is needed); V-cycle output within
+1e-12 relative; FP64 PCG solutions within 1e-10 relative and iteration counts
+within +-1.
+"""
+import numpy as np
+import pytest
+
+from paper_2006_16147_gb300 import workloads as W
+
+from gpu_util import setup, solve, vcycle
+
+pytestmark = pytest.mark.gpu
+
+
+def _w(A, seed):
+    if seed is None:
+        return np.ones(A.n)
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.3, 2.0, A.n) * rng.choice([-1.0, 1.0], A.n)
+
+
+# sizes that span several SELL slices / CTAs and leave ragged tails
+CASES = {
+    "poisson32": (lambda: W.poisson3d(32), None),
+    "poisson_ragged": (lambda: W.poisson3d(33, 17, 9), None),
+    "poisson_odd": (lambda: W.poisson3d(31, 29, 27), None),
+    "aniso": (lambda: W.poisson2d_aniso(96, 80, 1e-2), None),
+    "varcoef": (lambda: W.varcoef3d(24, seed=2), None),
+    "spd_random_w": (lambda: W.random_spd(700, 0.01, 7), 7),
+    "spd_dense_rows": (lambda: W.random_spd(300, 0.08, 8), 8),
+}
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_setup_bit_exact(orc, name):
+    from paper_2006_16147_gb300 import amg
+    mk, seed = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=40)
+    h = setup(A, w, keep_sweeps=1, max_coarse=40)
+    info = amg.amg_hierarchy_info(h)
+    assert info["n"] == [s[0] for s in H.sizes()]
+    assert info["nnz"] == [s[1] for s in H.sizes()]
+    for l in range(H.num_levels):
+        ol = H.level(l)
+        gl = amg.amg_export_level(h, l)
+        for k in ("row_ptr", "col", "val", "w", "minv"):
+            assert np.array_equal(getattr(ol, k), gl[k]), (l, k)
+        if l < H.num_levels - 1:
+            assert np.array_equal(ol.agg, gl["agg"]) and np.array_equal(ol.p, gl["p"]), l
+            assert info["sweeps_done"][l] == len(ol.sweeps)
+            for s, osw in enumerate(ol.sweeps):
+                gs = amg.amg_export_sweep(h, l, s)
+                assert gs["nc"] == osw["nc"] and gs["nnz_c"] == osw["nnz_c"]
+                for k in ("mate", "agg", "p", "wc"):
+                    assert np.array_equal(osw[k], gs[k]), (l, s, k)
+    assert np.array_equal(H.coarse_factor(), amg.amg_coarse_factor(h))
+    h.close()
+
+
+def test_matching_rounds_equal_ld_rounds(orc):
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(20, 16, 12)
+    H = orc.Hierarchy(A, use_ld=True, max_coarse=40)
+    h = setup(A, max_coarse=40)
+    info = amg.amg_hierarchy_info(h)
+    for l in range(H.num_levels - 1):
+        assert info["rounds"][l] == [s["rounds"] for s in H.level(l).sweeps]
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_vcycle_parity(orc, name):
+    mk, seed = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=40)
+    h = setup(A, w, max_coarse=40)
+    r = np.random.default_rng(3).normal(size=A.n)
+    zo = H.vcycle(r)
+    zg = vcycle(h, r)
+    assert np.linalg.norm(zg - zo) <= 1e-12 * np.linalg.norm(zo)
+    h.close()
+
+
+@pytest.mark.parametrize("pre,post", [(2, 2), (3, 1), (1, 4)])
+def test_vcycle_parity_more_sweeps(orc, pre, post):
+    A = W.poisson3d(30, 20, 10)
+    H = orc.Hierarchy(A, max_coarse=40, pre=pre, post=post)
+    h = setup(A, max_coarse=40, pre=pre, post=post)
+    r = np.random.default_rng(4).normal(size=A.n)
+    zo = H.vcycle(r)
+    zg = vcycle(h, r)
+    assert np.linalg.norm(zg - zo) <= 1e-12 * np.linalg.norm(zo)
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pcg_parity(orc, name):
+    mk, seed = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    b, _ = W.rhs_uniform(A, 1)
+    H = orc.Hierarchy(A, w)
+    h = setup(A, w)
+    xo, io = H.pcg(b, rtol=1e-6, maxit=500)
+    xg, ig = solve(h, b, rtol=1e-6, maxit=500)
+    assert ig["status"] == 0 and io["status"] == 0
+    assert abs(ig["iterations"] - io["iterations"]) <= 1
+    assert ig["true_relres"] <= 1e-6
+    if ig["iterations"] == io["iterations"]:
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    # independent residual check in numpy
+    assert np.linalg.norm(b - A.scipy() @ xg) <= 1e-6 * np.linalg.norm(b)
+    h.close()
+
+
+def test_config1_32cubed(orc):
+    # 32^3 Poisson, b = A*1, x0 = 0, w = 1, 3 sweeps, l1-Jacobi 1+1, coarse 64 dense, rel-res 1e-6
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(32)
+    b, xs = W.rhs_ones(A)
+    H = orc.Hierarchy(A)
+    h = setup(A)
+    assert amg.amg_hierarchy_info(h)["n"] == [32768, 4096, 512, 64]
+    xo, io = H.pcg(b, rtol=1e-6)
+    xg, ig = solve(h, b, rtol=1e-6)
+    assert abs(ig["iterations"] - io["iterations"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    h.close()
+
+
+def test_zero_rhs_and_single_level(orc):
+    A = W.poisson3d(8)
+    h = setup(A, max_coarse=600)           # n = 512 <= max_coarse: B = A^{-1}
+    b = np.random.default_rng(0).normal(size=A.n)
+    x, info = solve(h, b, rtol=1e-12)
+    assert info["iterations"] == 1 and info["true_relres"] <= 1e-12
+    x, info = solve(h, np.zeros(A.n), x0=np.ones(A.n))
+    assert info["iterations"] == 0 and not x.any()
+    h.close()
+
+
+def test_no_edges_diagonal_matrix(orc):
+    # no off-diagonal entries: nothing to match, the fine level is the coarsest
+    n = 300
+    A = W.Csr(np.arange(n + 1), np.arange(n), np.linspace(1.0, 3.0, n))
+    h = setup(A, max_coarse=10)
+    from paper_2006_16147_gb300 import amg
+    assert amg.amg_hierarchy_info(h)["n"] == [n]
+    b = np.ones(n)
+    x, info = solve(h, b, rtol=1e-10)
+    assert np.allclose(x, 1.0 / np.linspace(1.0, 3.0, n), rtol=1e-12)
+    h.close()
+
+
+def test_errors_are_reported(orc):
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(6)
+    bad = A.val.copy()
+    bad[0] = -1.0                                   # negative diagonal
+    with pytest.raises(amg.AmgError) as e:
+        setup(W.Csr(A.row_ptr, A.col, bad))
+    assert e.value.status == -2
+    with pytest.raises(amg.AmgError) as e:
+        setup(A, np.zeros(A.n))                     # w = 0
+    assert e.value.status == -3
+    col = A.col.copy()
+    col[1], col[2] = col[2], col[1]                 # unsorted row
+    with pytest.raises(amg.AmgError) as e:
+        setup(W.Csr(A.row_ptr, col, A.val))
+    assert e.value.status == -1
+    # unsymmetric pattern: drop one off-diagonal entry
+    keep = np.ones(A.nnz, bool)
+    keep[1] = False
+    rp = A.row_ptr.copy()
+    rp[1:] -= 1
+    with pytest.raises(amg.AmgError) as e:
+        setup(W.Csr(rp, A.col[keep], A.val[keep]))
+    assert e.value.status == -1
+    h = setup(A)
+    x, info = solve(h, np.ones(A.n))
+    assert info["status"] == 0
+    h.close()
+
+
+def test_host_entry_points(orc):
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(16)
+    b, _ = W.rhs_uniform(A, 2)
+    h = amg.amg_setup_host(A.row_ptr, A.col, A.val, np.ones(A.n))
+    x = np.zeros(A.n)
+    info = amg.amg_solve_host(h, b, x, rtol=1e-8)
+    H = orc.Hierarchy(A)
+    xo, io = H.pcg(b, rtol=1e-8)
+    assert abs(info["iterations"] - io["iterations"]) <= 1
+    assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+    h.close()
