@@ -174,6 +174,36 @@ amg_status amg_kernel_stats_reset(amg_hierarchy* h);
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t amg_launch_count(void);
 
+/*
+ * Matching without allocation. The paper has no counterpart: this is a
+ * service for callers that may not allocate device memory when they need a
+ * matching -- code that runs while a stream is being captured into a CUDA
+ * graph, applications that hand out all device memory from their own pool or
+ * budget, and hosts that forbid allocation after start-up.
+ *
+ * Computes the Eq. 3 weights of (A, w) and the locally-dominant matching with
+ * the index tiebreak, exactly as the first sweep of amg_setup does, and
+ * writes mate[i] (partner index, or -1 for an unmatched row) to the caller's
+ * DEVICE array of length n. A and w are device arrays as for amg_setup;
+ * `stream` is a cudaStream_t (NULL = legacy default stream); *rounds (host,
+ * may be NULL) receives the number of matching rounds. The call returns after
+ * the stream work has finished.
+ *
+ * The only working memory is a fixed array inside the library image
+ * (about 5.5 MB of device memory on every GPU that loads the library, held
+ * until the process exits). Limits: n <= AMG_NOALLOC_MAX_N and
+ * nnz <= AMG_NOALLOC_MAX_NNZ; larger inputs return AMG_ERR_TOO_LARGE before
+ * any device work. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture begins. All calls share the one array: calls that overlap on the
+ * GPU (other threads, other streams) race and must be serialised by the
+ * caller. No cudaMalloc, cudaFree or other allocating routine is called.
+ * Errors as amg_setup (validation codes), AMG_ERR_TIMEOUT, AMG_ERR_CUDA.
+ */
+#define AMG_NOALLOC_MAX_N 65536
+#define AMG_NOALLOC_MAX_NNZ 524288
+amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds);
+
 /* Releases every device allocation of h. NULL is accepted. */
 void amg_free(amg_hierarchy* h);
 

@@ -33,8 +33,10 @@ EXPORTED = [
     "amg_options_default", "amg_setup", "amg_setup_host", "amg_solve", "amg_solve_host", "amg_vcycle",
     "amg_hierarchy_info", "amg_export_level", "amg_sweep_dims", "amg_export_sweep", "amg_coarse_factor",
     "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
-    "amg_launch_count",
+    "amg_launch_count", "amg_match_noalloc",
 ]
+NOALLOC_MAX_N = 65536
+NOALLOC_MAX_NNZ = 524288
 
 
 class amg_csr(ctypes.Structure):
@@ -115,6 +117,8 @@ def lib() -> ctypes.CDLL:
         L.amg_kernel_stats.restype = ctypes.c_int
         L.amg_kernel_stats_reset.argtypes = [_vp]
         L.amg_kernel_stats_reset.restype = ctypes.c_int
+        L.amg_match_noalloc.argtypes = [ctypes.POINTER(amg_csr), _vp, _vp, _vp, _i32p]
+        L.amg_match_noalloc.restype = ctypes.c_int
         L.amg_launch_count.argtypes = []
         L.amg_launch_count.restype = ctypes.c_int64
         _lib = L
@@ -281,3 +285,19 @@ def amg_kernel_stats_reset(h: Hierarchy) -> None:
 
 def amg_launch_count() -> int:
     return int(lib().amg_launch_count())
+
+
+def amg_match_noalloc(row_ptr, col, val, w, mate, stream=None) -> int:
+    """Matching of (A, w) into the device tensor `mate` without any device allocation.
+
+    For callers that may not allocate when they need it (during stream capture,
+    under an external memory pool or budget). Uses the library's fixed scratch
+    array, so n <= NOALLOC_MAX_N and nnz <= NOALLOC_MAX_NNZ; calls must not
+    overlap on the GPU. Returns the number of matching rounds.
+    """
+    n = int(row_ptr.shape[0] - 1)
+    A = amg_csr(n, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    rounds = ctypes.c_int32(0)
+    st = _current_stream() if stream is None else stream
+    _check(lib().amg_match_noalloc(ctypes.byref(A), _ptr(w), _ptr(mate), ctypes.c_void_p(st), ctypes.byref(rounds)))
+    return rounds.value

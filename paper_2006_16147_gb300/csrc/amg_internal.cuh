@@ -192,5 +192,6 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* A, const double* w);
 void prepare_solve(amg_hierarchy* h);
 amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info);
 void vcycle_apply(amg_hierarchy* h, const double* r, double* z);
+amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds_out);
 
 }  // namespace amg

@@ -288,4 +288,11 @@ amg_status amg_kernel_stats_reset(amg_hierarchy* h) {
 
 int64_t amg_launch_count(void) { return amg::launch_counter().load(); }
 
+amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds) {
+    if (!mate) return fail(AMG_ERR_ARG, "mate is null");
+    amg_status s = check_csr(A, w);
+    if (s != AMG_OK) return s;
+    return guarded([&]() -> amg_status { return amg::match_noalloc(A, w, mate, stream, rounds); });
+}
+
 }  // extern "C"

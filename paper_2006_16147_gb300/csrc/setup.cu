@@ -787,4 +787,125 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+
+// ---------------------------------------------------------------------------
+// Matching without any allocation (amg_match_noalloc).
+//
+// Some callers cannot call cudaMalloc at the point where they need a matching:
+// code running while a stream is being captured into a CUDA graph, callers
+// that own all device memory through their own pool or budget, and hosts that
+// forbid allocation after start-up. For them this entry point computes the
+// Eq. 3 weights and the locally-dominant matching of one matrix using only a
+// fixed scratch area that is part of the library image (a file-scope
+// __device__ array, resident on every GPU that loads the library until the
+// process exits). The caller passes A, w and the output array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NA_ALIGN = 256;
+constexpr size_t na_round(size_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN * NA_ALIGN; }
+constexpr size_t NA_DIAG = 0;
+constexpr size_t NA_C = NA_DIAG + na_round(sizeof(double) * AMG_NOALLOC_MAX_N);
+constexpr size_t NA_CAND = NA_C + na_round(sizeof(double) * (size_t)AMG_NOALLOC_MAX_NNZ);
+constexpr size_t NA_L0 = NA_CAND + na_round(sizeof(int) * AMG_NOALLOC_MAX_N);
+constexpr size_t NA_L1 = NA_L0 + na_round(sizeof(int) * AMG_NOALLOC_MAX_N);
+constexpr size_t NA_M = NA_L1 + na_round(sizeof(int) * AMG_NOALLOC_MAX_N);
+constexpr size_t NA_CNT = NA_M + na_round(sizeof(int) * AMG_NOALLOC_MAX_N);
+constexpr size_t NA_BYTES = NA_CNT + na_round(sizeof(int) * 16);
+
+static __device__ __align__(256) unsigned char g_match_scratch[NA_BYTES];
+
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[256] = {};   // device address of g_match_scratch, per device ordinal
+
+// Device address of the scratch array for the current device. Looked up once
+// per device with that device current (the host-side symbol is only a
+// stand-in and must never be handed to a kernel).
+unsigned char* noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> g(g_na_mu);
+    if (dev < 0 || dev >= 256) AMG_THROW(AMG_ERR_ARG, "device ordinal %d out of range", dev);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        CUDA_CHECK(cudaGetSymbolAddress(&p, g_match_scratch));
+        g_na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    return g_na_ptr[dev];
+}
+
+__global__ void k_mate_normalize(int n, int* mate) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (mate[i] < 0) mate[i] = -1;
+}
+
+int noalloc_read_int(const int* dev, cudaStream_t st) {
+    int v = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&v, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return v;
+}
+
+}  // namespace
+
+amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds_out) {
+    const int n = A->n, nnz = A->nnz;
+    if (n > AMG_NOALLOC_MAX_N || nnz > AMG_NOALLOC_MAX_NNZ)
+        AMG_THROW(AMG_ERR_TOO_LARGE, "amg_match_noalloc: n = %d, nnz = %d exceed the fixed scratch limits (%d, %d)", n,
+                  nnz, AMG_NOALLOC_MAX_N, AMG_NOALLOC_MAX_NNZ);
+    int dev = 0, sms = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned char* base = noalloc_scratch(dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* diag = reinterpret_cast<double*>(base + NA_DIAG);
+    double* c = reinterpret_cast<double*>(base + NA_C);
+    int* cand = reinterpret_cast<int*>(base + NA_CAND);
+    int* lists[2] = {reinterpret_cast<int*>(base + NA_L0), reinterpret_cast<int*>(base + NA_L1)};
+    int* mlist = reinterpret_cast<int*>(base + NA_M);
+    int* cnt = reinterpret_cast<int*>(base + NA_CNT);   // [0,1] lists, [2,3] matches, [4] rounds, [5] flags
+    const int grid = blocks_for(n, TPB, sms * 16);
+    const int* ptr = A->row_ptr;
+    const int* col = A->col;
+    const double* val = A->val;
+
+    // every counter starts at zero on every call (the array keeps the last call's contents)
+    CUDA_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, st));
+    k_check_ptr<<<blocks_for(n + 1, TPB, sms * 16), TPB, 0, st>>>(n, nnz, ptr, cnt + 5);
+    KERNEL_CHECK();
+    int f = noalloc_read_int(cnt + 5, st);
+    if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "row_ptr is not a valid CSR row pointer");
+    k_check_rows<<<grid, TPB, 0, st>>>(n, ptr, col, val, w, diag, cnt + 5);
+    KERNEL_CHECK();
+    f = noalloc_read_int(cnt + 5, st);
+    if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "CSR columns unsorted, out of range, or pattern not symmetric");
+    if (f & F_NOT_SPD) AMG_THROW(AMG_ERR_NOT_SPD, "non-finite value or diagonal entry missing or <= 0");
+    if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "smooth vector w has a zero or non-finite entry");
+
+    k_weights<<<grid, TPB, 0, st>>>(n, ptr, col, val, diag, w, c);
+    KERNEL_CHECK();
+    CUDA_CHECK(cudaMemsetAsync(mate, 0xff, sizeof(int) * n, st));
+    k_ld_init<<<grid, TPB, 0, st>>>(n, ptr, col, c, cand, mate);
+    KERNEL_CHECK();
+    const int rgrid = sms * 8;
+    const long long max_rounds = (long long)n + 4;
+    long long r = 0;
+    for (;;) {
+        for (int b = 0; b < 16; ++b, ++r) {
+            const int cur = (int)(r & 1), nxt = (int)((r + 1) & 1);
+            k_ld_match<<<rgrid, TPB, 0, st>>>(n, r == 0 ? nullptr : lists[cur], &cnt[cur], cand, mate, mlist,
+                                              &cnt[2 + cur], &cnt[nxt], cnt + 4);
+            KERNEL_CHECK();
+            k_ld_update<<<rgrid, TPB, 0, st>>>(n, ptr, col, c, cand, mate, mlist, &cnt[2 + cur], lists[nxt], &cnt[nxt],
+                                               &cnt[2 + nxt]);
+            KERNEL_CHECK();
+        }
+        if (noalloc_read_int(&cnt[r & 1], st) == 0) break;
+        if (r > max_rounds) AMG_THROW(AMG_ERR_TIMEOUT, "matching did not settle after %lld rounds", r);
+    }
+    k_mate_normalize<<<grid, TPB, 0, st>>>(n, mate);
+    KERNEL_CHECK();
+    const int rounds = noalloc_read_int(cnt + 4, st);
+    if (rounds_out) *rounds_out = rounds;
+    return AMG_OK;
+}
+
 }  // namespace amg
