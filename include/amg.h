@@ -76,6 +76,7 @@ typedef struct {
     int max_dense;     /* [4096] largest coarsest level accepted for the dense Cholesky solve */
     int keep_sweeps;   /* [0] keep every sweep's matching and aggregates for amg_export_sweep */
     int profile;       /* [0] time every kernel / setup phase with CUDA events (amg_kernel_stats) */
+    int match_kernel;  /* [0] matching rounds in one cooperative launch when possible; 1: a launch pair per round */
     void* stream;      /* [NULL] cudaStream_t for every device operation; NULL = legacy default */
 } amg_options;
 

@@ -48,7 +48,7 @@ class amg_options(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):

@@ -89,7 +89,7 @@ struct DevCsr {
 // SELL-32 (sliced ELLPACK, slice height 32, no row sorting): slice s holds
 // rows 32s..32s+31; its entries start at sptr[s] and are stored column-major
 // inside the slice (entry k of lane r at sptr[s] + 32k + r). Short rows are
-// padded with (col = row, val = 0).
+// padded with (col = the row's last column, val = 0).
 constexpr int SELL_C = 32;
 struct DevSell {
     int n = 0;
@@ -113,7 +113,11 @@ struct SweepRecord {
 
 struct Level {
     DevCsr A;
-    DevSell S;
+    DevSell S;                  // A_l in SELL-32 (PCG product, extra smoothing sweeps)
+    double* valm = nullptr;     // A_l M_l^{-1} values in S's layout (first pre-smoothing sweep)
+    float* valm32 = nullptr;
+    DevSell AP;                 // A_l P_l in SELL-32 (coarse-correction residual update)
+    int64_t ap_nnz = 0;
     double* w = nullptr;        // smooth vector on this level
     double* minv = nullptr;     // l1-Jacobi inverse diagonal
     float* minv32 = nullptr;
@@ -156,6 +160,7 @@ struct amg_hierarchy {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
+    int coop_blocks = 0;        // grid of the cooperative matching kernel (0: not available)
     amg::DevArena mem;
     std::vector<amg::Level> lev;
     int nc = 0;                 // coarsest size

@@ -94,6 +94,7 @@ void amg_options_default(amg_options* o) {
     o->max_dense = 4096;
     o->keep_sweeps = 0;
     o->profile = 0;
+    o->match_kernel = 0;
     o->stream = nullptr;
 }
 

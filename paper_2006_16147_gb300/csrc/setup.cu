@@ -193,6 +193,224 @@ __global__ void k_ld_update(int n, const int* __restrict__ ptr, const int* __res
     }
 }
 
+
+// ------------------------------- all matching rounds in one cooperative launch
+// The same rounds as k_ld_match / k_ld_update, separated by a software grid
+// barrier instead of kernel boundaries. Each vertex's edges are sorted once
+// by the strict edge order, so its best free neighbour is found by moving a
+// forward-only pointer past neighbours that are no longer free (vertices only
+// ever stop being free). Values that other blocks change during the launch
+// (mate, cand, pos, lists, counters) are read with ld.cg so the per-SM L1
+// cannot serve a stale copy. Every wait is bounded by a 2 s timer: a block
+// that waits longer sets *err and all blocks leave the round loop.
+constexpr unsigned long long BAR_TIMEOUT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier number `epoch` (1, 2, ...): every block adds one to *count and
+// waits until it reaches epoch * gridDim.x. *count starts at 0 per launch.
+__device__ __forceinline__ void grid_sync(unsigned* count, unsigned epoch, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned target = epoch * gridDim.x;
+        if (ld_acquire_u32(count) < target) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(count) < target) {
+                if (global_ns() - t0 > BAR_TIMEOUT_NS) {
+                    atomicExch(err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Sorts row v's edges by the strict order into (sc, nbr) at the row's own
+// CSR segment; entries that are not edges go last with nbr = -1.
+__global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const double* __restrict__ c, double* __restrict__ sc, int* __restrict__ nbr,
+                             int* __restrict__ pos, int* __restrict__ cand, int* mate) {
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int b = ptr[v], e = ptr[v + 1];
+        int m = b;
+        for (int k = b; k < e; ++k) {
+            const double cw = c[k];
+            if (cw == NEG_INF) continue;
+            const int u = col[k];
+            int d = m - 1;
+            // insert (cw, u) keeping the order: larger weight, then smaller (lo, hi)
+            while (d >= b && key_better(cw, min(u, v), max(u, v), sc[d], min(nbr[d], v), max(nbr[d], v))) {
+                sc[d + 1] = sc[d];
+                nbr[d + 1] = nbr[d];
+                --d;
+            }
+            sc[d + 1] = cw;
+            nbr[d + 1] = u;
+            ++m;
+        }
+        for (int k = m; k < e; ++k) nbr[k] = -1;
+        pos[v] = b;
+        cand[v] = m > b ? nbr[b] : -1;
+        if (m == b) mate[v] = -2;
+    }
+}
+
+// Best free neighbour of v from its sorted list; advances pos[v].
+__device__ __forceinline__ int best_free_sorted(int v, const int* __restrict__ ptr, const int* __restrict__ nbr,
+                                                int* pos, const int* mate) {
+    const int e = __ldg(ptr + v + 1);
+    int k = __ldcg(pos + v);
+    while (k < e) {
+        const int u = __ldg(nbr + k);
+        if (u < 0) { k = e; break; }
+        if (__ldcg(mate + u) == -1) break;
+        ++k;
+    }
+    pos[v] = k;
+    return k < e ? __ldg(nbr + k) : -1;
+}
+
+// Appends each thread's k items (k <= BA_MAX) to list[*cnt...] with one
+// atomic per block. Every thread of the block must call it.
+constexpr int BA_MAX = 8;
+__device__ __forceinline__ void block_append(int k, const int* items, int* list, int* cnt, int cap) {
+    __shared__ int s_base;
+    const int off = block_exclusive_scan_int(k);
+    if (threadIdx.x == blockDim.x - 1) {
+        const int total = off + k;
+        s_base = total > 0 ? atomicAdd(cnt, total) : 0;
+    }
+    __syncthreads();
+    const int b = s_base + off;
+    for (int i = 0; i < k; ++i)
+        if (b + i < cap) list[b + i] = items[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+
+// One round per grid barrier. Round 0 matches the mutual pairs of the initial
+// candidates. Round r >= 1 takes the vertices matched in round r-1; each of
+// their free neighbours whose candidate was one of them picks its next best
+// free neighbour b, publishes cand[x] = b, and (after a sequentially
+// consistent fence) checks cand[b] == x. When x and b recompute in the same
+// round, the store-fence-load on both sides guarantees that at least one of
+// them sees the pair; the CAS on mate[min] matches it once. A vertex
+// recomputes only because its old candidate was matched, so a stale read of
+// cand never names a free vertex; a pick that is matched concurrently is
+// redone in the next round, when that vertex's neighbours are revisited.
+// The set of pairs matched in each round equals one round of the
+// locally-dominant algorithm.
+//
+// cnt: [0..2] match-list counters (ring of three rounds), [6] barrier
+// arrivals, [7] error, [8] rounds that matched at least one pair.
+__global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __restrict__ ptr,
+                                                        const int* __restrict__ col, const int* __restrict__ nbr,
+                                                        int* pos, int* cand, int* mate, int* list0, int* list1,
+                                                        int* mlist, int* cnt, long long max_rounds) {
+    (void)mlist;
+    int* lists[2] = {list0, list1};
+    unsigned* bar = reinterpret_cast<unsigned*>(cnt + 6);
+    int* err = cnt + 7;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    __shared__ int s_chunks;
+    unsigned epoch = 0;
+    int items[BA_MAX];
+    // round 0: mutual initial candidates
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int v = base + threadIdx.x;
+        int k = 0;
+        if (v < n && __ldcg(mate + v) == -1) {
+            const int u = __ldcg(cand + v);
+            if (u > v && __ldcg(cand + u) == v && atomicCAS(&mate[v], -1, u) == -1) {
+                mate[u] = v;
+                items[0] = v;
+                items[1] = u;
+                k = 2;
+            }
+        }
+        block_append(k, items, lists[0], cnt + 0, n);
+    }
+    grid_sync(bar, ++epoch, err);
+    if (__ldcg(err)) return;
+    if (leader && __ldcg(cnt + 0) > 0) cnt[8] += 1;
+    constexpr int NG = 8;
+    const int gpb = blockDim.x / NG, grp = threadIdx.x / NG, gl = threadIdx.x % NG;
+    for (long long r = 1;; ++r) {
+        const int* M = lists[(r - 1) & 1];
+        const int m_cnt = min(__ldcg(cnt + (int)((r - 1) % 3)), n);
+        if (m_cnt == 0) return;
+        if (r > max_rounds) {
+            if (leader) atomicExch(err, 2);
+            return;
+        }
+        int* nl = lists[r & 1];
+        int* nc = cnt + (int)(r % 3);
+        // slot (r+1) % 3 was last read at the start of round r-1; it collects round r+1's pairs
+        if (leader) cnt[(int)((r + 1) % 3)] = 0;
+        // one group of NG lanes per matched vertex, one lane per neighbour
+        for (int base = blockIdx.x * gpb; base < m_cnt; base += gridDim.x * gpb) {   // block-uniform trip count
+            const int t = base + grp;
+            int kb = 0, ke = 0, m = -1;
+            if (t < m_cnt) {
+                m = __ldcg(M + t);
+                kb = __ldg(ptr + m);
+                ke = __ldg(ptr + m + 1);
+            }
+            if (threadIdx.x == 0) s_chunks = 0;
+            __syncthreads();
+            const int my_chunks = (ke - kb + NG - 1) / NG;
+            if (gl == 0 && my_chunks > 0) atomicMax(&s_chunks, my_chunks);
+            __syncthreads();
+            const int chunks = s_chunks;
+            for (int ch = 0; ch < chunks; ++ch) {
+                int k = 0;
+                const int q = kb + ch * NG + gl;
+                if (q < ke) {
+                    const int x = __ldg(col + q);
+                    if (x != m && __ldcg(mate + x) == -1 && __ldcg(cand + x) == m) {
+                        const int b = best_free_sorted(x, ptr, nbr, pos, mate);
+                        cand[x] = b;
+                        if (b < 0) {
+                            mate[x] = -2;
+                        } else {
+                            fence_sc_gpu();
+                            if (__ldcg(cand + b) == x) {
+                                const int lo = min(x, b), hi = max(x, b);
+                                if (atomicCAS(&mate[lo], -1, hi) == -1) {
+                                    mate[hi] = lo;
+                                    items[0] = lo;
+                                    items[1] = hi;
+                                    k = 2;
+                                }
+                            }
+                        }
+                    }
+                }
+                block_append(k, items, nl, nc, n);
+            }
+        }
+        grid_sync(bar, ++epoch, err);
+        if (__ldcg(err)) return;
+        if (leader && __ldcg(nc) > 0) cnt[8] += 1;
+    }
+}
+
 // ------------------------------------------ aggregates + Eq. 4 prolongator --
 __global__ void k_head_flags(int n, const int* __restrict__ mate, int* __restrict__ flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -386,7 +604,9 @@ __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, con
         long long pos = (long long)sptr[s] * 32 + lane;
         int len = 0, b = 0;
         if (i < n) { b = ptr[i]; len = ptr[i + 1] - b; }
-        const int pad = i < n ? i : 0;
+        // padding repeats the row's last column (a valid index of this
+        // matrix's column space, also for rectangular A P) with value 0
+        const int pad = len > 0 ? col[b + len - 1] : 0;
         for (int k = 0; k < width; ++k, pos += 32) {
             if (k < len) { scol[pos] = col[b + k]; sval[pos] = val[b + k]; }
             else { scol[pos] = pad; sval[pos] = 0.0; }
@@ -451,6 +671,53 @@ __global__ void k_gram(int n, const double* __restrict__ Y, double* __restrict__
     Ainv[(size_t)i * n + j] = s;
 }
 
+// Column scaling for the pre-smoother: valm_k = val_k * minv[col_k].
+__global__ void k_scale_cols(long long m, const int* __restrict__ col, const double* __restrict__ val,
+                             const double* __restrict__ minv, double* __restrict__ valm, float* __restrict__ valm32) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
+        const double v = val[k] * minv[col[k]];
+        valm[k] = v;
+        if (valm32) valm32[k] = (float)v;
+    }
+}
+
+// Row i of A P: terms a_ij p_j keyed by agg(j), stably sorted by key and
+// summed per key in column order, in scratch at row i's own CSR segment.
+__global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ val, const int* __restrict__ agg, const double* __restrict__ p,
+                          int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = ptr[i], len = ptr[i + 1] - b;
+        int* K = skey + b;
+        double* V = sval + b;
+        for (int k = 0; k < len; ++k) {
+            const int j = col[b + k];
+            K[k] = agg[j];
+            V[k] = val[b + k] * p[j];
+        }
+        for (int a = 1; a < len; ++a) {
+            const int key = K[a];
+            const double v = V[a];
+            int c = a - 1;
+            while (c >= 0 && K[c] > key) { K[c + 1] = K[c]; V[c + 1] = V[c]; --c; }
+            K[c + 1] = key;
+            V[c + 1] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < len;) {
+            const int key = K[a];
+            double sum = V[a];
+            int e = a + 1;
+            while (e < len && K[e] == key) { sum += V[e]; ++e; }
+            K[u] = key;
+            V[u] = sum;
+            ++u;
+            a = e;
+        }
+        cnt[i] = u;
+    }
+}
+
 // ------------------------------------------------------------ host side ----
 struct Scratch {
     DevArena mem;
@@ -481,10 +748,35 @@ int read_int(const int* dev, int* host, cudaStream_t st) {
 }
 
 // Locally-dominant matching by frontier rounds. Returns the number of rounds.
+// All rounds run in one cooperative launch when the device allows it; else
+// each round is one launch pair with a host check every 16 rounds.
 int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
     cudaStream_t st = h->stream;
     const int n = A.n;
     CUDA_CHECK(cudaMemsetAsync(S.mate, 0xff, sizeof(int) * n, st));   // all -1
+    if (h->opt.match_kernel == 0 && h->coop_blocks > 0) {
+        int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
+        double* sc = S.sval;
+        int* pos = S.flag;
+        CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 16, st));
+        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate);
+        KERNEL_CHECK();
+        int nn = n;
+        const int* ptr = A.ptr;
+        const int* col = A.col;
+        long long max_rounds = (long long)n + 4;
+        void* args[] = {&nn, &ptr, &col, &nbr, &pos, &S.cand, &S.mate, &S.list0, &S.list1, &S.mlist, &S.cnt,
+                        &max_rounds};
+        CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_ld_persistent, dim3(h->coop_blocks), dim3(1024), args, 0,
+                                               st));
+        KERNEL_CHECK();
+        int hc[16];
+        CUDA_CHECK(cudaMemcpyAsync(hc, S.cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        CUDA_CHECK(cudaStreamSynchronize(st));
+        if (hc[7] == 1) AMG_THROW(AMG_ERR_TIMEOUT, "matching kernel: grid barrier wait exceeded 2 s");
+        if (hc[7] == 2) AMG_THROW(AMG_ERR_TIMEOUT, "matching did not settle after n rounds");
+        return hc[8];
+    }
     CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 5, st));
     k_ld_init<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.cand, S.mate);
     KERNEL_CHECK();
@@ -540,13 +832,12 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     return C;
 }
 
-void build_sell(amg_hierarchy* h, Level& L, Scratch& S, bool fp32) {
+void build_sell(amg_hierarchy* h, const DevCsr& A, DevSell& E, Scratch& S, bool fp32) {
     cudaStream_t st = h->stream;
-    DevSell& E = L.S;
-    E.n = L.A.n;
-    E.nslices = (L.A.n + SELL_C - 1) / SELL_C;
+    E.n = A.n;
+    E.nslices = (A.n + SELL_C - 1) / SELL_C;
     E.sptr = h->mem.alloc<int>(E.nslices + 1);
-    k_sell_width<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(L.A.n, E.nslices, L.A.ptr,
+    k_sell_width<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(A.n, E.nslices, A.ptr,
                                                                                              S.ub);
     KERNEL_CHECK();
     scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
@@ -554,13 +845,46 @@ void build_sell(amg_hierarchy* h, Level& L, Scratch& S, bool fp32) {
     E.col = h->mem.alloc<int>(E.padded);
     E.val = h->mem.alloc<double>(E.padded);
     k_sell_fill<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-        L.A.n, E.nslices, L.A.ptr, L.A.col, L.A.val, E.sptr, E.col, E.val);
+        A.n, E.nslices, A.ptr, A.col, A.val, E.sptr, E.col, E.val);
     KERNEL_CHECK();
     if (fp32) {
         E.val32 = h->mem.alloc<float>(E.padded);
         k_to_float<<<blocks_for(E.padded, TPB, h->num_sms * 16), TPB, 0, st>>>(E.padded, E.val, E.val32);
         KERNEL_CHECK();
     }
+}
+
+// Column-scaled values of A M^{-1} in A's SELL layout (padding stays 0).
+void build_scaled(amg_hierarchy* h, Level& L, bool fp32) {
+    cudaStream_t st = h->stream;
+    const long long m = L.S.padded;
+    L.valm = h->mem.alloc<double>(m);
+    if (fp32) L.valm32 = h->mem.alloc<float>(m);
+    k_scale_cols<<<blocks_for(m, TPB, h->num_sms * 16), TPB, 0, st>>>(m, L.S.col, L.S.val, L.minv, L.valm, L.valm32);
+    KERNEL_CHECK();
+}
+
+// A_l P_l in SELL (rows of A_l, columns the aggregates of level l+1).
+void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
+    cudaStream_t st = h->stream;
+    const int n = L.A.n;
+    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, S.skey, S.sval, S.ub);
+    KERNEL_CHECK();
+    DevCsr AP;
+    AP.n = n;
+    AP.ptr = S.mem.alloc<int>(n + 1);
+    scan_exclusive(S.ub, AP.ptr, n, AP.ptr + n, st, S.scan_tmp);
+    AP.nnz = read_int(AP.ptr + n, S.host, st);
+    AP.col = S.mem.alloc<int>(AP.nnz);
+    AP.val = S.mem.alloc<double>(AP.nnz);
+    k_rap_copy<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val);
+    KERNEL_CHECK();
+    L.ap_nnz = AP.nnz;
+    build_sell(h, AP, L.AP, S, fp32);
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    S.mem.release(AP.ptr);
+    S.mem.release(AP.col);
+    S.mem.release(AP.val);
 }
 
 void build_members(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
@@ -589,6 +913,12 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
 
     Scratch S;
     CUDA_CHECK(cudaHostAlloc(&S.host, 64, cudaHostAllocDefault));
+    {
+        int coop = 0, per_sm = 0;
+        CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ld_persistent, 1024, 0));
+        h->coop_blocks = (coop && per_sm >= 1) ? h->num_sms : 0;
+    }
     S.diag = S.mem.alloc<double>(n0);
     S.c = S.mem.alloc<double>(nnz0);
     S.mate = S.mem.alloc<int>(n0);
@@ -747,9 +1077,11 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             KERNEL_CHECK();
         }
         Scope sc_(&h->prof, st, S_FORMAT, 24.0 * L.A.nnz);
-        if (l == 0 || l < nlev - 1) build_sell(h, L, S, fp32);
+        if (l == 0 || l < nlev - 1) build_sell(h, L.A, L.S, S, fp32);
         if (l == nlev - 1) break;
+        build_scaled(h, L, fp32);
         build_members(h, L, h->lev[l + 1].A.n, S);
+        build_ap(h, L, h->lev[l + 1].A.n, S, fp32);
         if (fp32) {
             L.p32 = h->mem.alloc<float>(n);
             k_to_float<<<grid_for(h, n), TPB, 0, st>>>(n, L.p, L.p32);

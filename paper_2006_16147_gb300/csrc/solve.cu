@@ -89,27 +89,50 @@ struct SellView {
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Row dot product of one SELL slice lane: sum_k val[k] * xv(col[k]). The
+// loop is unrolled by four with two accumulators so that the column, value
+// and gather loads of four entries are in flight together.
+template <typename T, typename F>
+__device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __restrict__ val, long long base, int w,
+                                      F&& xv) {
+    T a0 = 0, a1 = 0;
+    int k = 0;
+    for (; k + 4 <= w; k += 4, base += 128) {
+        const int j0 = ld(col + base), j1 = ld(col + base + 32), j2 = ld(col + base + 64), j3 = ld(col + base + 96);
+        const T v0 = ld(val + base), v1 = ld(val + base + 32), v2 = ld(val + base + 64), v3 = ld(val + base + 96);
+        const T x0 = xv(j0), x1 = xv(j1), x2 = xv(j2), x3 = xv(j3);
+        a0 = fma(v0, x0, a0);
+        a1 = fma(v1, x1, a1);
+        a0 = fma(v2, x2, a0);
+        a1 = fma(v3, x3, a1);
+    }
+    for (; k < w; ++k, base += 32) a0 = fma(ld(val + base), xv(ld(col + base)), a0);
+    return a0 + a1;
+}
+
+#define SELL_LOOP(S)                                                                 \
+    const int lane = threadIdx.x & 31;                                               \
+    const int nw_ = gridDim.x * WARPS;                                               \
+    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < (S).nslices; s += nw_)
+
+#define SELL_ROW_ARGS(S) (S).col, (long long)(S).sptr[s] * 32 + lane, (S).sptr[s + 1] - (S).sptr[s]
+
 // --------------------------------------------------------- V-cycle ---------
+// First pre-smoothing sweep from a zero guess, fused with the residual:
+//   x = omega M^-1 b,  r = b - omega (A M^-1) b,
+// with the column-scaled values valm = A M^-1 (one FMA per stored entry).
 template <typename T, typename TB>
-__global__ void __launch_bounds__(TPB) k_pre_residual(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
-                                                      T omega, const TB* __restrict__ b, T* __restrict__ x,
-                                                      T* __restrict__ r) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        T acc = 0;
-        for (int k = 0; k < w; ++k, base += 32) {
-            const int j = ld(S.col + base);
-            const T xj = (omega * ld(minv + j)) * (T)ld(b + j);
-            acc = fma(ld(val + base), xj, acc);
-        }
+__global__ void __launch_bounds__(TPB) k_pre(SellView S, const T* __restrict__ valm, const T* __restrict__ minv,
+                                             T omega, const TB* __restrict__ b, T* __restrict__ x,
+                                             T* __restrict__ r) {
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, valm, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return (T)ld(b + j); });
         const int i = s * 32 + lane;
         if (i < S.n) {
             const T bi = (T)b[i];
             x[i] = (omega * minv[i]) * bi;
-            r[i] = bi - acc;
+            r[i] = fma(-omega, acc, bi);
         }
     }
 }
@@ -127,33 +150,28 @@ __global__ void __launch_bounds__(TPB) k_restrict(int nc, const int* __restrict_
     }
 }
 
-// y = x + P e, then y += omega M^-1 (b - A y). With DOT, also r . z on level
-// 0 (r = b, z = out), finished into the CG scalars.
+// Coarse correction and first post-smoothing sweep, fused:
+//   y = x + P e,  out = y + omega M^-1 (b - A y),
+// evaluated as out = y + omega M^-1 (r - (A P) e) since b - A y = r - A P e
+// with r = b - A x from the pre-smoother; A P has about half the entries of A
+// and gathers only the short coarse vector e. With DOT, also bdot . out
+// (r . z of CG on level 0), finished into the CG scalars.
 template <typename T, typename TB, typename TO, bool DOT>
-__global__ void __launch_bounds__(TPB) k_post(SellView S, const T* __restrict__ val, const T* __restrict__ minv, T omega,
-                                              const int* __restrict__ agg, const T* __restrict__ p,
-                                              const T* __restrict__ e, const TB* __restrict__ b,
-                                              const T* __restrict__ x, TO* __restrict__ out, Reducer red,
-                                              PcgScalars* sc, int mode) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
+__global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict__ apval, const T* __restrict__ minv,
+                                              T omega, const int* __restrict__ agg, const T* __restrict__ p,
+                                              const T* __restrict__ e, const T* __restrict__ x,
+                                              const T* __restrict__ r, const TB* __restrict__ bdot,
+                                              TO* __restrict__ out, Reducer red, PcgScalars* sc, int mode) {
     double dot = 0.0;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        T acc = 0;
-        for (int k = 0; k < w; ++k, base += 32) {
-            const int j = ld(S.col + base);
-            const T yj = fma(ld(p + j), ld(e + ld(agg + j)), ld(x + j));
-            acc = fma(ld(val + base), yj, acc);
-        }
+    SELL_LOOP(SAP) {
+        const T acc = sell_row(SAP.col, apval, (long long)SAP.sptr[s] * 32 + lane, SAP.sptr[s + 1] - SAP.sptr[s],
+                               [&](int q) { return ld(e + q); });
         const int i = s * 32 + lane;
-        if (i < S.n) {
+        if (i < SAP.n) {
             const T yi = fma(p[i], e[agg[i]], x[i]);
-            const T bi = (T)b[i];
-            const T o = fma(omega * minv[i], bi - acc, yi);
+            const T o = fma(omega * minv[i], r[i] - acc, yi);
             out[i] = (TO)o;
-            if (DOT) dot = fma((double)b[i], (double)(TO)o, dot);
+            if (DOT) dot = fma((double)bdot[i], (double)(TO)o, dot);
         }
     }
     if (DOT) reduce_and_finish(dot, 0.0, red, sc, mode);
@@ -166,17 +184,9 @@ __global__ void __launch_bounds__(TPB) k_pre_step(SellView S, const T* __restric
                                                   T omega, const TB* __restrict__ b, const T* __restrict__ xin,
                                                   const T* __restrict__ rin, T* __restrict__ xout,
                                                   T* __restrict__ rout) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        T acc = 0;
-        for (int k = 0; k < w; ++k, base += 32) {
-            const int j = ld(S.col + base);
-            const T xj = fma(omega * ld(minv + j), ld(rin + j), ld(xin + j));
-            acc = fma(ld(val + base), xj, acc);
-        }
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return fma(omega * ld(minv + j), ld(rin + j), ld(xin + j)); });
         const int i = s * 32 + lane;
         if (i < S.n) {
             xout[i] = fma(omega * minv[i], rin[i], xin[i]);
@@ -190,13 +200,9 @@ template <typename T, typename TB, typename TO>
 __global__ void __launch_bounds__(TPB) k_smooth(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
                                                 T omega, const TB* __restrict__ b, const T* __restrict__ yin,
                                                 TO* __restrict__ yout) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        T acc = 0;
-        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(yin + ld(S.col + base)), acc);
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return ld(yin + j); });
         const int i = s * 32 + lane;
         if (i < S.n) yout[i] = (TO)fma(omega * minv[i], (T)b[i] - acc, yin[i]);
     }
@@ -231,14 +237,10 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* 
 __global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __restrict__ val,
                                                   const double* __restrict__ x, const double* __restrict__ b,
                                                   double* __restrict__ r, Reducer red, PcgScalars* sc) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
     double rr = 0.0, bb = 0.0;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        double acc = 0.0;
-        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(x + ld(S.col + base)), acc);
+    SELL_LOOP(S) {
+        const double acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                                    [&](int j) { return ld(x + j); });
         const int i = s * 32 + lane;
         if (i < S.n) {
             const double bi = b[i];
@@ -255,14 +257,10 @@ __global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __re
 __global__ void __launch_bounds__(TPB) k_spmv_dot(SellView S, const double* __restrict__ val,
                                                   const double* __restrict__ p, double* __restrict__ q, Reducer red,
                                                   PcgScalars* sc) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * WARPS;
     double pq = 0.0;
-    for (int s = blockIdx.x * WARPS + (threadIdx.x >> 5); s < S.nslices; s += nw) {
-        const int w = S.sptr[s + 1] - S.sptr[s];
-        long long base = (long long)S.sptr[s] * 32 + lane;
-        double acc = 0.0;
-        for (int k = 0; k < w; ++k, base += 32) acc = fma(ld(val + base), ld(p + ld(S.col + base)), acc);
+    SELL_LOOP(S) {
+        const double acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                                    [&](int j) { return ld(p + j); });
         const int i = s * 32 + lane;
         if (i < S.n) {
             q[i] = acc;
@@ -299,11 +297,12 @@ __global__ void __launch_bounds__(TPB) k_update_p(int n, const double* __restric
 // or written once (index 4 B, value V B, the level-0 input/output in FP64);
 // matrix entries counted without SELL padding.
 double by_pre(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 3.0 * V); }
+// post: A P entries + x, r, p, minv (V) + agg (4) + out (Vo) [+ CG r for the dot] + e (n_c)
+double by_post2(const Level& L, int nc, int V, int Vo, bool dot) {
+    return (double)L.ap_nnz * (V + 4) + (double)L.A.n * (4.0 * V + 4 + Vo + (dot ? 8 : 0)) + (double)nc * V;
+}
 double by_pre_step(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 5.0 * V); }
 double by_restrict(int n, int nc, int V) { return (double)n * (4 + 2.0 * V) + (double)nc * (4 + V); }
-double by_post(const Level& L, int nc, int V, int Vb, int Vo) {
-    return (double)L.A.nnz * (V + 4) + (double)L.A.n * (3.0 * V + 4 + Vb + Vo) + (double)nc * V;
-}
 double by_smooth(const Level& L, int V, int Vb, int Vo) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (2.0 * V + Vb + Vo); }
 double by_coarse(int nc, int Vi, int Vo) { return 8.0 * nc * nc + (double)nc * (Vi + Vo); }
 
@@ -354,6 +353,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         return;
     }
     auto val = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.S.val32 : (const T*)Lv.S.val; };
+    auto valm = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm; };
+    auto apv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val; };
     auto minv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv; };
     auto pv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.p32 : (const T*)Lv.p; };
     auto vec = [&](Level& Lv, int which) -> T* {
@@ -368,7 +369,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     const int V = sizeof(T);
     const int pre = h->opt.pre < 1 ? 1 : h->opt.pre;
     const int post = h->opt.post < 1 ? 1 : h->opt.post;
-    std::vector<T*> xcur(L + 1), out(L + 1), spare(L + 1);
+    std::vector<T*> xcur(L + 1), rcur(L + 1), out(L + 1), spare(L + 1);
 
     // downward: level 0 reads the FP64 r directly
     for (int l = 0; l < L; ++l) {
@@ -379,8 +380,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         const int Vb = l == 0 ? 8 : V;
         {
             Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, Vb));
-            if (l == 0) k_pre_residual<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra);
-            else k_pre_residual<T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra);
+            if (l == 0) k_pre<T, double><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, r, xa, ra);
+            else k_pre<T, T><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra);
             KERNEL_CHECK();
         }
         for (int k = 1; k < pre; ++k) {
@@ -392,6 +393,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             std::swap(ra, rb);
         }
         xcur[l] = xa;
+        rcur[l] = ra;
         spare[l] = (xa == vec(Lv, VX)) ? vec(Lv, VT) : vec(Lv, VX);
         const int nc = h->lev[l + 1].A.n;
         Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(Lv.A.n, nc, V));
@@ -405,15 +407,16 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     for (int l = L - 1; l >= 0; --l) {
         Level& Lv = h->lev[l];
         const SellView S = view(Lv);
+        const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col};
         const int g = sell_grid(h, S.nslices);
         const T* e = out[l + 1];
         const int nc = h->lev[l + 1].A.n;
         if (l > 0) {
             T *ya = vec(Lv, VY), *yb = spare[l];
             {
-                Scope sc_(&h->prof, st, K_POST, by_post(Lv, nc, V, V, V));
-                k_post<T, T, T, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, vec(Lv, VB),
-                                                          xcur[l], ya, h->red, h->sc, FIN_NONE);
+                Scope sc_(&h->prof, st, K_POST, by_post2(Lv, nc, V, V, false));
+                k_post<T, T, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[l],
+                                                          rcur[l], (const T*)nullptr, ya, h->red, h->sc, FIN_NONE);
                 KERNEL_CHECK();
             }
             for (int k = 1; k < post; ++k) {
@@ -426,20 +429,20 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             continue;
         }
         if (post == 1) {
-            Scope sc_(&h->prof, st, K_POST_L0, by_post(Lv, nc, V, 8, 8));
+            Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, 8, rz_mode != FIN_NONE));
             if (rz_mode != FIN_NONE)
                 k_post<T, double, double, true><<<red_grid(h), TPB, 0, st>>>(
-                    S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r, xcur[0], z, h->red, h->sc, rz_mode);
+                    SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[0], rcur[0], r, z, h->red, h->sc, rz_mode);
             else
-                k_post<T, double, double, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r,
-                                                                   xcur[0], z, h->red, h->sc, FIN_NONE);
+                k_post<T, double, double, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
+                                                                   xcur[0], rcur[0], r, z, h->red, h->sc, FIN_NONE);
             KERNEL_CHECK();
         } else {
             T *ya = vec(Lv, VY), *yb = spare[0];
             {
-                Scope sc_(&h->prof, st, K_POST_L0, by_post(Lv, nc, V, 8, V));
-                k_post<T, double, T, false><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, r,
-                                                              xcur[0], ya, h->red, h->sc, FIN_NONE);
+                Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, V, false));
+                k_post<T, double, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
+                                                              xcur[0], rcur[0], r, ya, h->red, h->sc, FIN_NONE);
                 KERNEL_CHECK();
             }
             for (int k = 1; k < post - 1; ++k) {
@@ -502,7 +505,7 @@ void prepare_solve(amg_hierarchy* h) {
     h->sc = h->mem.alloc<PcgScalars>(1);
     CUDA_CHECK(cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->stream));
     if (!h->sc_host) CUDA_CHECK(cudaHostAlloc(&h->sc_host, sizeof(PcgScalars), cudaHostAllocDefault));
-    h->red.blocks = h->num_sms * 4;
+    h->red.blocks = h->num_sms * 8;
     h->red.partial = h->mem.alloc<double>(2 * (size_t)h->red.blocks);
     h->red.ticket = h->mem.alloc<unsigned>(1);
     CUDA_CHECK(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));

@@ -72,10 +72,11 @@ def test_setup_bit_exact(orc, name):
 
 
 def test_matching_rounds_equal_ld_rounds(orc):
+    # one launch pair per round follows the textbook round schedule exactly
     from paper_2006_16147_gb300 import amg
     A = W.poisson3d(20, 16, 12)
     H = orc.Hierarchy(A, use_ld=True, max_coarse=40)
-    h = setup(A, max_coarse=40)
+    h = setup(A, max_coarse=40, match_kernel=1)
     info = amg.amg_hierarchy_info(h)
     for l in range(H.num_levels - 1):
         assert info["rounds"][l] == [s["rounds"] for s in H.level(l).sweeps]
@@ -209,3 +210,25 @@ def test_host_entry_points(orc):
     assert abs(info["iterations"] - io["iterations"]) <= 1
     assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
     h.close()
+
+
+@pytest.mark.parametrize("name", ["poisson_ragged", "spd_random_w", "aniso", "varcoef"])
+def test_match_kernel_modes_agree(orc, name):
+    # one cooperative launch for all rounds vs one launch pair per round: the
+    # same matching; the cooperative kernel may need fewer rounds because a
+    # recompute can already see pairs matched earlier in the same round
+    from paper_2006_16147_gb300 import amg
+    mk, seed = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    hs = [setup(A, w, keep_sweeps=1, max_coarse=40, match_kernel=m) for m in (0, 1)]
+    infos = [amg.amg_hierarchy_info(h) for h in hs]
+    assert infos[0]["n"] == infos[1]["n"]
+    for r0, r1 in zip(infos[0]["rounds"], infos[1]["rounds"]):
+        assert all(0 < a <= b for a, b in zip(r0, r1))
+    for l in range(infos[0]["num_levels"] - 1):
+        for s in range(infos[0]["sweeps_done"][l]):
+            a, b = (amg.amg_export_sweep(h, l, s)["mate"] for h in hs)
+            assert np.array_equal(a, b)
+    for h in hs:
+        h.close()

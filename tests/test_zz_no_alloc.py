@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 def _reference_mate(A, w):
     from paper_2006_16147_gb300 import amg
-    h = setup(A, w, keep_sweeps=1, max_coarse=1)
+    h = setup(A, w, keep_sweeps=1, max_coarse=1, match_kernel=1)
     m = amg.amg_export_sweep(h, 0, 0)["mate"]
     rounds = amg.amg_hierarchy_info(h)["rounds"][0][0]
     h.close()
