@@ -39,6 +39,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--workload", default="poisson", choices=["poisson", "varcoef"],
+                    help="poisson: 7-point Laplacian (default line); varcoef: jump coefficients exp(g), sigma 2")
+    ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -111,10 +114,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(grid):
+def _workload(grid, kind="poisson"):
     from paper_2006_16147_gb300 import workloads as W
-    A = W.poisson3d(grid)
-    b, _ = W.rhs_uniform(A, 1)
+    if kind == "varcoef":
+        A = W.varcoef3d(grid, seed=2)
+        b, _ = W.rhs_uniform(A, 3)
+    else:
+        A = W.poisson3d(grid)
+        b, _ = W.rhs_uniform(A, 1)
     return A, b
 
 
@@ -151,7 +158,9 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve", "grid": args.grid,
+            "config": {"workload": (f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve" if args.workload == "poisson" else
+                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve"),
+                       "grid": args.grid,
                        "rtol": args.rtol},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -178,7 +187,7 @@ def main():
     from paper_2006_16147_gb300 import amg
     amg.lib()
 
-    A, b = _workload(args.grid)
+    A, b = _workload(args.grid, args.workload)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     d_ptr, d_col, d_val = t(A.row_ptr), t(A.col), t(A.val)
     d_w = torch.ones(A.n, dtype=torch.float64, device=dev)
@@ -189,7 +198,8 @@ def main():
 
     def step(profile=0, keep=False):
         d_x.zero_()
-        h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, stream=stream.cuda_stream)
+        h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, krylov=args.krylov,
+                          stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
             return h, info
@@ -237,6 +247,24 @@ def main():
     xs = d_x.cpu().numpy()
     rel = float(np.linalg.norm(b - A.scipy() @ xs) / np.linalg.norm(b))
 
+    # ---- accuracy of a mixed-precision or non-default run: error against an
+    # FP64 solve of the same system to rel-res 1e-10, and iterations at 1e-8
+    accuracy = None
+    if args.precision == "fp32" or args.workload != "poisson":
+        accuracy = {}
+        h64 = amg.amg_setup(d_ptr, d_col, d_val, d_w, stream=stream.cuda_stream)
+        xr = torch.zeros_like(d_x)
+        amg.amg_solve(h64, d_b, xr, rtol=1e-10, maxit=2000)
+        h64.close()
+        for tol in (args.rtol, 1e-8):
+            hh = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov, stream=stream.cuda_stream)
+            xt = torch.zeros_like(d_x)
+            inf = amg.amg_solve(hh, d_b, xt, rtol=tol, maxit=2000)
+            hh.close()
+            e = float(torch.linalg.norm(xt - xr) / torch.linalg.norm(xr))
+            accuracy[f"rtol_{tol:g}"] = {"iterations": inf["iterations"], "true_relres": inf["true_relres"],
+                                         "rel_error_vs_fp64_1e-10": e}
+
     # ---- roofline of the dominant solve kernel (largest summed time)
     peak, peak_kind = _peaks()
     solve_k = {k: v for k, v in kstats.items() if not k.startswith("setup_")}
@@ -258,13 +286,13 @@ def main():
               for k, v in dict(ptr=A.row_ptr, col=A.col, val=A.val, w=np.ones(A.n), b=b).items()}
         xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
         e2e_steps = max(1, min(3, args.steps))
-        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec)
+        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov)
         amg_h.close()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             xh[:] = 0.0
-            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec)
+            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov)
             amg.amg_solve_host(hh, hp["b"], xh, rtol=args.rtol, maxit=1000)
             hh.close()
         barrier()
@@ -292,7 +320,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle",
             "data": "synthetic",
-            "config": {"workload": f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve", "grid": args.grid,
+            "config": {"workload": (f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve" if args.workload == "poisson" else
+                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve"),
+                       "grid": args.grid,
                        "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
                        "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",
                        "precision": args.precision, "parallelism": "replicas" if world > 1 else "single"},
@@ -300,7 +330,7 @@ def main():
             "setup_ms": round(statistics.mean(h["setup_ms"] for h in hinfos), 3),
             "solve_ms": round(statistics.mean(i["solve_ms"] for i in infos), 3),
             "levels": hi["n"], "opc": round(hi["opc"], 4), "solves_per_s": round(world * 1e3 / ms, 3),
-            "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches),
+            "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches), "accuracy": accuracy,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

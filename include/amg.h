@@ -73,10 +73,15 @@ typedef struct {
     int pre, post;     /* [1, 1] l1-Jacobi sweeps before and after the coarse correction (Eq. 2) */
     double omega;      /* [1.0] smoother damping */
     int precision;     /* [AMG_FP64] or AMG_FP32_VCYCLE: V-cycle in float inside FP64 CG */
-    int max_dense;     /* [4096] largest coarsest level accepted for the dense Cholesky solve */
+    int max_dense;     /* [4096] largest coarsest level solved by dense Cholesky; a larger coarsest level is
+                          solved by CG with l1-Jacobi to rel-res 1e-4 or 30 iterations (the coarsest-solver
+                          setting of Section 5); use krylov = 1 then, as that solve is not a fixed operator */
     int keep_sweeps;   /* [0] keep every sweep's matching and aggregates for amg_export_sweep */
     int profile;       /* [0] time every kernel / setup phase with CUDA events (amg_kernel_stats) */
     int match_kernel;  /* [0] matching rounds in one cooperative launch when possible; 1: a launch pair per round */
+    int krylov;        /* [0] 0 = PCG; 1 = flexible CG keeping one direction (FCG(1), the paper's outer
+                          solver, Section 5), robust to a V-cycle that is not exactly linear (FP32) */
+    double min_ratio;  /* [1.5] stop coarsening after a level with n_l / n_{l+1} below this (stalled matching) */
     void* stream;      /* [NULL] cudaStream_t for every device operation; NULL = legacy default */
 } amg_options;
 
@@ -102,6 +107,7 @@ typedef struct {
     double opc;                                      /* sum nnz(A_l) / nnz(A_0) */
     double avg_coarsening_ratio;                     /* mean of n_l / n_{l+1} over the nl-1 steps */
     double setup_ms;                                 /* wall time of amg_setup */
+    int coarse_solver;                               /* 0: dense Cholesky, 1: CG (coarsest above max_dense) */
     size_t device_bytes;                             /* device memory held by the hierarchy */
 } amg_hier_info;
 
@@ -156,7 +162,8 @@ amg_status amg_sweep_dims(const amg_hierarchy* h, int level, int sweep, int32_t*
 amg_status amg_export_sweep(const amg_hierarchy* h, int level, int sweep, int32_t* mate, int32_t* agg, double* p,
                             double* wc);
 
-/* Dense Cholesky factor L (lower, column-major nc x nc, HOST) of the coarsest level. */
+/* Dense Cholesky factor L (lower, column-major nc x nc, HOST) of the coarsest level
+ * (AMG_ERR_ARG when the coarsest level is solved by CG). */
 amg_status amg_coarse_factor(const amg_hierarchy* h, double* L);
 
 /*

@@ -42,7 +42,9 @@ def lib():
             L = ctypes.CDLL(build())
             L.orc_setup.restype = ctypes.c_void_p
             L.orc_setup.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
-                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _ip]
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, _ip]
+            L.orc_coarse_is_cg.argtypes = [ctypes.c_void_p]
             for name in ("orc_free",):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
             L.orc_num_levels.argtypes = [ctypes.c_void_p]
@@ -56,7 +58,8 @@ def lib():
             L.orc_coarse_factor.argtypes = [ctypes.c_void_p, _f64p]
             L.orc_vcycle.argtypes = [ctypes.c_void_p, _f64p, _f64p]
             L.orc_vcycle_level.argtypes = [ctypes.c_void_p, ctypes.c_int, _f64p, _f64p]
-            L.orc_pcg.argtypes = [ctypes.c_void_p, _f64p, _f64p, ctypes.c_double, ctypes.c_int, _ip, _f64p, _f64p]
+            L.orc_pcg.argtypes = [ctypes.c_void_p, _f64p, _f64p, ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip,
+                                  _f64p, _f64p]
             L.orc_weights.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _f64p]
             L.orc_match_greedy.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _i32p]
             L.orc_match_ld.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, _i32p, _ip]
@@ -119,12 +122,13 @@ class Hierarchy:
     """Oracle hierarchy: setup in the constructor, then V-cycle and PCG."""
 
     def __init__(self, A, w=None, sweeps=3, max_coarse=200, max_levels=32, pre=1, post=1, omega=1.0,
-                 use_ld=False):
+                 use_ld=False, min_ratio=1.5, max_dense=4096):
         rp, cl, vl = _csr_args(A)
         w = np.ones(A.n) if w is None else np.ascontiguousarray(w, dtype=np.float64)
         st = ctypes.c_int(0)
         self._h = lib().orc_setup(A.n, _p(rp, _i32p), _p(cl, _i32p), _p(vl, _f64p), _p(w, _f64p), sweeps,
-                                  max_coarse, max_levels, pre, post, float(omega), int(use_ld), ctypes.byref(st))
+                                  max_coarse, max_levels, pre, post, float(omega), int(use_ld), float(min_ratio),
+                                  int(max_dense), ctypes.byref(st))
         if not self._h:
             raise OracleError(f"orc_setup failed: {st.value}")
         self.n = A.n
@@ -186,6 +190,10 @@ class Hierarchy:
             out.append((n.value, nnz.value))
         return out
 
+    @property
+    def coarse_is_cg(self) -> bool:
+        return bool(lib().orc_coarse_is_cg(self._h))
+
     def coarse_factor(self) -> np.ndarray:
         nc = self.sizes()[-1][0]
         L = np.empty(nc * nc)
@@ -198,12 +206,12 @@ class Hierarchy:
         lib().orc_vcycle_level(self._h, level, _p(r, _f64p), _p(z, _f64p))
         return z
 
-    def pcg(self, b, x0=None, rtol=1e-6, maxit=1000):
+    def pcg(self, b, x0=None, rtol=1e-6, maxit=1000, flexible=False):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
         it = ctypes.c_int(0)
         rr = ctypes.c_double(0)
         tr = ctypes.c_double(0)
-        st = lib().orc_pcg(self._h, _p(b, _f64p), _p(x, _f64p), float(rtol), int(maxit), ctypes.byref(it),
+        st = lib().orc_pcg(self._h, _p(b, _f64p), _p(x, _f64p), float(rtol), int(maxit), int(flexible), ctypes.byref(it),
                            ctypes.byref(rr), ctypes.byref(tr))
         return x, dict(status=st, iterations=it.value, relres=rr.value, true_relres=tr.value)

@@ -18,10 +18,13 @@
 //   aggregates + prolongator (Eq. 4) -- partition, orthonormal columns, P w_c = w
 //   pairwise Galerkin product        -- dense P^T A P (numpy) on small inputs
 //   level loop + stop rule           -- paper's hierarchy table: 80^3 -> 5 levels,
-//                                      ratio 8.00, coarsest 125; opc 1.141
+//                                      ratio 8.00, coarsest 125; opc 1.141; stall rule
+//                                      by construction on a star graph
+//   coarsest CG (large coarsest)     -- residual of the returned x vs 1e-4 / 30 it
 //   l1-Jacobi (Eq. 5-6, nb = 1)      -- two-level constant K = 5.6220 (Table 1)
 //   V-cycle (Eq. 2)                  -- dense error-propagation product; SPD
 //   PCG                              -- dense Cholesky solve of A
+//   flexible CG (FCG(1))             -- equals PCG for a fixed SPD preconditioner
 // Nothing here is "parity unpinned".
 #include <algorithm>
 #include <cmath>
@@ -266,6 +269,7 @@ struct Level {
 struct Hierarchy {
     std::vector<Level> lev;
     int nc = 0;                    // coarsest size
+    int coarse_cg = 0;             // 1: coarsest level solved by CG (too large for the dense factor)
     std::vector<double> L;         // dense Cholesky factor, column-major nc x nc
     int pre = 1, post = 1;
     double omega = 1.0;
@@ -333,7 +337,7 @@ void cholesky_solve(const std::vector<double>& L, int n, const double* b, double
 // new level has at most max_coarse rows, when a level brings no reduction, or
 // at max_levels levels; the last level is solved by dense Cholesky.
 int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps, int max_coarse,
-          int max_levels) {
+          int max_levels, double min_ratio, int max_dense) {
     H.lev.clear();
     H.lev.push_back(Level{});
     H.lev[0].A = A0;
@@ -369,11 +373,17 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
         Level next;
         next.A = std::move(A);
         next.w = std::move(w);
+        const double ratio = (double)cur.A.n / (double)next.A.n;
         H.lev.push_back(std::move(next));
+        if (ratio < min_ratio) break;              // coarsening has stalled: stop here
     }
     for (auto& L : H.lev) L.minv = l1_jacobi_inverse(L.A);
     const Csr& Ac = H.lev.back().A;
     H.nc = Ac.n;
+    if (Ac.n > max_dense) {
+        H.coarse_cg = 1;
+        return 0;
+    }
     if (!dense_cholesky(Ac, H.L)) return -2;
     return 0;
 }
@@ -394,13 +404,48 @@ void smooth(const Level& L, double omega, const double* b, double* x) {
     for (int i = 0; i < L.A.n; ++i) x[i] = x[i] + (omega * L.minv[i]) * (b[i] - r[i]);
 }
 
+double dot(const double* a, const double* b, int n);
+
+// Coarsest solve when the level is too large for the dense factor: CG with
+// the l1-Jacobi preconditioner from x = 0 to ||r|| <= 1e-4 ||b|| or 30
+// iterations, the coarsest-solver setting of Section 5 (with a Jacobi-type
+// preconditioner in place of block-Jacobi ILU(0)).
+void coarse_cg(const Level& L, const double* b, double* x) {
+    const int n = L.A.n;
+    std::vector<double> r(b, b + n), z(n), p(n), q(n);
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    const double nb = std::sqrt(dot(b, b, n));
+    if (nb == 0.0) return;
+    for (int i = 0; i < n; ++i) z[i] = L.minv[i] * r[i];
+    p = z;
+    double rho = dot(r.data(), z.data(), n);
+    for (int it = 0; it < 30; ++it) {
+        spmv(L.A, p.data(), q.data());
+        const double alpha = rho / dot(p.data(), q.data(), n);
+        for (int i = 0; i < n; ++i) {
+            x[i] = x[i] + alpha * p[i];
+            r[i] = r[i] - alpha * q[i];
+        }
+        if (std::sqrt(dot(r.data(), r.data(), n)) <= 1e-4 * nb) break;
+        for (int i = 0; i < n; ++i) z[i] = L.minv[i] * r[i];
+        const double rho_new = dot(r.data(), z.data(), n);
+        const double beta = rho_new / rho;
+        for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rho = rho_new;
+    }
+}
+
 // B_l b for the V-cycle of Eq. 2: pre-smoothing from a zero guess, coarse
 // correction with the restricted residual, post-smoothing; the coarsest level
 // is solved exactly.
 void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const Level& L = H.lev[l];
     const int n = L.A.n;
-    if (l == (int)H.lev.size() - 1) { cholesky_solve(H.L, H.nc, b, x); return; }
+    if (l == (int)H.lev.size() - 1) {
+        if (H.coarse_cg) coarse_cg(L, b, x);
+        else cholesky_solve(H.L, H.nc, b, x);
+        return;
+    }
     for (int i = 0; i < n; ++i) x[i] = 0.0;
     for (int s = 0; s < H.pre; ++s) smooth(L, H.omega, b, x);
     std::vector<double> r(n);
@@ -424,12 +469,15 @@ double dot(const double* a, const double* b, int n) {
 // a fixed s.p.d. preconditioner). Iterations count products A p. Convergence
 // on ||r|| <= rtol ||b|| with the recursive residual; at that point the true
 // residual b - A x is formed and, if it is not below rtol, the iteration
-// restarts from it. Returns 0 converged, 1 not converged, -6 breakdown.
-int pcg(const Hierarchy& H, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
-        double* true_relres) {
+// restarts from it. flexible != 0 gives flexible CG keeping one previous
+// direction (FCG(1), the outer solver of Section 5): beta = z'^T (r' - r) /
+// (z^T r), with the previous residual kept. Returns 0 converged,
+// 1 not converged, -6 breakdown.
+int pcg(const Hierarchy& H, const double* b, double* x, double rtol, int maxit, int flexible, int* iters,
+        double* relres, double* true_relres) {
     const Level& L0 = H.lev[0];
     const int n = L0.A.n;
-    std::vector<double> r(n), z(n), p(n), q(n);
+    std::vector<double> r(n), z(n), p(n), q(n), r_old;
     double nb = std::sqrt(dot(b, b, n));
     *iters = 0;
     if (nb == 0.0) {
@@ -457,6 +505,7 @@ int pcg(const Hierarchy& H, const double* b, double* x, double rtol, int maxit, 
         double pq = dot(p.data(), q.data(), n);
         if (!(pq > 0.0) || !std::isfinite(rho)) { status = -6; break; }
         double alpha = rho / pq;
+        if (flexible) r_old = r;
         for (int i = 0; i < n; ++i) {
             x[i] = x[i] + alpha * p[i];
             r[i] = r[i] - alpha * q[i];
@@ -475,6 +524,11 @@ int pcg(const Hierarchy& H, const double* b, double* x, double rtol, int maxit, 
         vcycle(H, 0, r.data(), z.data());
         double rho_new = dot(r.data(), z.data(), n);
         double beta = rho_new / rho;
+        if (flexible) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s = s + z[i] * (r[i] - r_old[i]);
+            beta = s / rho;
+        }
         for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         rho = rho_new;
     }
@@ -543,7 +597,8 @@ int orc_match_ld(int n, const int32_t* ptr, const int32_t* col, const double* va
 // matching (same result, also records the round counts). Returns a handle or
 // null; *status receives 0 or a negative code.
 void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
-                int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, int* status) {
+                int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
+                int max_dense, int* status) {
     Csr A = make_csr(n, ptr, col, val);
     int e = validate(A);
     for (int i = 0; e == 0 && i < n; ++i)
@@ -551,7 +606,7 @@ void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val
     if (e) { *status = e; return nullptr; }
     Hierarchy* H = new Hierarchy;
     H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld;
-    e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels);
+    e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels, min_ratio, max_dense);
     *status = e;
     if (e) { delete H; return nullptr; }
     return H;
@@ -607,6 +662,8 @@ void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* 
     std::copy(pw.wc.begin(), pw.wc.end(), wc);
 }
 
+int orc_coarse_is_cg(void* h) { return static_cast<Hierarchy*>(h)->coarse_cg; }
+
 void orc_coarse_factor(void* h, double* L) {
     const Hierarchy* H = static_cast<Hierarchy*>(h);
     std::copy(H->L.begin(), H->L.end(), L);
@@ -620,9 +677,9 @@ void orc_vcycle_level(void* h, int l, const double* r, double* z) {
     vcycle(*static_cast<Hierarchy*>(h), l, r, z);
 }
 
-int orc_pcg(void* h, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+int orc_pcg(void* h, const double* b, double* x, double rtol, int maxit, int flexible, int* iters, double* relres,
             double* true_relres) {
-    return pcg(*static_cast<Hierarchy*>(h), b, x, rtol, maxit, iters, relres, true_relres);
+    return pcg(*static_cast<Hierarchy*>(h), b, x, rtol, maxit, flexible, iters, relres, true_relres);
 }
 
 }  // extern "C"

@@ -48,7 +48,8 @@ class amg_options(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
-                ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):
@@ -61,7 +62,7 @@ class amg_hier_info(ctypes.Structure):
                 ("nnz", ctypes.c_int64 * MAX_LEVELS), ("sweeps_done", ctypes.c_int * MAX_LEVELS),
                 ("rounds", (ctypes.c_int * MAX_SWEEPS) * MAX_LEVELS), ("opc", ctypes.c_double),
                 ("avg_coarsening_ratio", ctypes.c_double), ("setup_ms", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("coarse_solver", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
 
 
 class AmgError(RuntimeError):
@@ -227,7 +228,7 @@ def amg_hierarchy_info(h: Hierarchy) -> dict:
                 sweeps_done=[inf.sweeps_done[i] for i in range(nl)],
                 rounds=[[inf.rounds[i][s] for s in range(inf.sweeps_done[i])] for i in range(nl)],
                 opc=inf.opc, avg_coarsening_ratio=inf.avg_coarsening_ratio, setup_ms=inf.setup_ms,
-                device_bytes=inf.device_bytes)
+                coarse_solver=inf.coarse_solver, device_bytes=inf.device_bytes)
 
 
 def amg_export_level(h: Hierarchy, level: int) -> dict:

@@ -89,13 +89,18 @@ struct DevCsr {
 // SELL-32 (sliced ELLPACK, slice height 32, no row sorting): slice s holds
 // rows 32s..32s+31; its entries start at sptr[s] and are stored column-major
 // inside the slice (entry k of lane r at sptr[s] + 32k + r). Short rows are
-// padded with (col = the row's last column, val = 0).
+// padded with (col = the row's last column, val = 0). When identity slicing
+// would pad more than 30%, rows are sorted by length inside windows of 256
+// (SELL-C-sigma) and perm maps slice positions to rows.
 constexpr int SELL_C = 32;
 struct DevSell {
     int n = 0;
     int nslices = 0;
     int64_t padded = 0;
-    int* sptr = nullptr;   // nslices + 1, in entries
+    int* sptr = nullptr;   // nslices + 1, in units of 32 entries
+    int* perm = nullptr;   // row held by each slice position (SELL-C-sigma); null: identity
+    int nlong = 0;         // hybrid layout only: rows kept out of the slices (read from the CSR)
+    int* long_rows = nullptr;
     int* col = nullptr;
     double* val = nullptr;
     float* val32 = nullptr;
@@ -147,6 +152,14 @@ struct PcgScalars {
     int pad;
 };
 
+// Workspace of the iterative coarsest solve (coarsest level above max_dense).
+struct CoarseCg {
+    int blocks = 0;
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double* part = nullptr;   // 2 buffers x 2 slots x blocks
+    int* ctl = nullptr;       // [0] barrier arrivals, [1] error
+};
+
 struct Reducer {
     double* partial = nullptr;   // one slot per block
     unsigned* ticket = nullptr;  // last-block counter
@@ -164,6 +177,8 @@ struct amg_hierarchy {
     amg::DevArena mem;
     std::vector<amg::Level> lev;
     int nc = 0;                 // coarsest size
+    int coarse_cg = 0;          // 1: coarsest solved by CG (above max_dense)
+    amg::CoarseCg ccg;
     double* coarse_L = nullptr;  // dense Cholesky factor (column-major)
     double* coarse_inv = nullptr;// dense inverse A_L^{-1} (row-major)
     // PCG workspace (level 0 sized)

@@ -55,7 +55,7 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     else amg_options_default(&o);
     if (o.sweeps < 1 || o.sweeps > AMG_MAX_SWEEPS || o.max_levels < 1 || o.max_coarse < 1 || o.pre < 0 ||
         o.post < 0 || !(o.omega > 0.0) || (o.precision != AMG_FP64 && o.precision != AMG_FP32_VCYCLE) ||
-        o.max_dense < 1)
+        o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0))
         return fail(AMG_ERR_ARG, "invalid options");
     amg_hierarchy* h = new amg_hierarchy;
     h->opt = o;
@@ -95,6 +95,8 @@ void amg_options_default(amg_options* o) {
     o->keep_sweeps = 0;
     o->profile = 0;
     o->match_kernel = 0;
+    o->krylov = 0;
+    o->min_ratio = 1.5;
     o->stream = nullptr;
 }
 
@@ -177,6 +179,7 @@ amg_status amg_hierarchy_info(const amg_hierarchy* h, amg_hier_info* out) {
     out->opc = sum / (double)h->lev[0].A.nnz;
     out->avg_coarsening_ratio = nl > 1 ? cr / (nl - 1) : 0.0;
     out->setup_ms = h->setup_ms;
+    out->coarse_solver = h->coarse_cg;
     out->device_bytes = h->mem.bytes;
     return AMG_OK;
 }
@@ -234,6 +237,7 @@ amg_status amg_export_sweep(const amg_hierarchy* h, int level, int sweep, int32_
 
 amg_status amg_coarse_factor(const amg_hierarchy* h, double* L) {
     if (!h || !L) return fail(AMG_ERR_ARG, "null argument");
+    if (h->coarse_cg) return fail(AMG_ERR_ARG, "the coarsest level is solved by CG; there is no dense factor");
     amg_hierarchy* hh = const_cast<amg_hierarchy*>(h);
     std::lock_guard<std::mutex> g(hh->lock);
     return guarded([&]() -> amg_status {

@@ -581,29 +581,35 @@ __global__ void k_to_float(long long n, const double* __restrict__ a, float* __r
 
 // ------------------------------------------------------------ SELL-32 ------
 // width[s] = longest row of slice s.
-__global__ void k_sell_width(int n, int nslices, const int* __restrict__ ptr, int* __restrict__ width) {
+__global__ void k_sell_width(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ perm,
+                             int* __restrict__ width) {
     const int lane = threadIdx.x & 31;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
          t += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(t >> 5);
-        const int i = (int)t;
-        const int len = i < n ? ptr[i + 1] - ptr[i] : 0;
+        const int ip = (int)t;
+        const int i = ip < n ? (perm ? perm[ip] : ip) : 0;
+        const int len = ip < n ? ptr[i + 1] - ptr[i] : 0;
         const int m = warp_max_int(len);
         if (lane == 0) width[s] = m;
     }
 }
 
 __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ col,
-                            const double* __restrict__ val, const int* __restrict__ sptr, int* __restrict__ scol,
-                            double* __restrict__ sval) {
+                            const double* __restrict__ val, const int* __restrict__ sptr,
+                            const int* __restrict__ perm, int* __restrict__ scol, double* __restrict__ sval) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
          t += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(t >> 5), lane = (int)(t & 31);
-        const int i = (int)t;
+        const int ip = (int)t;
         const int width = sptr[s + 1] - sptr[s];
         long long pos = (long long)sptr[s] * 32 + lane;
         int len = 0, b = 0;
-        if (i < n) { b = ptr[i]; len = ptr[i + 1] - b; }
+        if (ip < n) {
+            const int i = perm ? perm[ip] : ip;
+            b = ptr[i];
+            len = ptr[i + 1] - b;
+        }
         // padding repeats the row's last column (a valid index of this
         // matrix's column space, also for rectangular A P) with value 0
         const int pad = len > 0 ? col[b + len - 1] : 0;
@@ -611,6 +617,46 @@ __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, con
             if (k < len) { scol[pos] = col[b + k]; sval[pos] = val[b + k]; }
             else { scol[pos] = pad; sval[pos] = 0.0; }
         }
+    }
+}
+
+// SELL-C-sigma row order: inside each window of SIGMA consecutive rows, rows
+// by decreasing length (ties by index), so a slice holds rows of similar
+// length. One block of SIGMA threads per window, bitonic sort in shared memory.
+constexpr int SIGMA = 256;
+__global__ void __launch_bounds__(SIGMA) k_sort_window(int n, const int* __restrict__ rows, const int* __restrict__ ptr,
+                                                      int* __restrict__ perm) {
+    __shared__ long long key[SIGMA];
+    const int t = threadIdx.x;
+    const int it = blockIdx.x * SIGMA + t;
+    const int i = it < n ? (rows ? rows[it] : it) : 0;
+    // key: larger length first, then smaller row index; items past n sort last
+    key[t] = it < n ? ((long long)(0x7fffffff - (ptr[i + 1] - ptr[i])) << 32) | (unsigned)i : 0x7fffffffffffffffLL;
+    __syncthreads();
+    for (int k = 2; k <= SIGMA; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int o = t ^ j;
+            if (o > t) {
+                const bool up = (t & k) == 0;
+                const long long a = key[t], b = key[o];
+                if ((a > b) == up) { key[t] = b; key[o] = a; }
+            }
+            __syncthreads();
+        }
+    }
+    if (it < n) perm[it] = (int)(key[t] & 0xffffffffLL);
+}
+
+// Rows longer than lmax are listed in long_rows (kept rows in short_rows).
+__global__ void k_long_flags(int n, const int* __restrict__ ptr, int lmax, int* __restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = (ptr[i + 1] - ptr[i]) > lmax ? 1 : 0;
+}
+__global__ void k_split_rows(int n, const int* __restrict__ flag, const int* __restrict__ pos,
+                             int* __restrict__ long_rows, int* __restrict__ short_rows) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (flag[i]) long_rows[pos[i]] = i;
+        else short_rows[i - pos[i]] = i;
     }
 }
 
@@ -837,21 +883,68 @@ void build_sell(amg_hierarchy* h, const DevCsr& A, DevSell& E, Scratch& S, bool 
     E.n = A.n;
     E.nslices = (A.n + SELL_C - 1) / SELL_C;
     E.sptr = h->mem.alloc<int>(E.nslices + 1);
-    k_sell_width<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(A.n, E.nslices, A.ptr,
-                                                                                             S.ub);
+    const int wgrid = blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16);
+    k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, nullptr, S.ub);
     KERNEL_CHECK();
     scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
     E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
+    if ((double)E.padded > 1.3 * (double)A.nnz) {
+        // uneven rows: sort by length inside windows (SELL-C-sigma)
+        E.perm = h->mem.alloc<int>(A.n);
+        k_sort_window<<<(A.n + SIGMA - 1) / SIGMA, SIGMA, 0, st>>>(A.n, nullptr, A.ptr, E.perm);
+        KERNEL_CHECK();
+        k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, E.perm, S.ub);
+        KERNEL_CHECK();
+        scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
+        E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
+    }
     E.col = h->mem.alloc<int>(E.padded);
     E.val = h->mem.alloc<double>(E.padded);
     k_sell_fill<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-        A.n, E.nslices, A.ptr, A.col, A.val, E.sptr, E.col, E.val);
+        A.n, E.nslices, A.ptr, A.col, A.val, E.sptr, E.perm, E.col, E.val);
     KERNEL_CHECK();
     if (fp32) {
         E.val32 = h->mem.alloc<float>(E.padded);
         k_to_float<<<blocks_for(E.padded, TPB, h->num_sms * 16), TPB, 0, st>>>(E.padded, E.val, E.val32);
         KERNEL_CHECK();
     }
+}
+
+// Hybrid layout for the iterative coarsest solve: rows with at most lmax
+// entries in SELL-C-sigma (positions map to rows through perm), longer rows
+// listed in long_rows and read straight from the CSR by one warp each, so a
+// few long rows cannot hold up a whole slice.
+void build_sell_hybrid(amg_hierarchy* h, const DevCsr& A, DevSell& E, Scratch& S, int lmax) {
+    cudaStream_t st = h->stream;
+    const int n = A.n;
+    k_long_flags<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, lmax, S.flag);
+    KERNEL_CHECK();
+    scan_exclusive(S.flag, S.qid, n, S.cnt + 6, st, S.scan_tmp);
+    const int nlong = read_int(S.cnt + 6, S.host, st);
+    const int nshort = n - nlong;
+    E.nlong = nlong;
+    E.long_rows = h->mem.alloc<int>(nlong > 0 ? nlong : 1);
+    int* short_rows = S.mem.alloc<int>(nshort > 0 ? nshort : 1);
+    k_split_rows<<<grid_for(h, n), TPB, 0, st>>>(n, S.flag, S.qid, E.long_rows, short_rows);
+    KERNEL_CHECK();
+    E.n = nshort;
+    E.nslices = (nshort + SELL_C - 1) / SELL_C;
+    E.sptr = h->mem.alloc<int>(E.nslices + 1);
+    E.perm = h->mem.alloc<int>(nshort > 0 ? nshort : 1);
+    k_sort_window<<<(nshort + SIGMA - 1) / SIGMA > 0 ? (nshort + SIGMA - 1) / SIGMA : 1, SIGMA, 0, st>>>(
+        nshort, short_rows, A.ptr, E.perm);
+    KERNEL_CHECK();
+    const int wgrid = blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16);
+    k_sell_width<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, E.perm, S.ub);
+    KERNEL_CHECK();
+    scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
+    E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
+    E.col = h->mem.alloc<int>(E.padded);
+    E.val = h->mem.alloc<double>(E.padded);
+    k_sell_fill<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, A.col, A.val, E.sptr, E.perm, E.col, E.val);
+    KERNEL_CHECK();
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    S.mem.release(short_rows);
 }
 
 // Column-scaled values of A M^{-1} in A's SELL layout (padding stays 0).
@@ -1061,6 +1154,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         next.A = A;
         next.w = w;
         h->lev.push_back(std::move(next));
+        if ((double)nl / (double)A.n < o.min_ratio) break;   // coarsening has stalled: stop here
     }
 
     // ---- per-level solve data: smoother, SELL copies, member lists
@@ -1077,7 +1171,9 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             KERNEL_CHECK();
         }
         Scope sc_(&h->prof, st, S_FORMAT, 24.0 * L.A.nnz);
-        if (l == 0 || l < nlev - 1) build_sell(h, L.A, L.S, S, fp32);
+        const bool coarsest_cg = l == nlev - 1 && L.A.n > o.max_dense;
+        if (coarsest_cg && l > 0) build_sell_hybrid(h, L.A, L.S, S, 32);
+        else if (l == 0 || l < nlev - 1 || coarsest_cg) build_sell(h, L.A, L.S, S, fp32);
         if (l == nlev - 1) break;
         build_scaled(h, L, fp32);
         build_members(h, L, h->lev[l + 1].A.n, S);
@@ -1093,9 +1189,12 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     {
         Level& Lc = h->lev.back();
         const int nc = Lc.A.n;
-        if (nc > o.max_dense)
-            AMG_THROW(AMG_ERR_TOO_LARGE, "coarsest level has %d rows, above max_dense = %d", nc, o.max_dense);
         h->nc = nc;
+        h->coarse_cg = nc > o.max_dense ? 1 : 0;
+    }
+    if (!h->coarse_cg) {
+        Level& Lc = h->lev.back();
+        const int nc = Lc.A.n;
         Scope sc_(&h->prof, st, S_COARSE, 0.0);
         double* D = S.mem.alloc<double>((size_t)nc * nc);
         double* Y = S.mem.alloc<double>((size_t)nc * nc);

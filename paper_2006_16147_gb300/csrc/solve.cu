@@ -26,7 +26,9 @@ namespace {
 constexpr int TPB = 256;
 constexpr int WARPS = TPB / 32;
 
-enum FinMode : int { FIN_NORMS = 0, FIN_PQ = 1, FIN_RR = 2, FIN_RHO_INIT = 3, FIN_RHO_UPDATE = 4, FIN_NONE = 5 };
+enum FinMode : int {
+    FIN_NORMS = 0, FIN_PQ = 1, FIN_RR = 2, FIN_RHO_INIT = 3, FIN_RHO_UPDATE = 4, FIN_NONE = 5, FIN_RHO_UPDATE_FCG = 6
+};
 
 __device__ void finish(int mode, double a, double b, PcgScalars* sc) {
     switch (mode) {
@@ -42,6 +44,16 @@ __device__ void finish(int mode, double a, double b, PcgScalars* sc) {
         case FIN_RHO_INIT: sc->rho = a; if (!isfinite(a)) sc->breakdown = 1; break;
         case FIN_RHO_UPDATE: {
             const double beta = a / sc->rho;
+            sc->rho_new = a;
+            sc->beta = beta;
+            sc->rho = a;
+            if (!isfinite(beta)) sc->breakdown = 1;
+            break;
+        }
+        case FIN_RHO_UPDATE_FCG: {
+            // flexible CG, one direction kept: beta = z'^T (r' - r) / rho with
+            // r' - r = -alpha q, so beta = -alpha (z' . q) / rho  (b = z' . q)
+            const double beta = -sc->alpha * b / sc->rho;
             sc->rho_new = a;
             sc->beta = beta;
             sc->rho = a;
@@ -84,7 +96,11 @@ struct SellView {
     int n, nslices;
     const int* __restrict__ sptr;
     const int* __restrict__ col;
+    const int* __restrict__ perm;   // row held by slice position (null: identity)
 };
+
+// Row index held by SELL position ip (rows may be permuted by length).
+__device__ __forceinline__ int sell_rowid(const SellView& S, int ip) { return S.perm ? __ldg(S.perm + ip) : ip; }
 
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
@@ -128,8 +144,9 @@ __global__ void __launch_bounds__(TPB) k_pre(SellView S, const T* __restrict__ v
     SELL_LOOP(S) {
         const T acc = sell_row(S.col, valm, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                [&](int j) { return (T)ld(b + j); });
-        const int i = s * 32 + lane;
-        if (i < S.n) {
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
             const T bi = (T)b[i];
             x[i] = (omega * minv[i]) * bi;
             r[i] = fma(-omega, acc, bi);
@@ -161,20 +178,25 @@ __global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict_
                                               T omega, const int* __restrict__ agg, const T* __restrict__ p,
                                               const T* __restrict__ e, const T* __restrict__ x,
                                               const T* __restrict__ r, const TB* __restrict__ bdot,
-                                              TO* __restrict__ out, Reducer red, PcgScalars* sc, int mode) {
-    double dot = 0.0;
+                                              TO* __restrict__ out, Reducer red, PcgScalars* sc, int mode,
+                                              const double* __restrict__ q2) {
+    double dot = 0.0, dot2 = 0.0;
     SELL_LOOP(SAP) {
         const T acc = sell_row(SAP.col, apval, (long long)SAP.sptr[s] * 32 + lane, SAP.sptr[s + 1] - SAP.sptr[s],
                                [&](int q) { return ld(e + q); });
-        const int i = s * 32 + lane;
-        if (i < SAP.n) {
+        const int ip = s * 32 + lane;
+        if (ip < SAP.n) {
+            const int i = sell_rowid(SAP, ip);
             const T yi = fma(p[i], e[agg[i]], x[i]);
             const T o = fma(omega * minv[i], r[i] - acc, yi);
             out[i] = (TO)o;
-            if (DOT) dot = fma((double)bdot[i], (double)(TO)o, dot);
+            if (DOT) {
+                dot = fma((double)bdot[i], (double)(TO)o, dot);
+                if (q2) dot2 = fma(q2[i], (double)(TO)o, dot2);
+            }
         }
     }
-    if (DOT) reduce_and_finish(dot, 0.0, red, sc, mode);
+    if (DOT) reduce_and_finish(dot, dot2, red, sc, mode);
 }
 
 // Extra pre-smoothing sweep from (x, r = b - A x):
@@ -187,8 +209,9 @@ __global__ void __launch_bounds__(TPB) k_pre_step(SellView S, const T* __restric
     SELL_LOOP(S) {
         const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                [&](int j) { return fma(omega * ld(minv + j), ld(rin + j), ld(xin + j)); });
-        const int i = s * 32 + lane;
-        if (i < S.n) {
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
             xout[i] = fma(omega * minv[i], rin[i], xin[i]);
             rout[i] = (T)b[i] - acc;
         }
@@ -203,16 +226,23 @@ __global__ void __launch_bounds__(TPB) k_smooth(SellView S, const T* __restrict_
     SELL_LOOP(S) {
         const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                [&](int j) { return ld(yin + j); });
-        const int i = s * 32 + lane;
-        if (i < S.n) yout[i] = (TO)fma(omega * minv[i], (T)b[i] - acc, yin[i]);
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
+            yout[i] = (TO)fma(omega * minv[i], (T)b[i] - acc, yin[i]);
+        }
     }
 }
 
+// a . b and, if c is given, b . c.
 __global__ void __launch_bounds__(TPB) k_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
-                                             Reducer red, PcgScalars* sc, int mode) {
-    double d = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) d = fma(a[i], b[i], d);
-    reduce_and_finish(d, 0.0, red, sc, mode);
+                                             const double* __restrict__ c, Reducer red, PcgScalars* sc, int mode) {
+    double d = 0.0, d2 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        d = fma(a[i], b[i], d);
+        if (c) d2 = fma(b[i], c[i], d2);
+    }
+    reduce_and_finish(d, d2, red, sc, mode);
 }
 
 // x = A_L^{-1} b on the coarsest level, in FP64 whatever T is.
@@ -232,6 +262,149 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* 
     }
 }
 
+
+// ------------------------------------- iterative coarsest solve (large n_L)
+// When the coarsest level is too large for the dense factor, it is solved
+// with CG preconditioned by l1-Jacobi from x = 0 to ||r|| <= rtol ||b|| or
+// maxit iterations, all in FP64 and in one cooperative launch. Scalars are
+// block partials written to a double buffer; after each grid barrier every
+// block sums the partials in the same order, so all blocks hold identical
+// scalars without a broadcast step. Waits are bounded (2 s).
+__device__ __forceinline__ unsigned long long cg_global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned cg_ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cg_grid_sync(unsigned* count, unsigned epoch, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned target = epoch * gridDim.x;
+        const unsigned long long t0 = cg_global_ns();
+        while (cg_ld_acquire(count) < target) {
+            if (cg_global_ns() - t0 > 2000000000ull) { atomicExch(err, 1); break; }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Sum of the G block partials of slot k in buffer `buf`, same order in every block.
+__device__ __forceinline__ double cg_sum(const double* part, int G) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) s += __ldcg(part + k);
+    return block_sum(s);
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(512) k_coarse_cg(SellView S, const double* __restrict__ val, int n,
+                                                   int nlong, const int* __restrict__ long_rows,
+                                                   const int* __restrict__ cptr, const int* __restrict__ ccol,
+                                                   const double* __restrict__ cval,
+                                                   const double* __restrict__ minv, const TI* __restrict__ b,
+                                                   TO* __restrict__ xout, double* x, double* r, double* z, double* p,
+                                                   double* q, double* part, unsigned* bar, int* err, int maxit,
+                                                   double rtol) {
+    const int G = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = G * blockDim.x;
+    unsigned epoch = 0;
+    int red = 0;   // reduction counter: buffer = red & 1, two slots per buffer
+    auto slot = [&](int k) { return part + (size_t)((red & 1) * 2 + k) * G; };
+    double a = 0.0, c = 0.0;
+    for (int i = tid; i < n; i += stride) {
+        const double bi = (double)b[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        const double zi = minv[i] * bi;
+        z[i] = zi;
+        p[i] = zi;
+        a = fma(bi, zi, a);
+        c = fma(bi, bi, c);
+    }
+    a = block_sum(a);
+    c = block_sum(c);
+    if (threadIdx.x == 0) { slot(0)[blockIdx.x] = a; slot(1)[blockIdx.x] = c; }
+    cg_grid_sync(bar, ++epoch, err);
+    if (__ldcg(err)) return;
+    double rho = cg_sum(slot(0), G);
+    const double bb = cg_sum(slot(1), G);
+    ++red;
+    if (bb > 0.0) {
+        const double stop2 = rtol * rtol * bb;
+        for (int it = 0; it < maxit; ++it) {
+            // q = A p, p . q
+            double pq = 0.0;
+            const int lane = threadIdx.x & 31, nw = G * (blockDim.x >> 5);
+            for (int sl = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sl < S.nslices; sl += nw) {
+                const double acc = sell_row(S.col, val, (long long)S.sptr[sl] * 32 + lane, S.sptr[sl + 1] - S.sptr[sl],
+                                            [&](int j) { return __ldcg(p + j); });
+                const int ip = sl * 32 + lane;
+                if (ip < S.n) {
+                    const int i = sell_rowid(S, ip);
+                    q[i] = acc;
+                    pq = fma(__ldcg(p + i), acc, pq);
+                }
+            }
+            // long rows: one warp per row, straight from the CSR
+            for (int lr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); lr < nlong; lr += nw) {
+                const int i = __ldg(long_rows + lr);
+                double acc = 0.0;
+                for (int k = __ldg(cptr + i) + lane; k < __ldg(cptr + i + 1); k += 32)
+                    acc = fma(__ldg(cval + k), __ldcg(p + __ldg(ccol + k)), acc);
+                acc = warp_sum(acc);
+                if (lane == 0) {
+                    q[i] = acc;
+                    pq = fma(__ldcg(p + i), acc, pq);
+                }
+            }
+            pq = block_sum(pq);
+            if (threadIdx.x == 0) slot(0)[blockIdx.x] = pq;
+            cg_grid_sync(bar, ++epoch, err);
+            if (__ldcg(err)) return;
+            const double alpha = rho / cg_sum(slot(0), G);
+            ++red;
+            double rr = 0.0;
+            for (int i = tid; i < n; i += stride) {
+                x[i] = fma(alpha, __ldcg(p + i), x[i]);
+                const double ri = fma(-alpha, __ldcg(q + i), r[i]);
+                r[i] = ri;
+                rr = fma(ri, ri, rr);
+            }
+            rr = block_sum(rr);
+            if (threadIdx.x == 0) slot(0)[blockIdx.x] = rr;
+            cg_grid_sync(bar, ++epoch, err);
+            if (__ldcg(err)) return;
+            const double rr_all = cg_sum(slot(0), G);
+            ++red;
+            if (rr_all <= stop2) break;
+            double rz = 0.0;
+            for (int i = tid; i < n; i += stride) {
+                const double zi = minv[i] * r[i];
+                z[i] = zi;
+                rz = fma(r[i], zi, rz);
+            }
+            rz = block_sum(rz);
+            if (threadIdx.x == 0) slot(0)[blockIdx.x] = rz;
+            cg_grid_sync(bar, ++epoch, err);
+            if (__ldcg(err)) return;
+            const double rho_new = cg_sum(slot(0), G);
+            ++red;
+            const double beta = rho_new / rho;
+            rho = rho_new;
+            for (int i = tid; i < n; i += stride) p[i] = fma(beta, p[i], z[i]);
+            cg_grid_sync(bar, ++epoch, err);
+            if (__ldcg(err)) return;
+        }
+    }
+    for (int i = tid; i < n; i += stride) xout[i] = (TO)x[i];
+}
+
 // ------------------------------------------------------------- PCG ---------
 // r = b - A x; ||r||^2 and ||b||^2.
 __global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __restrict__ val,
@@ -241,8 +414,9 @@ __global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __re
     SELL_LOOP(S) {
         const double acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                     [&](int j) { return ld(x + j); });
-        const int i = s * 32 + lane;
-        if (i < S.n) {
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
             const double bi = b[i];
             const double ri = bi - acc;
             r[i] = ri;
@@ -261,8 +435,9 @@ __global__ void __launch_bounds__(TPB) k_spmv_dot(SellView S, const double* __re
     SELL_LOOP(S) {
         const double acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                     [&](int j) { return ld(p + j); });
-        const int i = s * 32 + lane;
-        if (i < S.n) {
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
             q[i] = acc;
             pq = fma(p[i], acc, pq);
         }
@@ -306,7 +481,7 @@ double by_restrict(int n, int nc, int V) { return (double)n * (4 + 2.0 * V) + (d
 double by_smooth(const Level& L, int V, int Vb, int Vo) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (2.0 * V + Vb + Vo); }
 double by_coarse(int nc, int Vi, int Vo) { return 8.0 * nc * nc + (double)nc * (Vi + Vo); }
 
-SellView view(const Level& L) { return SellView{L.S.n, L.S.nslices, L.S.sptr, L.S.col}; }
+SellView view(const Level& L) { return SellView{L.S.n, L.S.nslices, L.S.sptr, L.S.col, L.S.perm}; }
 
 int sell_grid(const amg_hierarchy* h, int nslices) {
     int g = (nslices + WARPS - 1) / WARPS;
@@ -321,6 +496,32 @@ int red_grid(const amg_hierarchy* h) { return h->red.blocks; }
 
 void coarse_solve_launch(amg_hierarchy* h, const void* b, void* x, bool fp32_in, bool fp64_out) {
     const int n = h->nc;
+    if (h->coarse_cg) {
+        Level& Lc = h->lev.back();
+        CoarseCg& C = h->ccg;
+        Scope sc_(&h->prof, h->stream, K_COARSE, 8.0 * 30 * (3.0 * Lc.A.nnz + 10.0 * n));
+        CUDA_CHECK(cudaMemsetAsync(C.ctl, 0, sizeof(int) * 4, h->stream));
+        SellView S{Lc.S.n, Lc.S.nslices, Lc.S.sptr, Lc.S.col, Lc.S.perm};
+        const double* val = Lc.S.val;
+        int nrows = Lc.A.n;
+        int nlong = Lc.S.nlong;
+        const int* long_rows = Lc.S.long_rows;
+        const int* cptr = Lc.A.ptr;
+        const int* ccol = Lc.A.col;
+        const double* cval = Lc.A.val;
+        const double* minv = Lc.minv;
+        unsigned* bar = reinterpret_cast<unsigned*>(C.ctl);
+        int* err = C.ctl + 1;
+        int maxit = 30;
+        double rtol = 1e-4;
+        void* args[] = {&S, &val, &nrows, &nlong, &long_rows, &cptr, &ccol, &cval, &minv, const_cast<void**>(&b), &x,
+                        &C.x, &C.r, &C.z, &C.p, &C.q, &C.part, &bar, &err, &maxit, &rtol};
+        const void* fn = !fp32_in ? (const void*)k_coarse_cg<double, double>
+                                  : (fp64_out ? (const void*)k_coarse_cg<float, double> : (const void*)k_coarse_cg<float, float>);
+        CUDA_CHECK(cudaLaunchCooperativeKernel(fn, dim3(C.blocks), dim3(512), args, 0, h->stream));
+        KERNEL_CHECK();
+        return;
+    }
     const int threads = 256;
     int grid = (n + (threads / 32) - 1) / (threads / 32);
     if (grid > h->num_sms * 2) grid = h->num_sms * 2;
@@ -339,6 +540,7 @@ void coarse_solve_launch(amg_hierarchy* h, const void* b, void* x, bool fp32_in,
 template <typename T>
 void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     cudaStream_t st = h->stream;
+    const double* q2 = rz_mode == FIN_RHO_UPDATE_FCG ? h->q : nullptr;
     const int L = (int)h->lev.size() - 1;
     const bool f32 = sizeof(T) == 4;
     const T omega = (T)h->opt.omega;
@@ -347,7 +549,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         coarse_solve_launch(h, r, z, false, true);
         if (rz_mode != FIN_NONE) {
             Scope sc_(&h->prof, st, K_DOT, 16.0 * n0);
-            k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, h->red, h->sc, rz_mode);
+            k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, q2, h->red, h->sc, rz_mode);
             KERNEL_CHECK();
         }
         return;
@@ -407,7 +609,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     for (int l = L - 1; l >= 0; --l) {
         Level& Lv = h->lev[l];
         const SellView S = view(Lv);
-        const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col};
+        const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col, Lv.AP.perm};
         const int g = sell_grid(h, S.nslices);
         const T* e = out[l + 1];
         const int nc = h->lev[l + 1].A.n;
@@ -416,7 +618,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             {
                 Scope sc_(&h->prof, st, K_POST, by_post2(Lv, nc, V, V, false));
                 k_post<T, T, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[l],
-                                                          rcur[l], (const T*)nullptr, ya, h->red, h->sc, FIN_NONE);
+                                                          rcur[l], (const T*)nullptr, ya, h->red, h->sc, FIN_NONE,
+                                                          nullptr);
                 KERNEL_CHECK();
             }
             for (int k = 1; k < post; ++k) {
@@ -432,17 +635,19 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, 8, rz_mode != FIN_NONE));
             if (rz_mode != FIN_NONE)
                 k_post<T, double, double, true><<<red_grid(h), TPB, 0, st>>>(
-                    SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[0], rcur[0], r, z, h->red, h->sc, rz_mode);
+                    SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[0], rcur[0], r, z, h->red, h->sc, rz_mode, q2);
             else
                 k_post<T, double, double, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
-                                                                   xcur[0], rcur[0], r, z, h->red, h->sc, FIN_NONE);
+                                                                   xcur[0], rcur[0], r, z, h->red, h->sc, FIN_NONE,
+                                                                   nullptr);
             KERNEL_CHECK();
         } else {
             T *ya = vec(Lv, VY), *yb = spare[0];
             {
                 Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, V, false));
                 k_post<T, double, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
-                                                              xcur[0], rcur[0], r, ya, h->red, h->sc, FIN_NONE);
+                                                              xcur[0], rcur[0], r, ya, h->red, h->sc, FIN_NONE,
+                                                              nullptr);
                 KERNEL_CHECK();
             }
             for (int k = 1; k < post - 1; ++k) {
@@ -458,7 +663,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             }
             if (rz_mode != FIN_NONE) {
                 Scope sc_(&h->prof, st, K_DOT, 16.0 * n0);
-                k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, h->red, h->sc, rz_mode);
+                k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, q2, h->red, h->sc, rz_mode);
                 KERNEL_CHECK();
             }
         }
@@ -495,6 +700,21 @@ void prepare_solve(amg_hierarchy* h) {
             L.y = h->mem.alloc<double>(n);
             if (extra) { L.t = h->mem.alloc<double>(n); L.u = h->mem.alloc<double>(n); }
         }
+    }
+    if (h->coarse_cg) {
+        const int nc = h->lev.back().A.n;
+        CoarseCg& C = h->ccg;
+        int per_sm = 0;
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_cg<double, double>, 512, 0));
+        if (per_sm < 1) AMG_THROW(AMG_ERR_CUDA, "coarsest CG kernel cannot be resident");
+        C.blocks = h->num_sms;
+        C.x = h->mem.alloc<double>(nc);
+        C.r = h->mem.alloc<double>(nc);
+        C.z = h->mem.alloc<double>(nc);
+        C.p = h->mem.alloc<double>(nc);
+        C.q = h->mem.alloc<double>(nc);
+        C.part = h->mem.alloc<double>(4 * (size_t)C.blocks);
+        C.ctl = h->mem.alloc<int>(4);
     }
     const int n0 = h->lev[0].A.n;
     h->r = h->mem.alloc<double>(n0);
@@ -589,7 +809,7 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             ++inf.restarts;
             continue;
         }
-        vcycle_dispatch(h, h->r, h->z, FIN_RHO_UPDATE);
+        vcycle_dispatch(h, h->r, h->z, h->opt.krylov == 1 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
         Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
         k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
         KERNEL_CHECK();

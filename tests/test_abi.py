@@ -56,9 +56,10 @@ def test_struct_layouts_match_c():
 #include <stddef.h>
 #include "amg.h"
 int main(void){
- printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(amg_csr), sizeof(amg_options), offsetof(amg_options, omega),
+ printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(amg_csr), sizeof(amg_options), offsetof(amg_options, omega),
         offsetof(amg_options, stream), sizeof(amg_solve_info), sizeof(amg_hier_info),
-        offsetof(amg_options, keep_sweeps), offsetof(amg_options, profile), offsetof(amg_hier_info, opc));
+        offsetof(amg_options, keep_sweeps), offsetof(amg_options, profile), offsetof(amg_hier_info, opc),
+        offsetof(amg_options, min_ratio), offsetof(amg_hier_info, device_bytes));
  return 0;}
 '''
     import tempfile
@@ -70,5 +71,6 @@ int main(void){
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(amg.amg_csr), ctypes.sizeof(amg.amg_options), amg.amg_options.omega.offset,
             amg.amg_options.stream.offset, ctypes.sizeof(amg.amg_solve_info), ctypes.sizeof(amg.amg_hier_info),
-            amg.amg_options.keep_sweeps.offset, amg.amg_options.profile.offset, amg.amg_hier_info.opc.offset]
+            amg.amg_options.keep_sweeps.offset, amg.amg_options.profile.offset, amg.amg_hier_info.opc.offset,
+            amg.amg_options.min_ratio.offset, amg.amg_hier_info.device_bytes.offset]
     assert got == want

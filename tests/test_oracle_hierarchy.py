@@ -166,3 +166,44 @@ def test_paper_table1_convergence_constant(orc):
     assert abs(K(Mbar) - gold["HGS"][0]) <= gold["HGS"][1]
     Ml1 = np.diag(1.0 / lv.minv)          # the oracle's l1-Jacobi matrix
     assert abs(K(Ml1) - gold["l1-Jacobi"][0]) <= gold["l1-Jacobi"][1]
+
+
+def _star(n, seed=0):
+    # hub 0 joined to every leaf, leaves not joined to each other; SPD by
+    # diagonal dominance. Any matching of a star has exactly one pair.
+    rng = np.random.default_rng(seed)
+    d = np.zeros((n, n))
+    off = -rng.uniform(0.1, 1.0, n - 1)
+    d[0, 1:] = off
+    d[1:, 0] = off
+    d[0, 0] = np.abs(off).sum() + 1.0
+    d[np.arange(1, n), np.arange(1, n)] = np.abs(off) + rng.uniform(0.5, 1.0, n - 1)
+    rows, cols = np.nonzero(d)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return W.Csr(np.cumsum(rp), cols, d[rows, cols])
+
+
+def test_stalled_coarsening_stops(orc):
+    A = _star(300)
+    H = orc.Hierarchy(A, max_coarse=10, sweeps=1)
+    # one sweep matches one pair: 300 -> 299 is a ratio below 1.5, so the
+    # second level is the last one
+    assert [s[0] for s in H.sizes()] == [300, 299]
+    H = orc.Hierarchy(A, max_coarse=10, sweeps=1, min_ratio=1.0)
+    assert H.num_levels > 2
+    # the Laplacian's ratio of 8 is far from the stall rule
+    assert [s[0] for s in orc.Hierarchy(W.poisson3d(32)).sizes()] == [32768, 4096, 512, 64]
+
+
+def test_coarsest_cg_reaches_its_tolerance(orc):
+    # coarsest level above max_dense: CG with l1-Jacobi to 1e-4 (Section 5's
+    # coarsest-solver setting); on a single level B b is that CG's result
+    A = W.poisson3d(10)
+    H = orc.Hierarchy(A, max_coarse=2000, max_dense=100)
+    assert H.num_levels == 1 and H.coarse_is_cg
+    b = np.random.default_rng(3).normal(size=A.n)
+    x = H.vcycle(b)
+    assert np.linalg.norm(b - A.scipy() @ x) <= 1e-4 * np.linalg.norm(b)
+    # and it is a CG iterate, not the exact solution
+    assert np.linalg.norm(b - A.scipy() @ x) > 1e-10 * np.linalg.norm(b)

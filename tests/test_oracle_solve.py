@@ -111,3 +111,18 @@ def test_pcg_config1_exact_solution_ones(orc):
     assert info["status"] == 0 and info["true_relres"] <= 1e-6
     assert np.abs(x - xs).max() <= 442 * 1e-6 * np.sqrt(A.n)
     assert 5 <= info["iterations"] <= 60
+
+
+@pytest.mark.parametrize("name,mk,seed", CASES)
+def test_flexible_cg_equals_pcg_for_fixed_preconditioner(orc, name, mk, seed):
+    # With a fixed s.p.d. preconditioner z'^T r = 0 in exact arithmetic, so
+    # FCG(1)'s beta equals PCG's and the iterates coincide up to rounding.
+    A = mk()
+    H = orc.Hierarchy(A, _w(A, seed), max_coarse=8)
+    b = np.random.default_rng(2).normal(size=A.n)
+    x1, i1 = H.pcg(b, rtol=1e-10)
+    x2, i2 = H.pcg(b, rtol=1e-10, flexible=True)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert abs(i1["iterations"] - i2["iterations"]) <= 1
+    xd = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(x2 - xd) <= 1e-8 * np.linalg.norm(xd)
