@@ -138,6 +138,20 @@ amg_status amg_solve(amg_hierarchy* h, const double* b, double* x, double rtol, 
 amg_status amg_solve_host(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
                           amg_solve_info* info);
 
+/*
+ * Several right-hand sides at once: B and X are DEVICE arrays, row-major n x k
+ * (entry (i, c) at i*k + c), 1 <= k <= 256. Every column runs its own PCG
+ * (or flexible CG) with the V-cycle of Eq. 2 to ||b_c - A x_c|| <= rtol ||b_c||;
+ * the sparse products and the V-cycle serve all columns in one pass over the
+ * matrices. X holds the initial guesses on entry. infos (host, k entries, may
+ * be NULL) receives each column's iterations and true relative residual.
+ * Needs a hierarchy with at least two levels and pre = post = 1.
+ * Returns AMG_OK when every column converged, AMG_NOT_CONVERGED otherwise,
+ * AMG_ERR_BREAKDOWN if a column broke down.
+ */
+amg_status amg_solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
+                           amg_solve_info* infos);
+
 /* One application of the preconditioner, z = B r (Eq. 2), device pointers of length n. */
 amg_status amg_vcycle(amg_hierarchy* h, const double* r, double* z);
 

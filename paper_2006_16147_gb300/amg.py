@@ -33,7 +33,7 @@ EXPORTED = [
     "amg_options_default", "amg_setup", "amg_setup_host", "amg_solve", "amg_solve_host", "amg_vcycle",
     "amg_hierarchy_info", "amg_export_level", "amg_sweep_dims", "amg_export_sweep", "amg_coarse_factor",
     "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
-    "amg_launch_count", "amg_match_noalloc",
+    "amg_launch_count", "amg_match_noalloc", "amg_solve_batch",
 ]
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_NNZ = 524288
@@ -95,6 +95,9 @@ def lib() -> ctypes.CDLL:
             f = getattr(L, name)
             f.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(amg_solve_info)]
             f.restype = ctypes.c_int
+        L.amg_solve_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(amg_solve_info)]
+        L.amg_solve_batch.restype = ctypes.c_int
         L.amg_vcycle.argtypes = [_vp, _vp, _vp]
         L.amg_vcycle.restype = ctypes.c_int
         L.amg_hierarchy_info.argtypes = [_vp, ctypes.POINTER(amg_hier_info)]
@@ -214,6 +217,14 @@ def amg_solve_host(h: Hierarchy, b: np.ndarray, x: np.ndarray, rtol: float = 1e-
     inf = amg_solve_info()
     st = _check(lib().amg_solve_host(h.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(inf)))
     return _info_dict(inf, st)
+
+
+def amg_solve_batch(h: Hierarchy, B, X, rtol: float = 1e-6, maxit: int = 1000) -> list:
+    """Block solve of row-major n x k device tensors B (read) and X (x0 in, solution out)."""
+    k = int(B.shape[1])
+    infos = (amg_solve_info * k)()
+    st = _check(lib().amg_solve_batch(h.handle, k, _ptr(B), _ptr(X), float(rtol), int(maxit), infos))
+    return [dict(_info_dict(infos[c], st)) for c in range(k)]
 
 
 def amg_vcycle(h: Hierarchy, r, z) -> None:

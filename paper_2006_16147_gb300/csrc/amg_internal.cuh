@@ -160,6 +160,35 @@ struct CoarseCg {
     int* ctl = nullptr;       // [0] barrier arrivals, [1] error
 };
 
+// Column states of a block (multi right-hand side) solve.
+enum ColMode : int { COL_IDLE = 0, COL_START = 1, COL_ACTIVE = 2, COL_CHECK = 3, COL_DONE = 4, COL_FAILED = 5 };
+
+// Per-column scalars of a block solve, device arrays of length K.
+struct BlockScalars {
+    int* mode;
+    int* iters;
+    double *rho, *alpha, *beta, *pq, *rr, *bb, *rtol;
+};
+
+// Workspace of a block solve with K column slots (all arrays row-major n x K).
+struct BlockWork {
+    int K = 0;
+    int maxit_guard = 0;
+    DevArena mem;
+    std::vector<void*> b, x, r, y;      // per level V-cycle vectors (float or double)
+    double *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // level 0, FP64
+    BlockScalars sc{};
+    int* mode_host = nullptr;           // pinned mirrors
+    int* iters_host = nullptr;
+    double* rr_host = nullptr;
+    double* bb_host = nullptr;
+    double* partial = nullptr;          // grid x K x 2
+    unsigned* ticket = nullptr;
+    int grid = 0;
+    double *cb = nullptr, *cx = nullptr; // coarse CG column staging (coarsest size)
+    ~BlockWork();
+};
+
 struct Reducer {
     double* partial = nullptr;   // one slot per block
     unsigned* ticket = nullptr;  // last-block counter
@@ -186,6 +215,7 @@ struct amg_hierarchy {
     amg::PcgScalars* sc = nullptr;      // device
     amg::PcgScalars* sc_host = nullptr; // pinned mirror
     amg::Reducer red;
+    amg::BlockWork* blk = nullptr;      // block-solve workspace, created on first use
     double setup_ms = 0.0;
     amg::Profiler prof;
     std::mutex lock;
@@ -212,6 +242,12 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* A, const double* w);
 void prepare_solve(amg_hierarchy* h);
 amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info);
 void vcycle_apply(amg_hierarchy* h, const double* r, double* z);
+// Single-column coarsest CG solve on contiguous FP64 vectors (coarse_cg hierarchies).
+void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x);
+// Block (multi right-hand side) solve.
+amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
+                       amg_solve_info* infos);
+void block_free(amg_hierarchy* h);
 amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds_out);
 
 }  // namespace amg

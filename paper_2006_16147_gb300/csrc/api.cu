@@ -152,6 +152,19 @@ amg_status amg_solve_host(amg_hierarchy* h, const double* b, double* x, double r
     });
 }
 
+amg_status amg_solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
+                           amg_solve_info* infos) {
+    if (!h || !B || !X) return fail(AMG_ERR_ARG, "null argument");
+    if (!(rtol > 0.0) || maxit < 0 || k < 1) return fail(AMG_ERR_ARG, "bad k, rtol or maxit");
+    std::lock_guard<std::mutex> g(h->lock);
+    return guarded([&]() -> amg_status {
+        bind_device(h);
+        amg_status s = amg::solve_batch(h, k, B, X, rtol, maxit, infos);
+        if (s == AMG_ERR_BREAKDOWN) amg::set_last_error("CG breakdown in at least one column");
+        return s;
+    });
+}
+
 amg_status amg_vcycle(amg_hierarchy* h, const double* r, double* z) {
     if (!h || !r || !z) return fail(AMG_ERR_ARG, "null argument");
     std::lock_guard<std::mutex> g(h->lock);
@@ -254,6 +267,7 @@ void amg_free(amg_hierarchy* h) {
         cudaSetDevice(h->device);
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
+        amg::block_free(h);
         h->mem.free_all();
         if (h->sc_host) cudaFreeHost(h->sc_host);
         h->sc_host = nullptr;

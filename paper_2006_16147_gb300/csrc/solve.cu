@@ -732,6 +732,8 @@ void prepare_solve(amg_hierarchy* h) {
     CUDA_CHECK(cudaStreamSynchronize(h->stream));
 }
 
+void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x) { coarse_solve_launch(h, b, x, false, true); }
+
 void vcycle_apply(amg_hierarchy* h, const double* r, double* z) {
     vcycle_dispatch(h, r, z, FIN_NONE);
     CUDA_CHECK(cudaStreamSynchronize(h->stream));

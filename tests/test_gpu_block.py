@@ -1,0 +1,99 @@
+"""Block (multi right-hand side) solves: every column against the oracle's
+single-column PCG, and every column alone against the same column in a batch."""
+import numpy as np
+import pytest
+
+from paper_2006_16147_gb300 import workloads as W
+
+from gpu_util import dev, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _batch(h, B, X0=None, rtol=1e-6, maxit=500):
+    import torch
+    from paper_2006_16147_gb300 import amg
+    Bd = dev(B)
+    Xd = dev(np.zeros_like(B) if X0 is None else X0)
+    infos = amg.amg_solve_batch(h, Bd, Xd, rtol=rtol, maxit=maxit)
+    torch.cuda.synchronize()
+    return Xd.cpu().numpy(), infos
+
+
+@pytest.mark.parametrize("k", [1, 3, 16, 64])
+def test_block_columns_match_oracle(orc, k):
+    A = W.poisson3d(24, 22, 20)
+    B = W.rhs_normal(A.n, 4, k)
+    H = orc.Hierarchy(A)
+    h = setup(A)
+    X, infos = _batch(h, B)
+    S = A.scipy()
+    for c in range(k):
+        xo, io = H.pcg(B[:, c], rtol=1e-6)
+        assert infos[c]["status"] == 0 and infos[c]["true_relres"] <= 1e-6
+        assert abs(infos[c]["iterations"] - io["iterations"]) <= 1
+        if infos[c]["iterations"] == io["iterations"]:
+            assert np.linalg.norm(X[:, c] - xo) <= 1e-10 * np.linalg.norm(xo)
+        assert np.linalg.norm(B[:, c] - S @ X[:, c]) <= 1e-6 * np.linalg.norm(B[:, c])
+    h.close()
+
+
+@pytest.mark.parametrize("precision,krylov", [(1, 0), (1, 1), (0, 1)])
+def test_block_fp32_and_flexible(orc, precision, krylov):
+    A = W.varcoef3d(24, seed=2)
+    B = W.rhs_normal(A.n, 5, 8)
+    H = orc.Hierarchy(A)
+    h = setup(A, precision=precision, krylov=krylov)
+    X, infos = _batch(h, B, rtol=1e-8)
+    S = A.scipy()
+    for c in range(8):
+        xo, io = H.pcg(B[:, c], rtol=1e-8, flexible=bool(krylov))
+        assert np.linalg.norm(B[:, c] - S @ X[:, c]) <= 1e-8 * np.linalg.norm(B[:, c])
+        assert infos[c]["iterations"] <= io["iterations"] + (2 if precision else 1)
+    h.close()
+
+
+def test_block_with_iterative_coarsest(orc):
+    A = W.varcoef3d(32, seed=2)
+    B = W.rhs_normal(A.n, 6, 4)
+    H = orc.Hierarchy(A, max_dense=100)
+    h = setup(A, max_dense=100, krylov=1)
+    X, infos = _batch(h, B, rtol=1e-8)
+    for c in range(4):
+        xo, io = H.pcg(B[:, c], rtol=1e-8, flexible=True)
+        assert infos[c]["true_relres"] <= 1e-8
+        assert abs(infos[c]["iterations"] - io["iterations"]) <= 1
+    h.close()
+
+
+def test_column_alone_equals_column_in_batch(orc):
+    # the result of a right-hand side must not depend on what it is batched with
+    A = W.poisson3d(20)
+    B = W.rhs_normal(A.n, 7, 16)
+    h = setup(A)
+    Xb, ib = _batch(h, B)
+    for c in (0, 5, 15):
+        Xa, ia = _batch(h, B[:, c:c + 1].copy())
+        assert abs(ia[0]["iterations"] - ib[c]["iterations"]) <= 1
+        assert np.linalg.norm(Xa[:, 0] - Xb[:, c]) <= 1e-10 * np.linalg.norm(Xb[:, c])
+    h.close()
+
+
+def test_zero_columns_and_initial_guess(orc):
+    A = W.poisson3d(16)
+    B = W.rhs_normal(A.n, 8, 5)
+    B[:, 2] = 0.0
+    X0 = np.ones_like(B)
+    h = setup(A)
+    X, infos = _batch(h, B, X0=X0)
+    assert not X[:, 2].any() and infos[2]["iterations"] == 0
+    for c in (0, 1, 3, 4):
+        assert infos[c]["true_relres"] <= 1e-6
+    h.close()
