@@ -47,6 +47,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-grid", type=int, default=128)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: 5 cached hierarchies, Poisson arrivals, p50/p99 latency and solves/s")
+    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-scale", type=float, default=1.0,
+                    help="grid scale factor of the served problems (1.0 = 64^3/128^3/192^3/2048^2/128^3)")
     return ap.parse_args()
 
 
@@ -168,10 +173,147 @@ def reference_arm(args):
     return 0
 
 
+def serve_arm(args):
+    """Served mixed-precision solves vs plain FP64 one-at-a-time FIFO.
+
+    Five cached hierarchies: Poisson 64^3, 128^3, 192^3; anisotropic 2D
+    -u_xx - 0.01 u_yy on 2048^2; jump coefficients 128^3. Requests pick a
+    hierarchy uniformly and bring k ~ U{1..16} right-hand sides N(0, 1).
+    Arrivals are Poisson at 50/80/95% of the measured capacity of the plain
+    FP64 server (one request at a time, one column at a time). Latency is
+    arrival to completion; solves/s counts right-hand sides.
+    """
+    import torch
+    from paper_2006_16147_gb300 import amg
+    from paper_2006_16147_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    sc = args.serve_scale
+    g = lambda v: max(8, int(round(v * sc)))
+    specs = [("poisson3d_%d" % g(64), lambda: W.poisson3d(g(64)), 0),
+             ("poisson3d_%d" % g(128), lambda: W.poisson3d(g(128)), 0),
+             ("poisson3d_%d" % g(192), lambda: W.poisson3d(g(192)), 0),
+             ("aniso2d_%d_eps1e-2" % g(2048), lambda: W.poisson2d_aniso(g(2048), g(2048), 1e-2), 0),
+             ("varcoef3d_%d_sigma2" % g(128), lambda: W.varcoef3d(g(128), seed=2), 1)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    mats, h64, h32, pools = [], [], [], []
+    rng = np.random.Generator(np.random.PCG64(6))
+    for name, mk, flex in specs:
+        A = mk()
+        mats.append(A)
+        args_dev = (t(A.row_ptr), t(A.col), t(A.val), torch.ones(A.n, dtype=torch.float64, device=dev))
+        h64.append(amg.amg_setup(*args_dev, precision=0, krylov=flex))
+        h32.append(amg.amg_setup(*args_dev, precision=1, krylov=flex))
+        pool = torch.from_numpy(rng.normal(0.0, 1.0, size=(A.n, 16))).pin_memory().numpy()
+        pools.append(pool)
+    torch.cuda.synchronize()
+    rtol = args.rtol
+
+    nreq = args.serve_requests
+    req_h = rng.integers(0, len(specs), size=nreq)
+    req_k = rng.integers(1, 17, size=nreq)
+    blocks = [np.ascontiguousarray(pools[h][:, :k]) for h, k in zip(req_h, req_k)]
+
+    def plain_solve(hid, B):
+        X = np.zeros_like(B)
+        it = 0
+        for c in range(B.shape[1]):
+            b = torch.from_numpy(np.ascontiguousarray(B[:, c])).to(dev)
+            x = torch.zeros_like(b)
+            inf = amg.amg_solve(h64[hid], b, x, rtol=rtol, maxit=2000)
+            X[:, c] = x.cpu().numpy()
+            it = max(it, inf["iterations"])
+        return X
+
+    # capacity of the plain server (columns per second), requests back to back
+    warm = min(5, nreq)
+    for j in range(warm):
+        plain_solve(int(req_h[j]), blocks[j])
+    t0 = time.perf_counter()
+    ncap = min(20, nreq)
+    cols = 0
+    for j in range(ncap):
+        plain_solve(int(req_h[j]), blocks[j])
+        cols += int(req_k[j])
+    capacity = cols / (time.perf_counter() - t0)
+    mean_k = float(np.mean(req_k))
+
+    def run_plain(arrivals):
+        lat = []
+        t_start = time.perf_counter()
+        free_at = 0.0
+        for j in range(nreq):
+            now = time.perf_counter() - t_start
+            if now < arrivals[j]:
+                time.sleep(arrivals[j] - now)
+            plain_solve(int(req_h[j]), blocks[j])
+            done = time.perf_counter() - t_start
+            lat.append((done - arrivals[j]) * 1e3)
+        elapsed = time.perf_counter() - t_start
+        return lat, elapsed
+
+    def run_served(arrivals, srv):
+        t_start = time.perf_counter()
+        j = 0
+        lat = {}
+        sub_t = {}
+        results = {}
+        while len(results) < nreq:
+            now = time.perf_counter() - t_start
+            while j < nreq and arrivals[j] <= now:
+                rid, X = srv.submit(int(req_h[j]), blocks[j])
+                sub_t[rid] = arrivals[j]
+                j += 1
+            pending = srv.step()
+            now2 = time.perf_counter() - t_start
+            for r in srv.poll():
+                results[r["id"]] = r
+                lat[r["id"]] = (now2 - sub_t[r["id"]]) * 1e3
+            if pending == 0 and j < nreq:
+                time.sleep(max(0.0, arrivals[j] - (time.perf_counter() - t_start)))
+        elapsed = time.perf_counter() - t_start
+        worst = max(r["relres"] for r in results.values())
+        return list(lat.values()), elapsed, worst
+
+    out = []
+    for load in (0.5, 0.8, 0.95):
+        lam = load * capacity / mean_k
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=nreq))
+        arr -= arr[0]
+        lp, ep = run_plain(arr)
+        srv = amg.Server(h32, slots=16, budget_bytes=120 << 30, rtol=rtol, maxit=2000)
+        ls, es, worst = run_served(arr, srv)
+        st = srv.stats()
+        srv.close()
+        q = lambda v, f: float(np.percentile(v, f))
+        out.append({"load": load, "arrival_rate_req_s": lam,
+                    "plain_fp64": {"p50_ms": q(lp, 50), "p99_ms": q(lp, 99), "solves_per_s": int(req_k.sum()) / ep},
+                    "served_fp32vcycle": {"p50_ms": q(ls, 50), "p99_ms": q(ls, 99),
+                                          "solves_per_s": int(req_k.sum()) / es, "worst_true_relres": worst,
+                                          "steps": st["steps"], "peak_bytes": st["peak_bytes"]}})
+    # throughput with every request queued at once (saturated server)
+    srv = amg.Server(h32, slots=16, budget_bytes=120 << 30, rtol=rtol, maxit=2000)
+    ls, es, worst = run_served(np.zeros(nreq), srv)
+    srv.close()
+    line = {"metric": "served solves/s and p50/p99 latency (continuous batching, FP32 V-cycle in FP64 CG)",
+            "value": int(req_k.sum()) / es, "unit": "solves/s", "higher_is_better": True,
+            "plain_fp64_capacity_solves_per_s": capacity, "requests": nreq, "mean_rhs_per_request": mean_k,
+            "hierarchies": [s[0] for s in specs], "rtol": rtol, "loads": out,
+            "saturated": {"solves_per_s": int(req_k.sum()) / es, "p50_ms": float(np.percentile(ls, 50)),
+                          "p99_ms": float(np.percentile(ls, 99)), "worst_true_relres": worst},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    for h in h64 + h32:
+        h.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serve:
+        return serve_arm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -226,6 +226,53 @@ int64_t amg_launch_count(void);
 #define AMG_NOALLOC_MAX_NNZ 524288
 amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds);
 
+/*
+ * Solve server with continuous batching over cached hierarchies. The paper
+ * reuses one preconditioner for many solves (Sections 1 and 5); the server
+ * keeps several hierarchies resident and serves right-hand sides for them.
+ *
+ * amg_serve_create takes nh hierarchies (they must outlive the server, which
+ * runs each on a stream of its own until amg_serve_free), `slots` column
+ * slots per hierarchy (1..256; the largest request), a device-memory budget
+ * in bytes for the columns in flight, and the tolerance / iteration limit of
+ * every solve. A hierarchy's workspace for `slots` columns is allocated here.
+ *
+ * amg_serve_submit queues a request of k right-hand sides for hierarchy hid:
+ * B and X are HOST arrays, row-major n x k, that must stay valid until the
+ * request completes (X receives the solutions, started from 0). Requests of
+ * one hierarchy are admitted in arrival order when enough slots are free and
+ * the budget allows; larger requests than the budget return AMG_ERR_BUDGET.
+ *
+ * amg_serve_step admits what fits, advances every hierarchy with columns in
+ * flight by one CG iteration (hierarchies overlap on their own streams),
+ * copies finished columns to their X and frees their slots; *pending gets the
+ * number of columns still in flight or queued. A column's arithmetic does not
+ * depend on the other columns in flight, so a request's result is the same
+ * whether it was served alone or in a mix.
+ *
+ * amg_serve_poll returns up to max completed requests (id, status, latency
+ * from submit to completion in ms, iterations, worst true relative residual);
+ * any output pointer may be NULL. amg_serve_stats fills latency percentiles
+ * and throughput over all completed requests.
+ */
+typedef struct amg_server amg_server;
+typedef struct {
+    int64_t submitted, completed, steps, columns_completed;
+    double p50_ms, p99_ms, mean_ms;
+    double columns_per_s;   /* right-hand sides completed per second, first submit to last completion */
+    double elapsed_s;
+    size_t budget_bytes, peak_bytes;
+} amg_serve_stats;
+
+amg_status amg_serve_create(int nh, amg_hierarchy* const* hs, int slots, size_t budget_bytes, double rtol, int maxit,
+                            amg_server** out);
+amg_status amg_serve_submit(amg_server* s, int hid, int k, const double* B, double* X, int64_t* id);
+amg_status amg_serve_step(amg_server* s, int64_t* pending);
+int amg_serve_poll(amg_server* s, int64_t* ids, int* statuses, double* latency_ms, int* iterations, double* relres,
+                   int max);
+amg_status amg_serve_stats_get(amg_server* s, amg_serve_stats* out);
+void amg_serve_free(amg_server* s);
+
 /* Releases every device allocation of h. NULL is accepted. */
 void amg_free(amg_hierarchy* h);
 

@@ -33,7 +33,8 @@ EXPORTED = [
     "amg_options_default", "amg_setup", "amg_setup_host", "amg_solve", "amg_solve_host", "amg_vcycle",
     "amg_hierarchy_info", "amg_export_level", "amg_sweep_dims", "amg_export_sweep", "amg_coarse_factor",
     "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
-    "amg_launch_count", "amg_match_noalloc", "amg_solve_batch",
+    "amg_launch_count", "amg_match_noalloc", "amg_solve_batch", "amg_serve_create", "amg_serve_submit",
+    "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free",
 ]
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_NNZ = 524288
@@ -63,6 +64,13 @@ class amg_hier_info(ctypes.Structure):
                 ("rounds", (ctypes.c_int * MAX_SWEEPS) * MAX_LEVELS), ("opc", ctypes.c_double),
                 ("avg_coarsening_ratio", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("coarse_solver", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+class amg_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("columns_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("columns_per_s", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+                ("budget_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t)]
 
 
 class AmgError(RuntimeError):
@@ -98,6 +106,20 @@ def lib() -> ctypes.CDLL:
         L.amg_solve_batch.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int,
                                       ctypes.POINTER(amg_solve_info)]
         L.amg_solve_batch.restype = ctypes.c_int
+        L.amg_serve_create.argtypes = [ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t,
+                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.amg_serve_create.restype = ctypes.c_int
+        L.amg_serve_submit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64p]
+        L.amg_serve_submit.restype = ctypes.c_int
+        L.amg_serve_step.argtypes = [_vp, _i64p]
+        L.amg_serve_step.restype = ctypes.c_int
+        L.amg_serve_poll.argtypes = [_vp, _i64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.amg_serve_poll.restype = ctypes.c_int
+        L.amg_serve_stats_get.argtypes = [_vp, ctypes.POINTER(amg_serve_stats)]
+        L.amg_serve_stats_get.restype = ctypes.c_int
+        L.amg_serve_free.argtypes = [_vp]
+        L.amg_serve_free.restype = None
         L.amg_vcycle.argtypes = [_vp, _vp, _vp]
         L.amg_vcycle.restype = ctypes.c_int
         L.amg_hierarchy_info.argtypes = [_vp, ctypes.POINTER(amg_hier_info)]
@@ -313,3 +335,58 @@ def amg_match_noalloc(row_ptr, col, val, w, mate, stream=None) -> int:
     st = _current_stream() if stream is None else stream
     _check(lib().amg_match_noalloc(ctypes.byref(A), _ptr(w), _ptr(mate), ctypes.c_void_p(st), ctypes.byref(rounds)))
     return rounds.value
+
+
+class Server:
+    """Continuous-batching solve server over cached hierarchies (amg_serve_*).
+
+    Host numpy arrays are kept referenced until their request completes.
+    """
+
+    def __init__(self, hierarchies, slots=16, budget_bytes=1 << 40, rtol=1e-6, maxit=1000):
+        arr = (ctypes.c_void_p * len(hierarchies))(*[h.handle for h in hierarchies])
+        out = ctypes.c_void_p()
+        _check(lib().amg_serve_create(len(hierarchies), arr, int(slots), int(budget_bytes), float(rtol), int(maxit),
+                                      ctypes.byref(out)))
+        self._s = out.value
+        self._hier = list(hierarchies)
+        self._live = {}
+
+    def submit(self, hid, B):
+        """Queue the columns of host array B (n x k); returns (id, X) with X filled at completion."""
+        B = np.ascontiguousarray(B if B.ndim == 2 else B[:, None], dtype=np.float64)
+        X = np.zeros_like(B)
+        rid = ctypes.c_int64()
+        _check(lib().amg_serve_submit(self._s, int(hid), int(B.shape[1]), _ptr(B), _ptr(X), ctypes.byref(rid)))
+        self._live[rid.value] = (B, X)
+        return rid.value, X
+
+    def step(self) -> int:
+        pending = ctypes.c_int64()
+        _check(lib().amg_serve_step(self._s, ctypes.byref(pending)))
+        return pending.value
+
+    def poll(self, max_items=256):
+        ids = (ctypes.c_int64 * max_items)()
+        st = (ctypes.c_int * max_items)()
+        lat = (ctypes.c_double * max_items)()
+        it = (ctypes.c_int * max_items)()
+        rel = (ctypes.c_double * max_items)()
+        n = lib().amg_serve_poll(self._s, ids, st, lat, it, rel, max_items)
+        out = []
+        for i in range(n):
+            B, X = self._live.pop(ids[i])
+            out.append(dict(id=ids[i], status=st[i], latency_ms=lat[i], iterations=it[i], relres=rel[i], X=X))
+        return out
+
+    def stats(self) -> dict:
+        s = amg_serve_stats()
+        _check(lib().amg_serve_stats_get(self._s, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in amg_serve_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().amg_serve_free(self._s)
+            self._s = None
+
+    __del__ = close

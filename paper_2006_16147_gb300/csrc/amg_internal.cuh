@@ -161,7 +161,9 @@ struct CoarseCg {
 };
 
 // Column states of a block (multi right-hand side) solve.
-enum ColMode : int { COL_IDLE = 0, COL_START = 1, COL_ACTIVE = 2, COL_CHECK = 3, COL_DONE = 4, COL_FAILED = 5 };
+enum ColMode : int {
+    COL_IDLE = 0, COL_START = 1, COL_ACTIVE = 2, COL_CHECK = 3, COL_DONE = 4, COL_FAILED = 5, COL_INIT = 6
+};
 
 // Per-column scalars of a block solve, device arrays of length K.
 struct BlockScalars {
@@ -173,7 +175,7 @@ struct BlockScalars {
 // Workspace of a block solve with K column slots (all arrays row-major n x K).
 struct BlockWork {
     int K = 0;
-    int maxit_guard = 0;
+    bool fixed_width = false;           // 32 lanes per row whatever the column count
     DevArena mem;
     std::vector<void*> b, x, r, y;      // per level V-cycle vectors (float or double)
     double *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // level 0, FP64
@@ -185,7 +187,9 @@ struct BlockWork {
     double* partial = nullptr;          // grid x K x 2
     unsigned* ticket = nullptr;
     int grid = 0;
-    double *cb = nullptr, *cx = nullptr; // coarse CG column staging (coarsest size)
+    double* cw[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // coarsest CG x, r, z, p, q (n_c x K)
+    double* cpart = nullptr;            // coarsest CG block partials
+    int* cctl = nullptr;                // [0] barrier arrivals, [1] error
     ~BlockWork();
 };
 
@@ -248,6 +252,24 @@ void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x);
 amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
                        amg_solve_info* infos);
 void block_free(amg_hierarchy* h);
+// Solve server (serve.cu).
+amg_server* serve_create(int nh, amg_hierarchy* const* hs, int K, size_t budget, double rtol, int maxit);
+void serve_free(amg_server* S);
+int64_t serve_submit(amg_server* S, int hid, int k, const double* B, double* X);
+int64_t serve_step(amg_server* S);
+int serve_poll(amg_server* S, int64_t* ids, int* statuses, double* latency_ms, int* iters, double* relres, int max);
+void serve_stats(amg_server* S, amg_serve_stats* o);
+// Pieces of a block solve for a scheduler (all launch-only on h->stream).
+BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width);
+size_t block_bytes_per_column(const amg_hierarchy* h);
+void block_set_columns(amg_hierarchy* h, int c0, int cnt, int mode, double rtol);
+void block_init_launch(amg_hierarchy* h, const double* B, double* X, int k);
+void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k);
+bool block_check_launch(amg_hierarchy* h, const double* B, double* X, int k);
+// Request staging for the server: scatter a contiguous n x k block into slot
+// columns (src null: zero them) / gather one slot column into column j of n x k.
+void block_scatter_request(amg_hierarchy* h, const double* src, int k, const int* slots, double* dst);
+void block_gather_column(amg_hierarchy* h, const double* src, int slot, double* dst, int k, int j);
 amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds_out);
 
 }  // namespace amg

@@ -307,6 +307,53 @@ amg_status amg_kernel_stats_reset(amg_hierarchy* h) {
 
 int64_t amg_launch_count(void) { return amg::launch_counter().load(); }
 
+amg_status amg_serve_create(int nh, amg_hierarchy* const* hs, int slots, size_t budget_bytes, double rtol, int maxit,
+                            amg_server** out) {
+    if (!out || nh < 1 || !hs || slots < 1 || slots > 256 || !(rtol > 0.0) || maxit < 1)
+        return fail(AMG_ERR_ARG, "bad server arguments");
+    *out = nullptr;
+    for (int i = 0; i < nh; ++i)
+        if (!hs[i]) return fail(AMG_ERR_ARG, "null hierarchy");
+    return guarded([&]() -> amg_status {
+        *out = amg::serve_create(nh, hs, slots, budget_bytes, rtol, maxit);
+        return AMG_OK;
+    });
+}
+
+amg_status amg_serve_submit(amg_server* s, int hid, int k, const double* B, double* X, int64_t* id) {
+    if (!s || !B || !X) return fail(AMG_ERR_ARG, "null argument");
+    return guarded([&]() -> amg_status {
+        const int64_t v = amg::serve_submit(s, hid, k, B, X);
+        if (id) *id = v;
+        return AMG_OK;
+    });
+}
+
+amg_status amg_serve_step(amg_server* s, int64_t* pending) {
+    if (!s) return fail(AMG_ERR_ARG, "null server");
+    return guarded([&]() -> amg_status {
+        const int64_t p = amg::serve_step(s);
+        if (pending) *pending = p;
+        return AMG_OK;
+    });
+}
+
+int amg_serve_poll(amg_server* s, int64_t* ids, int* statuses, double* latency_ms, int* iterations, double* relres,
+                   int max) {
+    if (!s || max < 1) return 0;
+    return amg::serve_poll(s, ids, statuses, latency_ms, iterations, relres, max);
+}
+
+amg_status amg_serve_stats_get(amg_server* s, amg_serve_stats* out) {
+    if (!s || !out) return fail(AMG_ERR_ARG, "null argument");
+    amg::serve_stats(s, out);
+    return AMG_OK;
+}
+
+void amg_serve_free(amg_server* s) {
+    if (s) amg::serve_free(s);
+}
+
 amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds) {
     if (!mate) return fail(AMG_ERR_ARG, "mate is null");
     amg_status s = check_csr(A, w);

@@ -135,21 +135,21 @@ __device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], co
 // ---------------------------------------------------------- V-cycle --------
 template <typename T, typename TB, int CPL>
 __global__ void __launch_bounds__(TPB) bk_pre(SellV S, const T* __restrict__ valm, const T* __restrict__ minv, T omega,
-                                              const TB* __restrict__ B, T* __restrict__ X, T* __restrict__ R, int k,
+                                              const TB* __restrict__ B, T* __restrict__ X, T* __restrict__ R, int k, int ld,
                                               int G) {
     const Grp g = make_grp(G);
     for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
         T acc[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) acc[m] = 0;
-        sell_row_k<T, CPL>(S, valm, ip, g, k, [&](int j, int c) { return (T)__ldg(B + (size_t)j * k + c); }, acc);
+        sell_row_k<T, CPL>(S, valm, ip, g, k, [&](int j, int c) { return (T)__ldg(B + (size_t)j * ld + c); }, acc);
         const int i = rowid(S, ip);
         const T mi = omega * minv[i];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
             if (c < k) {
-                const size_t o = (size_t)i * k + c;
+                const size_t o = (size_t)i * ld + c;
                 const T bi = (T)B[o];
                 X[o] = mi * bi;
                 R[o] = fma(-omega, acc[m], bi);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(TPB) bk_pre(SellV S, const T* __restrict__ val
 template <typename T, int CPL>
 __global__ void __launch_bounds__(TPB) bk_restrict(int nc, const int* __restrict__ pt_ptr,
                                                    const int* __restrict__ pt_idx, const T* __restrict__ p,
-                                                   const T* __restrict__ R, T* __restrict__ Bc, int k, int G) {
+                                                   const T* __restrict__ R, T* __restrict__ Bc, int k, int ld, int G) {
     const Grp g = make_grp(G);
     for (int q = g.gw; q < nc; q += g.ngroups) {
         T acc[CPL];
@@ -173,13 +173,13 @@ __global__ void __launch_bounds__(TPB) bk_restrict(int nc, const int* __restrict
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
                 const int c = g.gl + m * g.G;
-                if (c < k) acc[m] = fma(pi, __ldg(R + (size_t)i * k + c), acc[m]);
+                if (c < k) acc[m] = fma(pi, __ldg(R + (size_t)i * ld + c), acc[m]);
             }
         }
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
-            if (c < k) Bc[(size_t)q * k + c] = acc[m];
+            if (c < k) Bc[(size_t)q * ld + c] = acc[m];
         }
     }
 }
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(TPB) bk_restrict(int nc, const int* __restrict
 // X = A_L^{-1} B on the coarsest level, FP64 arithmetic.
 template <typename TI, typename TO, int CPL>
 __global__ void __launch_bounds__(TPB) bk_coarse_dense(int n, const double* __restrict__ Ainv, const TI* __restrict__ B,
-                                                       TO* __restrict__ X, int k, int G) {
+                                                       TO* __restrict__ X, int k, int ld, int G) {
     const Grp g = make_grp(G);
     for (int i = g.gw; i < n; i += g.ngroups) {
         double acc[CPL];
@@ -199,25 +199,15 @@ __global__ void __launch_bounds__(TPB) bk_coarse_dense(int n, const double* __re
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
                 const int c = g.gl + m * g.G;
-                if (c < k) acc[m] = fma(a, (double)__ldg(B + (size_t)j * k + c), acc[m]);
+                if (c < k) acc[m] = fma(a, (double)__ldg(B + (size_t)j * ld + c), acc[m]);
             }
         }
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
-            if (c < k) X[(size_t)i * k + c] = (TO)acc[m];
+            if (c < k) X[(size_t)i * ld + c] = (TO)acc[m];
         }
     }
-}
-
-// Column c of a row-major n x k array to / from a contiguous FP64 vector.
-template <typename T>
-__global__ void bk_gather_col(int n, const T* __restrict__ A, int k, int c, double* __restrict__ v) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = (double)A[(size_t)i * k + c];
-}
-template <typename T>
-__global__ void bk_scatter_col(int n, const double* __restrict__ v, int k, int c, T* __restrict__ A) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) A[(size_t)i * k + c] = (T)v[i];
 }
 
 // r . z finisher: START columns take rho and beta = 0 and become ACTIVE;
@@ -243,7 +233,7 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
                                                T omega, const int* __restrict__ agg, const T* __restrict__ p,
                                                const T* __restrict__ E, const T* __restrict__ X,
                                                const T* __restrict__ R, const double* __restrict__ Bdot,
-                                               const double* __restrict__ Q2, TO* __restrict__ Out, int k, int G,
+                                               const double* __restrict__ Q2, TO* __restrict__ Out, int k, int ld, int G,
                                                double* partial, unsigned* ticket, BlockScalars sc, int flexible) {
     const Grp g = make_grp(G);
     double d0[CPL], d1[CPL];
@@ -253,7 +243,7 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
         T acc[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) acc[m] = 0;
-        sell_row_k<T, CPL>(SAP, apval, ip, g, k, [&](int q, int c) { return __ldg(E + (size_t)q * k + c); }, acc);
+        sell_row_k<T, CPL>(SAP, apval, ip, g, k, [&](int q, int c) { return __ldg(E + (size_t)q * ld + c); }, acc);
         const int i = rowid(SAP, ip);
         const int a = agg[i];
         const T pi = p[i];
@@ -262,8 +252,8 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
             if (c < k) {
-                const size_t o = (size_t)i * k + c;
-                const T y = fma(pi, E[(size_t)a * k + c], X[o]);
+                const size_t o = (size_t)i * ld + c;
+                const T y = fma(pi, E[(size_t)a * ld + c], X[o]);
                 const T v = fma(mi, R[o] - acc[m], y);
                 Out[o] = (TO)v;
                 if (DOT) {
@@ -276,11 +266,255 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
     if (DOT) colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double a, double b) { fin_rz(sc, c, a, b, flexible); });
 }
 
+
+// ------------------------------------- iterative coarsest solve, k columns
+// CG with l1-Jacobi per column to ||r_c|| <= rtol ||b_c|| or maxit, FP64, all
+// columns in one cooperative launch (the multi-column form of the
+// single-column coarsest solve). Short rows come from the hybrid SELL layout
+// through lane groups, rows kept out of it are split over the 32 lanes of a
+// warp; per-column sums use one fixed reduction order, and every block sums
+// the block partials in the same order after each grid barrier, so all blocks
+// hold the same per-column scalars.
+__device__ __forceinline__ unsigned long long bk_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned bk_ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void bk_grid_sync(unsigned* count, unsigned epoch, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const unsigned target = epoch * gridDim.x;
+        const unsigned long long t0 = bk_ns();
+        while (bk_ld_acquire(count) < target) {
+            if (bk_ns() - t0 > 2000000000ull) { atomicExch(err, 1); break; }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Block partial of one value per column into out[blockIdx.x * k + c].
+template <int CPL>
+__device__ __forceinline__ void bk_colpart(double (&v)[CPL], const Grp& g, int k, double* out) {
+    __shared__ double sm[WARPS][MAXK];
+#pragma unroll
+    for (int m = 0; m < CPL; ++m)
+        for (int o = g.G; o < 32; o <<= 1) v[m] += __shfl_xor_sync(FULL_MASK, v[m], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < g.G) {
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = lane + m * g.G;
+            if (c < k) sm[warp][c] = v[m];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double a = 0.0;
+        for (int w = 0; w < WARPS; ++w) a += sm[w][c];
+        out[(size_t)blockIdx.x * k + c] = a;
+    }
+    __syncthreads();
+}
+
+// dst[c] = sum over blocks of part[blk * k + c], same order in every block.
+__device__ __forceinline__ void bk_colsum(const double* part, int k, double* dst) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double a = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(part + (size_t)b * k + c);
+        dst[c] = a;
+    }
+    __syncthreads();
+}
+
+template <typename TI, typename TO, int CPL>
+__global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __restrict__ sval, int n, int nlong,
+                                                    const int* __restrict__ long_rows, const int* __restrict__ cptr,
+                                                    const int* __restrict__ ccol, const double* __restrict__ cval,
+                                                    const double* __restrict__ minv, const TI* __restrict__ B,
+                                                    TO* __restrict__ Xo, int k, int ld, int G, double* x, double* r,
+                                                    double* z, double* p, double* q, double* part, unsigned* bar,
+                                                    int* err, int maxit, double rtol) {
+    __shared__ double s_rho[MAXK], s_bb[MAXK], s_t[MAXK];
+    __shared__ int s_live[MAXK];
+    __shared__ int s_any;
+    const Grp g = make_grp(G);
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const size_t PK = (size_t)gridDim.x * k;
+    unsigned epoch = 0;
+    int red = 0;
+    auto slot = [&]() { return part + (size_t)(red & 1) * PK; };
+    double d0[CPL];
+    // x = 0, r = b, z = M^-1 r, p = z; rho = r.z and bb = b.b per column
+#pragma unroll
+    for (int m = 0; m < CPL; ++m) d0[m] = 0.0;
+    double d1[CPL];
+#pragma unroll
+    for (int m = 0; m < CPL; ++m) d1[m] = 0.0;
+    for (int i = g.gw; i < n; i += g.ngroups) {
+        const double mi = minv[i];
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = g.gl + m * g.G;
+            if (c >= k) continue;
+            const size_t o = (size_t)i * ld + c;
+            const double bi = (double)B[o];
+            x[o] = 0.0;
+            r[o] = bi;
+            const double zi = mi * bi;
+            z[o] = zi;
+            p[o] = zi;
+            d0[m] = fma(bi, zi, d0[m]);
+            d1[m] = fma(bi, bi, d1[m]);
+        }
+    }
+    bk_colpart<CPL>(d0, g, k, slot());
+    bk_colpart<CPL>(d1, g, k, slot() + PK * 2);
+    bk_grid_sync(bar, ++epoch, err);
+    if (__ldcg(err)) return;
+    bk_colsum(slot(), k, s_rho);
+    bk_colsum(slot() + PK * 2, k, s_bb);
+    for (int c = threadIdx.x; c < k; c += blockDim.x) s_live[c] = s_bb[c] > 0.0;
+    __syncthreads();
+    ++red;
+    for (int it = 0; it < maxit; ++it) {
+        if (threadIdx.x == 0) {
+            int a = 0;
+            for (int c = 0; c < k; ++c) a |= s_live[c];
+            s_any = a;
+        }
+        __syncthreads();
+        if (!s_any) break;
+        // q = A p, p . q
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) d0[m] = 0.0;
+        for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
+            double acc[CPL];
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
+            sell_row_k<double, CPL>(S, sval, ip, g, k, [&](int j, int c) { return __ldcg(p + (size_t)j * ld + c); },
+                                    acc);
+            const int i = rowid(S, ip);
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) {
+                const int c = g.gl + m * g.G;
+                if (c >= k) continue;
+                const size_t o = (size_t)i * ld + c;
+                q[o] = acc[m];
+                d0[m] = fma(__ldcg(p + o), acc[m], d0[m]);
+            }
+        }
+        for (int lr = gwarp; lr < nlong; lr += nwarps) {
+            const int i = __ldg(long_rows + lr);
+            const int e0 = __ldg(cptr + i), e1 = __ldg(cptr + i + 1);
+            for (int c = 0; c < k; ++c) {
+                double a = 0.0;
+                for (int e = e0 + lane; e < e1; e += 32) a = fma(__ldg(cval + e), __ldcg(p + (size_t)__ldg(ccol + e) * ld + c), a);
+                a = warp_sum(a);
+                const size_t o = (size_t)i * ld + c;
+                if (lane == 0) q[o] = a;
+#pragma unroll
+                for (int m = 0; m < CPL; ++m)
+                    if (lane + m * G == c) d0[m] = fma(__ldcg(p + o), a, d0[m]);
+            }
+        }
+        bk_colpart<CPL>(d0, g, k, slot());
+        bk_grid_sync(bar, ++epoch, err);
+        if (__ldcg(err)) return;
+        bk_colsum(slot(), k, s_t);
+        ++red;
+        // alpha per live column; x += alpha p, r -= alpha q; r.r
+        double al[CPL];
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = g.gl + m * g.G;
+            al[m] = (c < k && s_live[c]) ? s_rho[c] / s_t[c] : 0.0;
+            d0[m] = 0.0;
+        }
+        for (int i = g.gw; i < n; i += g.ngroups) {
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) {
+                const int c = g.gl + m * g.G;
+                if (c >= k || al[m] == 0.0) continue;
+                const size_t o = (size_t)i * ld + c;
+                x[o] = fma(al[m], __ldcg(p + o), x[o]);
+                const double ri = fma(-al[m], __ldcg(q + o), r[o]);
+                r[o] = ri;
+                d0[m] = fma(ri, ri, d0[m]);
+            }
+        }
+        bk_colpart<CPL>(d0, g, k, slot());
+        bk_grid_sync(bar, ++epoch, err);
+        if (__ldcg(err)) return;
+        bk_colsum(slot(), k, s_t);
+        ++red;
+        for (int c = threadIdx.x; c < k; c += blockDim.x)
+            if (s_live[c] && s_t[c] <= rtol * rtol * s_bb[c]) s_live[c] = 0;
+        __syncthreads();
+        // z = M^-1 r; r.z; beta; p = z + beta p
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) d0[m] = 0.0;
+        for (int i = g.gw; i < n; i += g.ngroups) {
+            const double mi = minv[i];
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) {
+                const int c = g.gl + m * g.G;
+                if (c >= k || !s_live[c]) continue;
+                const size_t o = (size_t)i * ld + c;
+                const double zi = mi * r[o];
+                z[o] = zi;
+                d0[m] = fma(r[o], zi, d0[m]);
+            }
+        }
+        bk_colpart<CPL>(d0, g, k, slot());
+        bk_grid_sync(bar, ++epoch, err);
+        if (__ldcg(err)) return;
+        bk_colsum(slot(), k, s_t);
+        ++red;
+        double be[CPL];
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = g.gl + m * g.G;
+            be[m] = (c < k && s_live[c]) ? s_t[c] / s_rho[c] : 0.0;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < k; c += blockDim.x)
+            if (s_live[c]) s_rho[c] = s_t[c];
+        for (int i = g.gw; i < n; i += g.ngroups) {
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) {
+                const int c = g.gl + m * g.G;
+                if (c >= k || !s_live[c]) continue;
+                const size_t o = (size_t)i * ld + c;
+                p[o] = fma(be[m], p[o], z[o]);
+            }
+        }
+        bk_grid_sync(bar, ++epoch, err);
+        if (__ldcg(err)) return;
+    }
+    for (int i = g.gw; i < n; i += g.ngroups) {
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = g.gl + m * g.G;
+            if (c < k) Xo[(size_t)i * ld + c] = (TO)x[(size_t)i * ld + c];
+        }
+    }
+}
+
 // ------------------------------------------------------------- CG ----------
 // Q = A P; p . q per column; alpha = rho / p.q for ACTIVE columns, else 0.
 template <int CPL>
 __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __restrict__ val,
-                                                   const double* __restrict__ P, double* __restrict__ Q, int k, int G,
+                                                   const double* __restrict__ P, double* __restrict__ Q, int k, int ld, int G,
                                                    double* partial, unsigned* ticket, BlockScalars sc) {
     const Grp g = make_grp(G);
     double d0[CPL], d1[CPL];
@@ -290,13 +524,13 @@ __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __rest
         double acc[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
-        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(P + (size_t)j * k + c); }, acc);
+        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(P + (size_t)j * ld + c); }, acc);
         const int i = rowid(S, ip);
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
             if (c < k) {
-                const size_t o = (size_t)i * k + c;
+                const size_t o = (size_t)i * ld + c;
                 Q[o] = acc[m];
                 d0[m] = fma(P[o], acc[m], d0[m]);
             }
@@ -321,7 +555,7 @@ __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __rest
 // ACTIVE columns: X += alpha P, R -= alpha Q, ||R||^2; convergence -> CHECK.
 template <int CPL>
 __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restrict__ P, const double* __restrict__ Q,
-                                                    double* __restrict__ X, double* __restrict__ R, int k, int G,
+                                                    double* __restrict__ X, double* __restrict__ R, int k, int ld, int G,
                                                     double* partial, unsigned* ticket, BlockScalars sc) {
     const Grp g = make_grp(G);
     double al[CPL];
@@ -339,7 +573,7 @@ __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restr
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             if (!on[m]) continue;
-            const size_t o = (size_t)i * k + g.gl + m * g.G;
+            const size_t o = (size_t)i * ld + g.gl + m * g.G;
             X[o] = fma(al[m], P[o], X[o]);
             const double ri = fma(-al[m], Q[o], R[o]);
             R[o] = ri;
@@ -357,7 +591,7 @@ __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restr
 // ACTIVE columns: P = Z + beta P (P = Z when beta = 0, whatever P held).
 template <int CPL>
 __global__ void __launch_bounds__(TPB) bk_update_p(int n, const double* __restrict__ Z, double* __restrict__ P, int k,
-                                                   int G, BlockScalars sc) {
+                                                   int ld, int G, BlockScalars sc) {
     const Grp g = make_grp(G);
     double be[CPL];
     bool on[CPL];
@@ -371,21 +605,22 @@ __global__ void __launch_bounds__(TPB) bk_update_p(int n, const double* __restri
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             if (!on[m]) continue;
-            const size_t o = (size_t)i * k + g.gl + m * g.G;
+            const size_t o = (size_t)i * ld + g.gl + m * g.G;
             P[o] = be[m] == 0.0 ? Z[o] : fma(be[m], P[o], Z[o]);
         }
     }
 }
 
 // R = B - A X for the selected columns, ||R||^2 and ||B||^2.
-//   stage 0 (start): every non-idle column; DONE when ||B|| = 0, else START.
+//   stage 0 (start): INIT columns; DONE when ||B|| = 0 or x0 already meets
+//                    rtol, else START.
 //   stage 1 (check): CHECK columns; true residual below rtol -> DONE, else the
 //                    column restarts from R (START).
 //   stage 2 (report): every column; only records ||R||^2 in rr.
 template <int CPL>
 __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __restrict__ val,
                                                    const double* __restrict__ X, const double* __restrict__ B,
-                                                   double* __restrict__ R, int k, int G, double* partial,
+                                                   double* __restrict__ R, int k, int ld, int G, double* partial,
                                                    unsigned* ticket, BlockScalars sc, int stage) {
     const Grp g = make_grp(G);
     bool on[CPL];
@@ -393,7 +628,7 @@ __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __rest
     for (int m = 0; m < CPL; ++m) {
         const int c = g.gl + m * g.G;
         const int md = c < k ? sc.mode[c] : COL_IDLE;
-        on[m] = c < k && (stage == 0 ? md != COL_IDLE : (stage == 1 ? md == COL_CHECK : true));
+        on[m] = c < k && (stage == 0 ? md == COL_INIT : (stage == 1 ? md == COL_CHECK : true));
     }
     double d0[CPL], d1[CPL];
 #pragma unroll
@@ -402,12 +637,12 @@ __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __rest
         double acc[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
-        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(X + (size_t)j * k + c); }, acc);
+        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(X + (size_t)j * ld + c); }, acc);
         const int i = rowid(S, ip);
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             if (!on[m]) continue;
-            const size_t o = (size_t)i * k + g.gl + m * g.G;
+            const size_t o = (size_t)i * ld + g.gl + m * g.G;
             const double bi = B[o];
             const double ri = bi - acc[m];
             R[o] = ri;
@@ -418,7 +653,7 @@ __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __rest
     colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double rr, double bb) {
         const int md = sc.mode[c];
         if (stage == 0) {
-            if (md == COL_IDLE) return;
+            if (md != COL_INIT) return;
             sc.bb[c] = bb;
             sc.rr[c] = rr;
             sc.iters[c] = 0;
@@ -433,26 +668,58 @@ __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __rest
     });
 }
 
-__global__ void bk_zero_cols(int n, double* __restrict__ X, int k, const int* __restrict__ mode,
+// Slot lists of a request (at most MAXK slots) passed by value.
+struct SlotList {
+    int n;
+    int slot[MAXK];
+};
+
+// dst[:, slot[j]] = src[:, j] (src row-major n x k contiguous, dst row stride ld);
+// with src == nullptr the slot columns are zeroed.
+__global__ void bk_scatter_slots(int n, const double* __restrict__ src, int ld, double* __restrict__ dst,
+                                 SlotList sl) {
+    const int k = sl.n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * k;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = t / k;
+        const int j = (int)(t % k);
+        dst[i * ld + sl.slot[j]] = src ? src[t] : 0.0;
+    }
+}
+
+// dst[:, j] = src[:, slot] for one slot column j of a request (dst n x k).
+__global__ void bk_gather_slot(int n, const double* __restrict__ src, int ld, int slot, double* __restrict__ dst,
+                               int k, int j) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[(size_t)i * k + j] = src[(size_t)i * ld + slot];
+}
+
+__global__ void bk_zero_cols(int n, double* __restrict__ X, int k, int ld, const int* __restrict__ mode,
                              const double* __restrict__ bb) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * k;
          t += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(t % k);
-        if (bb[c] == 0.0 && mode[c] == COL_DONE) X[t] = 0.0;
+        const long long i = t / k;
+        if (bb[c] == 0.0 && mode[c] == COL_DONE) X[i * ld + c] = 0.0;
     }
 }
 
 // ------------------------------------------------------------- host --------
 SellV sv(const DevSell& S) { return SellV{S.n, S.nslices, S.sptr, S.col, S.perm}; }
 
-void group_shape(int k, int* G, int* cpl) {
-    int g = 1;
-    while (g < k && g < 32) g <<= 1;
-    int c = (k + g - 1) / g;
+int pow2_at_least(int v) {
     int p = 1;
-    while (p < c) p <<= 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Group width and columns per lane for k active columns. With a fixed width
+// (set by the slot count K, not by k) a column's arithmetic and reduction
+// order do not depend on how many columns are in flight.
+void group_shape(const BlockWork& W, int k, int* G, int* cpl) {
+    const int g = std::min(32, pow2_at_least(W.fixed_width ? W.K : k));
     *G = g;
-    *cpl = p;
+    *cpl = pow2_at_least((k + g - 1) / g);
 }
 
 #define DISPATCH_CPL(cpl, ...)                          \
@@ -468,8 +735,104 @@ int grid_rows(const amg_hierarchy* h, long long rows, int G) {
     return blocks_for(rows, (int)groups_per_block, h->num_sms * 8);
 }
 
-BlockWork& ensure_work(amg_hierarchy* h, int K) {
-    if (h->blk && h->blk->K == K) return *h->blk;
+// Z = B R for columns [0, k) (block V-cycle); level 0 finishes r . z per column.
+template <typename T>
+void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
+    cudaStream_t st = h->stream;
+    const int ld = W.K;
+    const int L = (int)h->lev.size() - 1;
+    const bool f32 = sizeof(T) == 4;
+    const T omega = (T)h->opt.omega;
+    int G, cpl;
+    group_shape(W, k, &G, &cpl);
+    auto lv = [&](std::vector<void*>& v, int l) { return static_cast<T*>(v[l]); };
+    for (int l = 0; l < L; ++l) {
+        Level& Lv = h->lev[l];
+        const T* valm = f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm;
+        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
+        const int g = grid_rows(h, Lv.S.n, G);
+        Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE,
+                  (double)Lv.A.nnz * (sizeof(T) + 4) + (double)Lv.A.n * k * ((l == 0 ? 8 : sizeof(T)) + 2.0 * sizeof(T)));
+        if (l == 0)
+            DISPATCH_CPL(cpl, bk_pre<T, double, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, W.R, lv(W.x, 0),
+                                                                       lv(W.r, 0), k, ld, G))
+        else
+            DISPATCH_CPL(cpl, bk_pre<T, T, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, lv(W.b, l), lv(W.x, l),
+                                                                  lv(W.r, l), k, ld, G))
+        KERNEL_CHECK();
+        const int nc = h->lev[l + 1].A.n;
+        const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
+        DISPATCH_CPL(cpl, bk_restrict<T, CPL><<<grid_rows(h, nc, G), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, p,
+                                                                                   lv(W.r, l), lv(W.b, l + 1), k, ld, G))
+        KERNEL_CHECK();
+    }
+    {
+        Scope sc_(&h->prof, st, K_COARSE, 8.0 * h->nc * h->nc + 16.0 * h->nc * k);
+        if (!h->coarse_cg) {
+            DISPATCH_CPL(cpl, bk_coarse_dense<T, T, CPL><<<grid_rows(h, h->nc, G), TPB, 0, st>>>(
+                                  h->nc, h->coarse_inv, lv(W.b, L), lv(W.x, L), k, ld, G))
+            KERNEL_CHECK();
+        } else {
+            Level& Lc = h->lev[L];
+            const SellV Sc = sv(Lc.S);
+            const double* sval = Lc.S.val;
+            int nrows = Lc.A.n, nlong = Lc.S.nlong, kk = k, ldd = ld, GG = G, maxit = 30;
+            const int* long_rows = Lc.S.long_rows;
+            const int* cptr = Lc.A.ptr;
+            const int* ccol = Lc.A.col;
+            const double* cval = Lc.A.val;
+            const double* cminv = Lc.minv;
+            const T* bin = lv(W.b, L);
+            T* xout = lv(W.x, L);
+            double rtol = 1e-4;
+            unsigned* bar = reinterpret_cast<unsigned*>(W.cctl);
+            int* err = W.cctl + 1;
+            CUDA_CHECK(cudaMemsetAsync(W.cctl, 0, sizeof(int) * 4, st));
+            void* args[] = {(void*)&Sc, (void*)&sval, &nrows, &nlong, (void*)&long_rows, (void*)&cptr, (void*)&ccol,
+                            (void*)&cval, (void*)&cminv, (void*)&bin, (void*)&xout, &kk, &ldd, &GG, &W.cw[0],
+                            &W.cw[1], &W.cw[2], &W.cw[3], &W.cw[4], &W.cpart, &bar, &err, &maxit, &rtol};
+            const void* fn = nullptr;
+            DISPATCH_CPL(cpl, fn = (const void*)bk_coarse_cg<T, T, CPL>)
+            CUDA_CHECK(cudaLaunchCooperativeKernel(fn, dim3(h->num_sms), dim3(TPB), args, 0, st));
+            KERNEL_CHECK();
+        }
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        Level& Lv = h->lev[l];
+        const T* apv = f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val;
+        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
+        const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
+        const T* e = l + 1 == L ? lv(W.x, L) : lv(W.y, l + 1);
+        const int g = grid_rows(h, Lv.AP.n, G);
+        Scope sc_(&h->prof, st, l == 0 ? K_POST_L0 : K_POST,
+                  (double)Lv.ap_nnz * (sizeof(T) + 4) + (double)Lv.A.n * k * (4.0 * sizeof(T) + 8));
+        if (l > 0)
+            DISPATCH_CPL(cpl, bk_post<T, T, CPL, false><<<g, TPB, 0, st>>>(
+                                  sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, l), lv(W.r, l), nullptr, nullptr,
+                                  lv(W.y, l), k, ld, G, W.partial, W.ticket, W.sc, flexible))
+        else
+            DISPATCH_CPL(cpl, bk_post<T, double, CPL, true><<<W.grid, TPB, 0, st>>>(
+                                  sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, 0), lv(W.r, 0), W.R,
+                                  flexible ? W.Q : nullptr, W.Z, k, ld, G, W.partial, W.ticket, W.sc, flexible))
+        KERNEL_CHECK();
+    }
+}
+
+void copy_state_async(amg_hierarchy* h, BlockWork& W) {
+    cudaStream_t st = h->stream;
+    CUDA_CHECK(cudaMemcpyAsync(W.mode_host, W.sc.mode, sizeof(int) * W.K, cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(W.iters_host, W.sc.iters, sizeof(int) * W.K, cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(W.rr_host, W.sc.rr, sizeof(double) * W.K, cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(W.bb_host, W.sc.bb, sizeof(double) * W.K, cudaMemcpyDeviceToHost, st));
+}
+
+}  // namespace
+
+BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width) {
+    if (h->blk && h->blk->K == K && h->blk->fixed_width == fixed_width) return *h->blk;
+    if (K < 1 || K > MAXK) AMG_THROW(AMG_ERR_TOO_LARGE, "block solves take 1..%d columns", MAXK);
+    if (h->opt.pre != 1 || h->opt.post != 1) AMG_THROW(AMG_ERR_ARG, "block solves use 1+1 smoothing sweeps");
+    if (h->lev.size() < 2) AMG_THROW(AMG_ERR_ARG, "block solves need at least two levels");
     if (h->blk) {
         CUDA_CHECK(cudaStreamSynchronize(h->stream));
         delete h->blk;
@@ -478,6 +841,7 @@ BlockWork& ensure_work(amg_hierarchy* h, int K) {
     BlockWork* W = new BlockWork;
     h->blk = W;
     W->K = K;
+    W->fixed_width = fixed_width;
     const bool f32 = h->opt.precision == AMG_FP32_VCYCLE;
     const size_t V = f32 ? 4 : 8;
     for (auto& L : h->lev) {
@@ -512,197 +876,146 @@ BlockWork& ensure_work(amg_hierarchy* h, int K) {
     CUDA_CHECK(cudaHostAlloc(&W->iters_host, sizeof(int) * K, cudaHostAllocDefault));
     CUDA_CHECK(cudaHostAlloc(&W->rr_host, sizeof(double) * K, cudaHostAllocDefault));
     CUDA_CHECK(cudaHostAlloc(&W->bb_host, sizeof(double) * K, cudaHostAllocDefault));
+    for (int c = 0; c < K; ++c) W->mode_host[c] = COL_IDLE;
     if (h->coarse_cg) {
-        W->cb = W->mem.alloc<double>(h->nc);
-        W->cx = W->mem.alloc<double>(h->nc);
+        for (int v = 0; v < 5; ++v) W->cw[v] = W->mem.alloc<double>((size_t)h->nc * K);
+        W->cpart = W->mem.alloc<double>((size_t)h->num_sms * K * 4);
+        W->cctl = W->mem.alloc<int>(4);
+        int per_sm = 0;
+        CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk_coarse_cg<double, double, 8>, TPB, 0));
+        if (per_sm < 1) AMG_THROW(AMG_ERR_CUDA, "multi-column coarsest CG kernel cannot be resident");
     }
     return *W;
 }
 
-// Z = B R for all K columns (block V-cycle); level 0 finishes r . z per column.
-template <typename T>
-void block_vcycle(amg_hierarchy* h, BlockWork& W, int flexible) {
-    cudaStream_t st = h->stream;
-    const int K = W.K;
-    const int L = (int)h->lev.size() - 1;
-    const bool f32 = sizeof(T) == 4;
-    const T omega = (T)h->opt.omega;
-    int G, cpl;
-    group_shape(K, &G, &cpl);
-    auto lv = [&](std::vector<void*>& v, int l) { return static_cast<T*>(v[l]); };
-    if (L == 0) {
-        // single level: the whole operator is the coarsest solve
-        AMG_THROW(AMG_ERR_ARG, "block solves need at least two levels");
-    }
-    for (int l = 0; l < L; ++l) {
-        Level& Lv = h->lev[l];
-        const T* valm = f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm;
-        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
-        const int g = grid_rows(h, Lv.S.n, G);
-        Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE,
-                  (double)Lv.A.nnz * (sizeof(T) + 4) + (double)Lv.A.n * K * ((l == 0 ? 8 : sizeof(T)) + 2.0 * sizeof(T)));
-        if (l == 0)
-            DISPATCH_CPL(cpl, bk_pre<T, double, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, W.R, lv(W.x, 0),
-                                                                       lv(W.r, 0), K, G))
-        else
-            DISPATCH_CPL(cpl, bk_pre<T, T, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, lv(W.b, l), lv(W.x, l),
-                                                                  lv(W.r, l), K, G))
-        KERNEL_CHECK();
-        const int nc = h->lev[l + 1].A.n;
-        const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
-        DISPATCH_CPL(cpl, bk_restrict<T, CPL><<<grid_rows(h, nc, G), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, p,
-                                                                                   lv(W.r, l), lv(W.b, l + 1), K, G))
-        KERNEL_CHECK();
-    }
-    {
-        Scope sc_(&h->prof, st, K_COARSE, 8.0 * h->nc * h->nc + 16.0 * h->nc * K);
-        if (!h->coarse_cg) {
-            DISPATCH_CPL(cpl, bk_coarse_dense<T, T, CPL><<<grid_rows(h, h->nc, G), TPB, 0, st>>>(
-                                  h->nc, h->coarse_inv, lv(W.b, L), lv(W.x, L), K, G))
-            KERNEL_CHECK();
-        } else {
-            const int gg = blocks_for(h->nc, TPB, h->num_sms * 4);
-            for (int c = 0; c < K; ++c) {
-                bk_gather_col<T><<<gg, TPB, 0, st>>>(h->nc, lv(W.b, L), K, c, W.cb);
-                KERNEL_CHECK();
-                coarse_cg_solve(h, W.cb, W.cx);
-                bk_scatter_col<T><<<gg, TPB, 0, st>>>(h->nc, W.cx, K, c, lv(W.x, L));
-                KERNEL_CHECK();
-            }
-        }
-    }
-    for (int l = L - 1; l >= 0; --l) {
-        Level& Lv = h->lev[l];
-        const T* apv = f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val;
-        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
-        const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
-        const T* e = l + 1 == L ? lv(W.x, L) : lv(W.y, l + 1);
-        const int g = grid_rows(h, Lv.AP.n, G);
-        Scope sc_(&h->prof, st, l == 0 ? K_POST_L0 : K_POST,
-                  (double)Lv.ap_nnz * (sizeof(T) + 4) + (double)Lv.A.n * K * (4.0 * sizeof(T) + 8));
-        if (l > 0)
-            DISPATCH_CPL(cpl, bk_post<T, T, CPL, false><<<g, TPB, 0, st>>>(
-                                  sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, l), lv(W.r, l), nullptr, nullptr,
-                                  lv(W.y, l), K, G, W.partial, W.ticket, W.sc, flexible))
-        else
-            DISPATCH_CPL(cpl, bk_post<T, double, CPL, true><<<W.grid, TPB, 0, st>>>(
-                                  sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, 0), lv(W.r, 0), W.R,
-                                  flexible ? W.Q : nullptr, W.Z, K, G, W.partial, W.ticket, W.sc, flexible))
-        KERNEL_CHECK();
-    }
+size_t block_bytes_per_column(const amg_hierarchy* h) {
+    const size_t V = h->opt.precision == AMG_FP32_VCYCLE ? 4 : 8;
+    size_t rows = 0;
+    for (auto& L : h->lev) rows += (size_t)L.A.n;
+    return rows * 4 * V + (size_t)h->lev[0].A.n * 5 * 8;
 }
 
-void read_state(amg_hierarchy* h, BlockWork& W) {
-    cudaStream_t st = h->stream;
-    CUDA_CHECK(cudaMemcpyAsync(W.mode_host, W.sc.mode, sizeof(int) * W.K, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaMemcpyAsync(W.iters_host, W.sc.iters, sizeof(int) * W.K, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaMemcpyAsync(W.rr_host, W.sc.rr, sizeof(double) * W.K, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaMemcpyAsync(W.bb_host, W.sc.bb, sizeof(double) * W.K, cudaMemcpyDeviceToHost, st));
-    CUDA_CHECK(cudaStreamSynchronize(st));
-}
-
-}  // namespace
-
-// One step of every column (see the file comment). Returns after the state
-// has been read back into W.mode_host / iters_host / rr_host / bb_host.
-void block_step(amg_hierarchy* h, const double* B, double* X) {
+// INIT columns among [0, k): residual of X, then START (or DONE for b = 0,
+// whose X column is zeroed). Launches only.
+void block_init_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     BlockWork& W = *h->blk;
     cudaStream_t st = h->stream;
-    const int K = W.K;
+    int G, cpl;
+    group_shape(W, k, &G, &cpl);
+    Level& L0 = h->lev[0];
+    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G, W.partial,
+                                                             W.ticket, W.sc, 0))
+    KERNEL_CHECK();
+    bk_zero_cols<<<blocks_for((long long)L0.A.n * k, TPB, h->num_sms * 8), TPB, 0, st>>>(L0.A.n, X, k, W.K, W.sc.mode,
+                                                                                      W.sc.bb);
+    KERNEL_CHECK();
+}
+
+// One step of columns [0, k) (see the file comment), then an asynchronous
+// copy of the column states to the host mirrors. Launches only.
+void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k) {
+    (void)B;
+    BlockWork& W = *h->blk;
+    cudaStream_t st = h->stream;
+    const int ld = W.K;
     const int flexible = h->opt.krylov == 1;
     int G, cpl;
-    group_shape(K, &G, &cpl);
+    group_shape(W, k, &G, &cpl);
     Level& L0 = h->lev[0];
     const int n = L0.A.n;
     const double nnz = (double)L0.A.nnz;
-    bool any_active = false, any_check = false;
-    for (int c = 0; c < K; ++c) {
-        any_active |= W.mode_host[c] == COL_ACTIVE;
-        any_check |= W.mode_host[c] == COL_CHECK;
-    }
+    bool any_active = false;
+    for (int c = 0; c < k; ++c) any_active |= W.mode_host[c] == COL_ACTIVE;
     if (any_active) {
         {
-            Scope sc_(&h->prof, st, K_SPMV_DOT, 12.0 * nnz + 16.0 * n * K);
-            DISPATCH_CPL(cpl, bk_spmv_dot<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, W.P, W.Q, K, G, W.partial,
-                                                                     W.ticket, W.sc))
+            Scope sc_(&h->prof, st, K_SPMV_DOT, 12.0 * nnz + 16.0 * n * k);
+            DISPATCH_CPL(cpl, bk_spmv_dot<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, W.P, W.Q, k, ld, G,
+                                                                     W.partial, W.ticket, W.sc))
             KERNEL_CHECK();
         }
         {
-            Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n * K);
-            DISPATCH_CPL(cpl, bk_update_xr<CPL><<<W.grid, TPB, 0, st>>>(n, W.P, W.Q, X, W.R, K, G, W.partial, W.ticket,
-                                                                      W.sc))
+            Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n * k);
+            DISPATCH_CPL(cpl, bk_update_xr<CPL><<<W.grid, TPB, 0, st>>>(n, W.P, W.Q, X, W.R, k, ld, G, W.partial,
+                                                                      W.ticket, W.sc))
             KERNEL_CHECK();
         }
     }
-    if (h->opt.precision == AMG_FP32_VCYCLE) block_vcycle<float>(h, W, flexible);
-    else block_vcycle<double>(h, W, flexible);
+    if (h->opt.precision == AMG_FP32_VCYCLE) block_vcycle<float>(h, W, k, flexible);
+    else block_vcycle<double>(h, W, k, flexible);
     {
-        Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n * K);
-        DISPATCH_CPL(cpl, bk_update_p<CPL><<<grid_rows(h, n, G), TPB, 0, st>>>(n, W.Z, W.P, K, G, W.sc))
+        Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n * k);
+        DISPATCH_CPL(cpl, bk_update_p<CPL><<<grid_rows(h, n, G), TPB, 0, st>>>(n, W.Z, W.P, k, ld, G, W.sc))
         KERNEL_CHECK();
     }
-    read_state(h, W);
-    any_check = false;
-    for (int c = 0; c < K; ++c) any_check |= W.mode_host[c] == COL_CHECK;
-    if (any_check) {
-        Scope sc_(&h->prof, st, K_RESIDUAL, 12.0 * nnz + 24.0 * n * K);
-        DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, X, B, W.R, K, G, W.partial,
-                                                                 W.ticket, W.sc, 1))
-        KERNEL_CHECK();
-        read_state(h, W);
-    }
+    copy_state_async(h, W);
 }
 
-// Marks every column START (or DONE for b = 0) from the residual of X.
-void block_begin(amg_hierarchy* h, const double* B, double* X, double rtol) {
+// After a synchronised step: true residual of the CHECK columns (DONE or
+// restart). Returns whether anything was launched.
+bool block_check_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     BlockWork& W = *h->blk;
-    cudaStream_t st = h->stream;
-    const int K = W.K;
+    bool any_check = false;
+    for (int c = 0; c < k; ++c) any_check |= W.mode_host[c] == COL_CHECK;
+    if (!any_check) return false;
     int G, cpl;
-    group_shape(K, &G, &cpl);
+    group_shape(W, k, &G, &cpl);
     Level& L0 = h->lev[0];
-    std::vector<double> rt(K, rtol);
-    std::vector<int> md(K, COL_START);
-    CUDA_CHECK(cudaMemcpyAsync(W.sc.rtol, rt.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
-    CUDA_CHECK(cudaMemcpyAsync(W.sc.mode, md.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
-    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, X, B, W.R, K, G, W.partial,
-                                                             W.ticket, W.sc, 0))
+    const double nnz = (double)L0.A.nnz;
+    Scope sc_(&h->prof, h->stream, K_RESIDUAL, 12.0 * nnz + 24.0 * L0.A.n * k);
+    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G,
+                                                                    W.partial, W.ticket, W.sc, 1))
     KERNEL_CHECK();
-    bk_zero_cols<<<blocks_for((long long)L0.A.n * K, TPB, h->num_sms * 8), TPB, 0, st>>>(L0.A.n, X, K, W.sc.mode,
-                                                                                      W.sc.bb);
+    copy_state_async(h, W);
+    return true;
+}
+
+void block_report_launch(amg_hierarchy* h, const double* B, const double* X, int k) {
+    BlockWork& W = *h->blk;
+    int G, cpl;
+    group_shape(W, k, &G, &cpl);
+    Level& L0 = h->lev[0];
+    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.T, k, W.K, G,
+                                                                    W.partial, W.ticket, W.sc, 2))
     KERNEL_CHECK();
-    read_state(h, W);
+    copy_state_async(h, W);
+}
+
+void block_set_columns(amg_hierarchy* h, int c0, int cnt, int mode, double rtol) {
+    BlockWork& W = *h->blk;
+    std::vector<int> md(cnt, mode);
+    std::vector<double> rt(cnt, rtol);
+    std::vector<int> zi(cnt, 0);
+    CUDA_CHECK(cudaMemcpyAsync(W.sc.mode + c0, md.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
+    CUDA_CHECK(cudaMemcpyAsync(W.sc.rtol + c0, rt.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, h->stream));
+    CUDA_CHECK(cudaMemcpyAsync(W.sc.iters + c0, zi.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, h->stream));
+    // host buffers are pageable: make sure they are consumed before they go out of scope
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
+    for (int c = c0; c < c0 + cnt; ++c) W.mode_host[c] = mode;
 }
 
 amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
                        amg_solve_info* infos) {
     auto t0 = std::chrono::steady_clock::now();
-    if (k < 1 || k > MAXK) AMG_THROW(AMG_ERR_TOO_LARGE, "block solves take 1..%d columns", MAXK);
-    if (h->opt.pre != 1 || h->opt.post != 1) AMG_THROW(AMG_ERR_ARG, "block solves use 1+1 smoothing sweeps");
-    if (h->lev.size() < 2) AMG_THROW(AMG_ERR_ARG, "block solves need at least two levels");
-    BlockWork& W = ensure_work(h, k);
-    block_begin(h, B, X, rtol);
+    BlockWork& W = block_ensure(h, k, false);
+    block_set_columns(h, 0, k, COL_INIT, rtol);
+    block_init_launch(h, B, X, k);
+    copy_state_async(h, W);
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
     int steps = 0;
     for (;;) {
         bool live = false;
-        for (int c = 0; c < k; ++c) live |= W.mode_host[c] == COL_START || W.mode_host[c] == COL_ACTIVE;
-        if (!live) break;
         int maxi = 0;
-        for (int c = 0; c < k; ++c) maxi = std::max(maxi, W.iters_host[c]);
-        if (maxi >= maxit) break;
-        block_step(h, B, X);
-        if (++steps > 4 * maxit + 16) break;
+        for (int c = 0; c < k; ++c) {
+            live |= W.mode_host[c] == COL_START || W.mode_host[c] == COL_ACTIVE;
+            maxi = std::max(maxi, W.iters_host[c]);
+        }
+        if (!live || maxi >= maxit || ++steps > 4 * maxit + 16) break;
+        block_step_launch(h, B, X, k);
+        CUDA_CHECK(cudaStreamSynchronize(h->stream));
+        if (block_check_launch(h, B, X, k)) CUDA_CHECK(cudaStreamSynchronize(h->stream));
     }
-    // true residual of every column for the report
-    {
-        int G, cpl;
-        group_shape(k, &G, &cpl);
-        Level& L0 = h->lev[0];
-        DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.T, k, G,
-                                                                        W.partial, W.ticket, W.sc, 2))
-        KERNEL_CHECK();
-        read_state(h, W);
-    }
+    block_report_launch(h, B, X, k);
+    CUDA_CHECK(cudaStreamSynchronize(h->stream));
     h->prof.flush();
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     amg_status status = AMG_OK;
@@ -726,6 +1039,22 @@ amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, doub
 void block_free(amg_hierarchy* h) {
     delete h->blk;
     h->blk = nullptr;
+}
+
+void block_scatter_request(amg_hierarchy* h, const double* src, int k, const int* slots, double* dst) {
+    SlotList sl;
+    sl.n = k;
+    for (int j = 0; j < k; ++j) sl.slot[j] = slots[j];
+    const int n = h->lev[0].A.n;
+    bk_scatter_slots<<<blocks_for((long long)n * k, TPB, h->num_sms * 8), TPB, 0, h->stream>>>(n, src, h->blk->K, dst,
+                                                                                            sl);
+    KERNEL_CHECK();
+}
+
+void block_gather_column(amg_hierarchy* h, const double* src, int slot, double* dst, int k, int j) {
+    const int n = h->lev[0].A.n;
+    bk_gather_slot<<<blocks_for(n, TPB, h->num_sms * 4), TPB, 0, h->stream>>>(n, src, h->blk->K, slot, dst, k, j);
+    KERNEL_CHECK();
 }
 
 }  // namespace amg
