@@ -152,6 +152,24 @@ amg_status amg_solve_host(amg_hierarchy* h, const double* b, double* x, double r
 amg_status amg_solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
                            amg_solve_info* infos);
 
+/*
+ * Many independent systems at once. amg_setup_many builds one hierarchy for
+ * the block-diagonal union of m systems (As[s], ws[s]: DEVICE arrays as for
+ * amg_setup). No edge joins two systems, so every system is matched and
+ * aggregated exactly as on its own; coarsening stops when the largest system
+ * has at most max_coarse rows, and the coarsest level is solved by a dense
+ * inverse per system. amg_solve_many runs one CG per system (its own
+ * scalars and convergence, all systems in each kernel, each step replayed
+ * as one CUDA graph); b and x are the systems' vectors concatenated in order
+ * (DEVICE, length = total rows), infos (host, m entries, may be NULL).
+ * amg_system_offsets copies the m + 1 row offsets of the systems (host).
+ */
+amg_status amg_setup_many(int m, const amg_csr* As, const double* const* ws, const amg_options* opt,
+                          amg_hierarchy** out);
+amg_status amg_solve_many(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
+                          amg_solve_info* infos);
+amg_status amg_system_offsets(const amg_hierarchy* h, int32_t* offsets);
+
 /* One application of the preconditioner, z = B r (Eq. 2), device pointers of length n. */
 amg_status amg_vcycle(amg_hierarchy* h, const double* r, double* z);
 

@@ -271,6 +271,10 @@ struct Hierarchy {
     int nc = 0;                    // coarsest size
     int coarse_cg = 0;             // 1: coarsest level solved by CG (too large for the dense factor)
     std::vector<double> L;         // dense Cholesky factor, column-major nc x nc
+    // batch of independent systems: coarsest row offsets and one dense
+    // Cholesky factor per system's diagonal block
+    std::vector<int> cseg;
+    std::vector<std::vector<double>> Lb;
     int pre = 1, post = 1;
     double omega = 1.0;
     int use_ld = 0;
@@ -336,16 +340,28 @@ void cholesky_solve(const std::vector<double>& L, int n, const double* b, double
 // that matches nothing ends the level early. Coarsening stops as soon as the
 // new level has at most max_coarse rows, when a level brings no reduction, or
 // at max_levels levels; the last level is solved by dense Cholesky.
+// For a batch of independent systems (block-diagonal A with row offsets
+// seg), the size test applies to the largest system; the offsets follow the
+// aggregates (each system's aggregates are contiguous and numbered after the
+// previous systems').
 int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps, int max_coarse,
-          int max_levels, double min_ratio, int max_dense) {
+          int max_levels, double min_ratio, int max_dense, const std::vector<int>* seg0 = nullptr) {
     H.lev.clear();
     H.lev.push_back(Level{});
     H.lev[0].A = A0;
     H.lev[0].w = w0;
+    std::vector<int> seg;
+    if (seg0) seg = *seg0;
+    auto largest = [&]() {
+        int mx = 0;
+        for (size_t s = 0; s + 1 < seg.size(); ++s) mx = std::max(mx, seg[s + 1] - seg[s]);
+        return mx;
+    };
     for (;;) {
         Level& cur = H.lev.back();
         const int l = (int)H.lev.size() - 1;
-        if (cur.A.n <= max_coarse || l + 1 >= max_levels) break;
+        const int size_rule = seg.empty() ? cur.A.n : largest();
+        if (size_rule <= max_coarse || l + 1 >= max_levels) break;
         Csr A = cur.A;
         std::vector<double> w = cur.w;
         std::vector<int32_t> agg(cur.A.n);
@@ -357,6 +373,8 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
             Pairwise pw = aggregate(mate, w);
             pw.rounds = rounds;
             if (pw.nc == A.n) break;
+            for (size_t s2 = 0; s2 + 1 < seg.size(); ++s2) seg[s2] = seg[s2] < A.n ? pw.agg[seg[s2]] : pw.nc;
+            if (!seg.empty()) seg.back() = pw.nc;
             Csr C = galerkin_onenz(A, pw.agg, pw.p, pw.nc);
             for (int i = 0; i < cur.A.n; ++i) {       // compose: P <- P P_s
                 p[i] = p[i] * pw.p[agg[i]];
@@ -380,6 +398,26 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
     for (auto& L : H.lev) L.minv = l1_jacobi_inverse(L.A);
     const Csr& Ac = H.lev.back().A;
     H.nc = Ac.n;
+    if (!seg.empty()) {                             // block-diagonal coarsest: factor each block
+        H.cseg = seg;
+        for (size_t s = 0; s + 1 < seg.size(); ++s) {
+            const int r0 = seg[s], nb = seg[s + 1] - seg[s];
+            if (nb > max_dense) return -8;
+            Csr B;
+            B.n = nb;
+            B.ptr.assign(1, 0);
+            for (int i = r0; i < r0 + nb; ++i) {
+                for (int64_t k = Ac.ptr[i]; k < Ac.ptr[i + 1]; ++k) {
+                    B.col.push_back(Ac.col[k] - r0);
+                    B.val.push_back(Ac.val[k]);
+                }
+                B.ptr.push_back((int64_t)B.col.size());
+            }
+            H.Lb.emplace_back();
+            if (!dense_cholesky(B, H.Lb.back())) return -2;
+        }
+        return 0;
+    }
     if (Ac.n > max_dense) {
         H.coarse_cg = 1;
         return 0;
@@ -442,8 +480,14 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const Level& L = H.lev[l];
     const int n = L.A.n;
     if (l == (int)H.lev.size() - 1) {
-        if (H.coarse_cg) coarse_cg(L, b, x);
-        else cholesky_solve(H.L, H.nc, b, x);
+        if (!H.cseg.empty()) {
+            for (size_t s = 0; s + 1 < H.cseg.size(); ++s)
+                cholesky_solve(H.Lb[s], H.cseg[s + 1] - H.cseg[s], b + H.cseg[s], x + H.cseg[s]);
+        } else if (H.coarse_cg) {
+            coarse_cg(L, b, x);
+        } else {
+            cholesky_solve(H.L, H.nc, b, x);
+        }
         return;
     }
     for (int i = 0; i < n; ++i) x[i] = 0.0;
@@ -596,9 +640,22 @@ int orc_match_ld(int n, const int32_t* ptr, const int32_t* col, const double* va
 // Builds the hierarchy. use_ld != 0 uses the locally-dominant rounds for the
 // matching (same result, also records the round counts). Returns a handle or
 // null; *status receives 0 or a negative code.
+void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
+                    int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
+                    int max_dense, int nseg, const int32_t* seg, int* status);
+
 void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                 int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
                 int max_dense, int* status) {
+    return orc_setup_seg(n, ptr, col, val, w, sweeps, max_coarse, max_levels, pre, post, omega, use_ld, min_ratio,
+                         max_dense, 0, nullptr, status);
+}
+
+// As orc_setup for the block-diagonal union of nseg systems with row offsets
+// seg[0..nseg] (the largest system decides when coarsening stops).
+void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
+                    int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
+                    int max_dense, int nseg, const int32_t* seg, int* status) {
     Csr A = make_csr(n, ptr, col, val);
     int e = validate(A);
     for (int i = 0; e == 0 && i < n; ++i)
@@ -606,7 +663,10 @@ void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val
     if (e) { *status = e; return nullptr; }
     Hierarchy* H = new Hierarchy;
     H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld;
-    e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels, min_ratio, max_dense);
+    std::vector<int> sv;
+    if (nseg > 0) sv.assign(seg, seg + nseg + 1);
+    e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels, min_ratio, max_dense,
+              nseg > 0 ? &sv : nullptr);
     *status = e;
     if (e) { delete H; return nullptr; }
     return H;

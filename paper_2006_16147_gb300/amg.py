@@ -34,7 +34,8 @@ EXPORTED = [
     "amg_hierarchy_info", "amg_export_level", "amg_sweep_dims", "amg_export_sweep", "amg_coarse_factor",
     "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
     "amg_launch_count", "amg_match_noalloc", "amg_solve_batch", "amg_serve_create", "amg_serve_submit",
-    "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free",
+    "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free", "amg_setup_many",
+    "amg_solve_many", "amg_system_offsets",
 ]
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_NNZ = 524288
@@ -120,6 +121,13 @@ def lib() -> ctypes.CDLL:
         L.amg_serve_stats_get.restype = ctypes.c_int
         L.amg_serve_free.argtypes = [_vp]
         L.amg_serve_free.restype = None
+        L.amg_setup_many.argtypes = [ctypes.c_int, ctypes.POINTER(amg_csr), ctypes.POINTER(_vp),
+                                     ctypes.POINTER(amg_options), ctypes.POINTER(_vp)]
+        L.amg_setup_many.restype = ctypes.c_int
+        L.amg_solve_many.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(amg_solve_info)]
+        L.amg_solve_many.restype = ctypes.c_int
+        L.amg_system_offsets.argtypes = [_vp, _i32p]
+        L.amg_system_offsets.restype = ctypes.c_int
         L.amg_vcycle.argtypes = [_vp, _vp, _vp]
         L.amg_vcycle.restype = ctypes.c_int
         L.amg_hierarchy_info.argtypes = [_vp, ctypes.POINTER(amg_hier_info)]
@@ -247,6 +255,36 @@ def amg_solve_batch(h: Hierarchy, B, X, rtol: float = 1e-6, maxit: int = 1000) -
     infos = (amg_solve_info * k)()
     st = _check(lib().amg_solve_batch(h.handle, k, _ptr(B), _ptr(X), float(rtol), int(maxit), infos))
     return [dict(_info_dict(infos[c], st)) for c in range(k)]
+
+
+def amg_setup_many(systems, **opts) -> Hierarchy:
+    """One hierarchy for the block-diagonal union of systems [(row_ptr, col, val, w), ...] (device tensors)."""
+    m = len(systems)
+    arr = (amg_csr * m)()
+    ws = (ctypes.c_void_p * m)()
+    for i, (rp, cl, vl, w) in enumerate(systems):
+        arr[i] = amg_csr(int(rp.shape[0] - 1), int(cl.shape[0]), _ptr(rp), _ptr(cl), _ptr(vl))
+        ws[i] = _ptr(w)
+    if "stream" not in opts:
+        opts["stream"] = _current_stream()
+    o = amg_options_default(**opts)
+    h = ctypes.c_void_p()
+    _check(lib().amg_setup_many(m, arr, ws, ctypes.byref(o), ctypes.byref(h)))
+    n = sum(int(rp.shape[0] - 1) for rp, _, _, _ in systems)
+    return Hierarchy(h.value, n)
+
+
+def amg_solve_many(h: Hierarchy, b, x, m: int, rtol: float = 1e-6, maxit: int = 1000) -> list:
+    """One CG per system on concatenated device vectors b, x; returns m info dicts."""
+    infos = (amg_solve_info * m)()
+    st = _check(lib().amg_solve_many(h.handle, _ptr(b), _ptr(x), float(rtol), int(maxit), infos))
+    return [_info_dict(infos[s], st) for s in range(m)]
+
+
+def amg_system_offsets(h: Hierarchy, m: int) -> np.ndarray:
+    off = np.empty(m + 1, dtype=np.int32)
+    _check(lib().amg_system_offsets(h.handle, off.ctypes.data_as(_i32p)))
+    return off
 
 
 def amg_vcycle(h: Hierarchy, r, z) -> None:

@@ -220,6 +220,12 @@ struct amg_hierarchy {
     amg::PcgScalars* sc_host = nullptr; // pinned mirror
     amg::Reducer red;
     amg::BlockWork* blk = nullptr;      // block-solve workspace, created on first use
+    // batch of independent systems (block-diagonal union): system offsets
+    std::vector<int> seg0;               // level 0, m + 1 entries (empty: one system)
+    std::vector<std::vector<int>> segs;  // per level
+    int* seg_row0 = nullptr;             // device: system of each level-0 row
+    int* segL_ptr = nullptr;             // device: coarsest-level system offsets
+    long long* segL_blk = nullptr;       // device: offsets of the per-system dense inverses
     double setup_ms = 0.0;
     amg::Profiler prof;
     std::mutex lock;
@@ -252,6 +258,9 @@ void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x);
 amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,
                        amg_solve_info* infos);
 void block_free(amg_hierarchy* h);
+// Batch of independent systems (many.cu, setup_many in setup.cu).
+void setup_many(amg_hierarchy* h, int m, const amg_csr* As, const double* const* ws);
+amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* infos);
 // Solve server (serve.cu).
 amg_server* serve_create(int nh, amg_hierarchy* const* hs, int K, size_t budget, double rtol, int maxit);
 void serve_free(amg_server* S);

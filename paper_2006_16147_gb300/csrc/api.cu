@@ -45,10 +45,17 @@ amg_status check_csr(const amg_csr* A, const double* w) {
     return AMG_OK;
 }
 
-amg_status setup_common(const amg_csr* A, const double* w, const amg_options* opt, amg_hierarchy** out) {
+amg_status setup_common(const amg_csr* A, const double* w, const amg_options* opt, amg_hierarchy** out,
+                        int many = 0, const double* const* ws = nullptr) {
     if (!out) return fail(AMG_ERR_ARG, "out is null");
     *out = nullptr;
-    amg_status s = check_csr(A, w);
+    amg_status s = AMG_OK;
+    if (many) {
+        if (!A || !ws) return fail(AMG_ERR_ARG, "null argument");
+        for (int i = 0; i < many && s == AMG_OK; ++i) s = check_csr(&A[i], ws[i]);
+    } else {
+        s = check_csr(A, w);
+    }
     if (s != AMG_OK) return s;
     amg_options o;
     if (opt) o = *opt;
@@ -64,7 +71,8 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     s = guarded([&]() -> amg_status {
         CUDA_CHECK(cudaGetDevice(&h->device));
         CUDA_CHECK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
-        amg::setup_hierarchy(h, A, w);
+        if (many) amg::setup_many(h, many, A, ws);
+        else amg::setup_hierarchy(h, A, w);
         amg::prepare_solve(h);
         return AMG_OK;
     });
@@ -150,6 +158,36 @@ amg_status amg_solve_host(amg_hierarchy* h, const double* b, double* x, double r
         if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         return s;
     });
+}
+
+amg_status amg_setup_many(int m, const amg_csr* As, const double* const* ws, const amg_options* opt,
+                          amg_hierarchy** out) {
+    if (m < 1) return fail(AMG_ERR_ARG, "m must be >= 1");
+    return setup_common(As, nullptr, opt, out, m, ws);
+}
+
+amg_status amg_solve_many(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit,
+                          amg_solve_info* infos) {
+    if (!h || !b || !x) return fail(AMG_ERR_ARG, "null argument");
+    if (!(rtol > 0.0) || maxit < 0) return fail(AMG_ERR_ARG, "rtol must be > 0 and maxit >= 0");
+    std::lock_guard<std::mutex> g(h->lock);
+    return guarded([&]() -> amg_status {
+        bind_device(h);
+        amg_status s = amg::solve_many(h, b, x, rtol, maxit, infos);
+        if (s == AMG_ERR_BREAKDOWN) amg::set_last_error("CG breakdown in at least one system");
+        return s;
+    });
+}
+
+amg_status amg_system_offsets(const amg_hierarchy* h, int32_t* offsets) {
+    if (!h || !offsets) return fail(AMG_ERR_ARG, "null argument");
+    if (h->seg0.empty()) {
+        offsets[0] = 0;
+        offsets[1] = h->lev[0].A.n;
+        return AMG_OK;
+    }
+    for (size_t i = 0; i < h->seg0.size(); ++i) offsets[i] = h->seg0[i];
+    return AMG_OK;
 }
 
 amg_status amg_solve_batch(amg_hierarchy* h, int k, const double* B, double* X, double rtol, int maxit,

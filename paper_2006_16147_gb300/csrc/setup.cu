@@ -7,6 +7,7 @@
 // choices: weights (Eq. 3), the pair normalisation (Eq. 4) and the Galerkin
 // sums use explicitly rounded operations (__dmul_rn, __dadd_rn, ...), never a
 // fused multiply-add, in a fixed order that is part of the definition.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -660,6 +661,31 @@ __global__ void k_split_rows(int n, const int* __restrict__ flag, const int* __r
     }
 }
 
+// Segment boundaries of the next level: aggregates are numbered by their
+// smallest member and never cross systems, so system s starts at the number
+// of aggregates whose head precedes its first row.
+__global__ void k_seg_map(int m, const int* __restrict__ seg, const int* __restrict__ qid, int n, int nc,
+                          int* __restrict__ out) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= m; s += gridDim.x * blockDim.x)
+        out[s] = seg[s] < n ? qid[seg[s]] : nc;
+}
+
+__global__ void k_seg_rows(int m, const int* __restrict__ seg, int* __restrict__ seg_row) {
+    const int s = blockIdx.x;
+    if (s >= m) return;
+    for (int i = seg[s] + threadIdx.x; i < seg[s + 1]; i += blockDim.x) seg_row[i] = s;
+}
+
+// Dense lower triangle of the diagonal block [r0, r0 + n) (block-diagonal matrix).
+__global__ void k_dense_lower_block(int n, int r0, const int* __restrict__ ptr, const int* __restrict__ col,
+                                    const double* __restrict__ val, double* __restrict__ D) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = ptr[r0 + i]; k < ptr[r0 + i + 1]; ++k) {
+            const int j = col[k] - r0;
+            if (j >= 0 && j <= i) D[(size_t)j * n + i] = val[k];
+        }
+}
+
 // ----------------------------------------------- coarsest: dense Cholesky --
 __global__ void k_dense_lower(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                               const double* __restrict__ val, double* __restrict__ D) {
@@ -1058,10 +1084,33 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "smooth vector w has a zero or non-finite entry");
     }
 
-    // ---- level loop (Section 3.2 coarsening, Section 5 stop rule)
+    // ---- batch of systems: level-0 offsets on the device
+    const int nseg = h->seg0.size() > 1 ? (int)h->seg0.size() - 1 : 0;
+    int* seg_dev = nullptr;
+    int* seg_next = nullptr;
+    h->segs.clear();
+    if (nseg) {
+        if (h->seg0.front() != 0 || h->seg0.back() != n0) AMG_THROW(AMG_ERR_ARG, "system offsets do not cover A");
+        seg_dev = S.mem.alloc<int>(nseg + 1);
+        seg_next = S.mem.alloc<int>(nseg + 1);
+        CUDA_CHECK(cudaMemcpyAsync(seg_dev, h->seg0.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, st));
+        h->segs.push_back(h->seg0);
+        h->seg_row0 = h->mem.alloc<int>(n0);
+        k_seg_rows<<<nseg, TPB, 0, st>>>(nseg, seg_dev, h->seg_row0);
+        KERNEL_CHECK();
+    }
+    auto largest_system = [&](int l) {
+        int mx = 0;
+        for (int s2 = 0; s2 < nseg; ++s2) mx = std::max(mx, h->segs[l][s2 + 1] - h->segs[l][s2]);
+        return mx;
+    };
+
+    // ---- level loop (Section 3.2 coarsening, Section 5 stop rule; for a
+    // batch of systems the rule applies to the largest system)
     for (;;) {
         const int l = (int)h->lev.size() - 1;
-        if (h->lev[l].A.n <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
+        const int size_rule = nseg ? largest_system(l) : h->lev[l].A.n;
+        if (size_rule <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
         const int nl = h->lev[l].A.n;
         DevCsr A = h->lev[l].A;
         double* w = h->lev[l].w;
@@ -1093,6 +1142,11 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 nc = read_int(S.cnt + 6, S.host, st);
             }
             if (nc == n) break;                                   // nothing matched: end the level
+            if (nseg) {
+                k_seg_map<<<1, TPB, 0, st>>>(nseg, seg_dev, S.qid, n, nc, seg_next);
+                KERNEL_CHECK();
+                std::swap(seg_dev, seg_next);
+            }
             SweepOut sw;
             sw.nc = nc;
             sw.agg = h->mem.alloc<int>(n);
@@ -1144,6 +1198,12 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             h->mem.release(p_l);
             break;
         }
+        if (nseg) {
+            std::vector<int> sp(nseg + 1);
+            CUDA_CHECK(cudaMemcpyAsync(sp.data(), seg_dev, sizeof(int) * (nseg + 1), cudaMemcpyDeviceToHost, st));
+            CUDA_CHECK(cudaStreamSynchronize(st));
+            h->segs.push_back(sp);
+        }
         Level& cur = h->lev[l];
         cur.agg = agg_l;
         cur.p = p_l;
@@ -1185,14 +1245,53 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         }
     }
 
-    // ---- coarsest level: dense Cholesky and explicit inverse
+    // ---- coarsest level: dense Cholesky and explicit inverse (per system
+    // for a batch of systems: the coarsest matrix is block diagonal)
     {
         Level& Lc = h->lev.back();
         const int nc = Lc.A.n;
         h->nc = nc;
-        h->coarse_cg = nc > o.max_dense ? 1 : 0;
+        h->coarse_cg = (!nseg && nc > o.max_dense) ? 1 : 0;
     }
-    if (!h->coarse_cg) {
+    if (nseg) {
+        Level& Lc = h->lev.back();
+        const std::vector<int>& sp = h->segs.back();
+        std::vector<long long> boff(nseg + 1, 0);
+        for (int s2 = 0; s2 < nseg; ++s2) {
+            const long long ns = sp[s2 + 1] - sp[s2];
+            if (ns > o.max_dense) AMG_THROW(AMG_ERR_TOO_LARGE, "coarsest block of system %d has %lld rows", s2, ns);
+            boff[s2 + 1] = boff[s2] + ns * ns;
+        }
+        Scope sc_(&h->prof, st, S_COARSE, 0.0);
+        h->coarse_inv = h->mem.alloc<double>(boff[nseg] > 0 ? boff[nseg] : 1);
+        h->coarse_L = nullptr;
+        h->segL_ptr = h->mem.alloc<int>(nseg + 1);
+        h->segL_blk = h->mem.alloc<long long>(nseg + 1);
+        CUDA_CHECK(cudaMemcpyAsync(h->segL_ptr, sp.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, st));
+        CUDA_CHECK(cudaMemcpyAsync(h->segL_blk, boff.data(), sizeof(long long) * (nseg + 1), cudaMemcpyHostToDevice, st));
+        int maxb = 0;
+        for (int s2 = 0; s2 < nseg; ++s2) maxb = std::max(maxb, sp[s2 + 1] - sp[s2]);
+        double* D = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+        double* Lf = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+        double* Y = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
+        for (int s2 = 0; s2 < nseg; ++s2) {
+            const int ns = sp[s2 + 1] - sp[s2];
+            if (ns == 0) continue;
+            CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * ns * ns, st));
+            CUDA_CHECK(cudaMemsetAsync(Lf, 0, sizeof(double) * ns * ns, st));
+            k_dense_lower_block<<<grid_for(h, ns), TPB, 0, st>>>(ns, sp[s2], Lc.A.ptr, Lc.A.col, Lc.A.val, D);
+            KERNEL_CHECK();
+            k_cholesky<<<1, 1024, 0, st>>>(ns, D, Lf, S.cnt + 5);
+            KERNEL_CHECK();
+            k_lower_inverse<<<(ns + 127) / 128, 128, 0, st>>>(ns, Lf, Y);
+            KERNEL_CHECK();
+            k_gram<<<(int)(((long long)ns * ns + 255) / 256), 256, 0, st>>>(ns, Y, h->coarse_inv + boff[s2]);
+            KERNEL_CHECK();
+        }
+        if (read_int(S.cnt + 5, S.host, st)) AMG_THROW(AMG_ERR_NOT_SPD, "a coarsest block hit a non-positive pivot");
+    }
+    if (!h->coarse_cg && !nseg) {
         Level& Lc = h->lev.back();
         const int nc = Lc.A.n;
         Scope sc_(&h->prof, st, S_COARSE, 0.0);
@@ -1337,6 +1436,54 @@ amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void*
     const int rounds = noalloc_read_int(cnt + 4, st);
     if (rounds_out) *rounds_out = rounds;
     return AMG_OK;
+}
+
+}  // namespace amg
+
+namespace amg {
+namespace {
+__global__ void k_cat_ptr(int n, const int* __restrict__ src, int nnz_off, int* __restrict__ dst, int last) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+        if (i < n || last) dst[i] = src[i] + nnz_off;
+}
+__global__ void k_cat_col(long long nnz, const int* __restrict__ src, int col_off, int* __restrict__ dst) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = src[k] + col_off;
+}
+}  // namespace
+
+// Block-diagonal union of m systems (device arrays), set up as one hierarchy
+// that keeps every system's row offsets.
+void setup_many(amg_hierarchy* h, int m, const amg_csr* As, const double* const* ws) {
+    cudaStream_t st = h->stream;
+    long long n = 0, nnz = 0;
+    h->seg0.assign(m + 1, 0);
+    for (int s = 0; s < m; ++s) {
+        n += As[s].n;
+        nnz += As[s].nnz;
+        h->seg0[s + 1] = (int)n;
+        if (n > 0x7ffffffe || nnz > 0x7ffffffe) AMG_THROW(AMG_ERR_TOO_LARGE, "the union exceeds int32 sizes");
+    }
+    DevArena tmp;
+    int* ptr = tmp.alloc<int>(n + 1);
+    int* col = tmp.alloc<int>(nnz);
+    double* val = tmp.alloc<double>(nnz);
+    double* w = tmp.alloc<double>(n);
+    long long ro = 0, no = 0;
+    for (int s = 0; s < m; ++s) {
+        const amg_csr& A = As[s];
+        k_cat_ptr<<<blocks_for(A.n + 1, TPB, h->num_sms * 8), TPB, 0, st>>>(A.n, A.row_ptr, (int)no, ptr + ro,
+                                                                          s == m - 1);
+        KERNEL_CHECK();
+        k_cat_col<<<blocks_for(A.nnz, TPB, h->num_sms * 8), TPB, 0, st>>>(A.nnz, A.col, (int)ro, col + no);
+        KERNEL_CHECK();
+        CUDA_CHECK(cudaMemcpyAsync(val + no, A.val, sizeof(double) * (size_t)A.nnz, cudaMemcpyDefault, st));
+        CUDA_CHECK(cudaMemcpyAsync(w + ro, ws[s], sizeof(double) * (size_t)A.n, cudaMemcpyDefault, st));
+        ro += A.n;
+        no += A.nnz;
+    }
+    amg_csr U{(int32_t)n, (int32_t)nnz, ptr, col, val};
+    setup_hierarchy(h, &U, w);
 }
 
 }  // namespace amg

@@ -405,6 +405,28 @@ __global__ void __launch_bounds__(512) k_coarse_cg(SellView S, const double* __r
     for (int i = tid; i < n; i += stride) xout[i] = (TO)x[i];
 }
 
+// Block-diagonal coarsest level of a batch of systems: x_i = sum_j of the
+// system's dense inverse block times b, one warp per row.
+template <typename T, typename TO>
+__global__ void k_coarse_solve_seg(int n, int m, const int* __restrict__ segp, const long long* __restrict__ blk,
+                                   const double* __restrict__ Ainv, const T* __restrict__ b, TO* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (segp[mid] <= i) lo = mid; else hi = mid;
+        }
+        const int r0 = segp[lo], ns = segp[lo + 1] - r0;
+        const double* row = Ainv + blk[lo] + (long long)(i - r0) * ns;
+        double acc = 0.0;
+        for (int j = lane; j < ns; j += 32) acc = fma(row[j], (double)b[r0 + j], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) x[i] = (TO)acc;
+    }
+}
+
 // ------------------------------------------------------------- PCG ---------
 // r = b - A x; ||r||^2 and ||b||^2.
 __global__ void __launch_bounds__(TPB) k_residual(SellView S, const double* __restrict__ val,
@@ -496,6 +518,22 @@ int red_grid(const amg_hierarchy* h) { return h->red.blocks; }
 
 void coarse_solve_launch(amg_hierarchy* h, const void* b, void* x, bool fp32_in, bool fp64_out) {
     const int n = h->nc;
+    if (h->segL_ptr) {
+        const int m = (int)h->seg0.size() - 1;
+        const int grid = blocks_for((long long)n * 32, 256, h->num_sms * 8);
+        Scope sc_(&h->prof, h->stream, K_COARSE, 16.0 * n);
+        if (!fp32_in)
+            k_coarse_solve_seg<double, double><<<grid, 256, 0, h->stream>>>(n, m, h->segL_ptr, h->segL_blk,
+                                                                            h->coarse_inv, (const double*)b, (double*)x);
+        else if (fp64_out)
+            k_coarse_solve_seg<float, double><<<grid, 256, 0, h->stream>>>(n, m, h->segL_ptr, h->segL_blk,
+                                                                           h->coarse_inv, (const float*)b, (double*)x);
+        else
+            k_coarse_solve_seg<float, float><<<grid, 256, 0, h->stream>>>(n, m, h->segL_ptr, h->segL_blk,
+                                                                          h->coarse_inv, (const float*)b, (float*)x);
+        KERNEL_CHECK();
+        return;
+    }
     if (h->coarse_cg) {
         Level& Lc = h->lev.back();
         CoarseCg& C = h->ccg;
@@ -733,6 +771,8 @@ void prepare_solve(amg_hierarchy* h) {
 }
 
 void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x) { coarse_solve_launch(h, b, x, false, true); }
+
+void vcycle_plain(amg_hierarchy* h, const double* r, double* z) { vcycle_dispatch(h, r, z, FIN_NONE); }
 
 void vcycle_apply(amg_hierarchy* h, const double* r, double* z) {
     vcycle_dispatch(h, r, z, FIN_NONE);

@@ -28,6 +28,7 @@ __all__ = [
     "rhs_uniform",
     "rhs_normal",
     "batch_edges",
+    "block_diagonal",
     "random_spd",
 ]
 
@@ -171,6 +172,20 @@ def batch_edges(m: int, seed: int, lo: int = 16, hi: int = 64) -> list[int]:
     """Grid edge lengths of m independent Poisson systems, uniform in lo..hi."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return [int(e) for e in rng.integers(lo, hi + 1, size=m)]
+
+
+def block_diagonal(mats: list) -> tuple:
+    """Union of systems as one block-diagonal CSR; returns (Csr, row offsets)."""
+    offs = np.zeros(len(mats) + 1, dtype=np.int64)
+    for i, M in enumerate(mats):
+        offs[i + 1] = offs[i] + M.n
+    nnz = np.zeros(len(mats) + 1, dtype=np.int64)
+    for i, M in enumerate(mats):
+        nnz[i + 1] = nnz[i] + M.nnz
+    rp = np.concatenate([M.row_ptr[:-1].astype(np.int64) + nnz[i] for i, M in enumerate(mats)] + [[nnz[-1]]])
+    col = np.concatenate([M.col.astype(np.int64) + offs[i] for i, M in enumerate(mats)])
+    val = np.concatenate([M.val for M in mats])
+    return Csr(rp, col, val, "block_diagonal"), offs.astype(np.int32)
 
 
 def random_spd(n: int, density: float, seed: int) -> Csr:
