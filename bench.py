@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: 5 cached hierarchies, Poisson arrivals, p50/p99 latency and solves/s")
     ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--many", action="store_true",
+                    help="batched benchmark: 256 independent Poisson systems, grid edges uniform in 16..64")
+    ap.add_argument("--many-systems", type=int, default=256)
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="grid scale factor of the served problems (1.0 = 64^3/128^3/192^3/2048^2/128^3)")
     return ap.parse_args()
@@ -308,12 +311,151 @@ def serve_arm(args):
     return 0
 
 
+def many_arm(args):
+    """Many uneven independent systems in one hierarchy and one solve.
+
+    256 3D Poisson systems with grid edges drawn uniformly from 16..64 (seed 5,
+    4,096 to 262,144 unknowns each), right-hand sides N(0, 1) (seed 5), x0 = 0,
+    rel-res 1e-6 per system. One step = amg_setup_many + amg_solve_many +
+    amg_free with the systems resident in HBM. Beside it: the same systems
+    set up and solved one at a time with the plain FP64 method.
+    """
+    import torch
+    from paper_2006_16147_gb300 import amg
+    from paper_2006_16147_gb300 import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    amg.lib()
+    edges = W.batch_edges(args.many_systems, seed=5)
+    mats = [W.poisson3d(e) for e in edges]
+    offs = np.concatenate([[0], np.cumsum([M.n for M in mats])]).astype(np.int64)
+    ntot = int(offs[-1])
+    nnz_tot = sum(M.nnz for M in mats)
+    b = W.rhs_normal(ntot, seed=5)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    systems = [(t(M.row_ptr), t(M.col), t(M.val), torch.ones(M.n, dtype=torch.float64, device=dev)) for M in mats]
+    d_b = t(b)
+    d_x = torch.zeros(ntot, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = amg.AMG_FP32_VCYCLE if args.precision == "fp32" else amg.AMG_FP64
+    m = len(mats)
+
+    def step():
+        d_x.zero_()
+        h = amg.amg_setup_many(systems, precision=prec, krylov=args.krylov, stream=stream.cuda_stream)
+        infos = amg.amg_solve_many(h, d_b, d_x, m, rtol=args.rtol, maxit=1000)
+        hi = amg.amg_hierarchy_info(h)
+        h.close()
+        return infos, hi
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = amg.amg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            runs.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (amg.amg_launch_count() - launches0) // args.steps
+    clocks = clk.summary()
+    infos, hi = runs[-1]
+    xs = d_x.cpu().numpy()
+    worst = 0.0
+    for s, M in enumerate(mats):
+        bs = b[offs[s]:offs[s + 1]]
+        worst = max(worst, float(np.linalg.norm(bs - M.scipy() @ xs[offs[s]:offs[s + 1]]) / np.linalg.norm(bs)))
+    its = [i["iterations"] for i in infos]
+
+    # the same systems one at a time, plain FP64 (setup + solve each)
+    torch.cuda.synchronize()
+    xo = torch.zeros(int(max(M.n for M in mats)), dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s, (rp, cl, vl, w) in enumerate(systems):
+        h = amg.amg_setup(rp, cl, vl, w, stream=stream.cuda_stream)
+        xo[:mats[s].n].zero_()
+        amg.amg_solve(h, d_b[offs[s]:offs[s + 1]], xo[:mats[s].n], rtol=args.rtol, maxit=1000)
+        h.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solo_ms = e0.elapsed_time(e1)
+
+    # end to end: systems and right-hand sides copied from pinned host memory
+    # inside the timed region, solutions read back
+    hp = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (M.row_ptr, M.col, M.val))
+          for M in mats]
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.empty(ntot, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sy = [(rp.to(dev, non_blocking=True), cl.to(dev, non_blocking=True), vl.to(dev, non_blocking=True),
+               torch.ones(rp.shape[0] - 1, dtype=torch.float64, device=dev)) for rp, cl, vl in hp]
+        db = bh.to(dev, non_blocking=True)
+        dx = torch.zeros(ntot, dtype=torch.float64, device=dev)
+        h = amg.amg_setup_many(sy, precision=prec, krylov=args.krylov, stream=stream.cuda_stream)
+        amg.amg_solve_many(h, db, dx, m, rtol=args.rtol, maxit=1000)
+        h.close()
+        xh.copy_(dx)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    h2d = sum(M.row_ptr.nbytes + M.col.nbytes + M.val.nbytes for M in mats) + b.nbytes
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        done = 0
+        for s, M in enumerate(mats):
+            H = oracle.Hierarchy(M)
+            H.pcg(b[offs[s]:offs[s + 1]], rtol=args.rtol)
+            done += M.n
+            if time.perf_counter() - t0 > 10.0:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": el * 1e3 * ntot / done, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"oracle setup + PCG of the first {s + 1} systems ({done} unknowns, {el:.1f} s), "
+                         f"scaled by unknowns x{ntot / done:.1f}"}
+
+    if rank == 0:
+        line = {
+            "metric": f"batched AMG-PCG: {m} independent systems to rel-res 1e-6 (setup + solve)",
+            "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle", "data": "synthetic",
+            "config": {"workload": f"{m}_poisson3d_edges16-64_seed5", "systems": m, "n": ntot, "nnz": nnz_tot,
+                       "edges_min": min(edges), "edges_max": max(edges), "rtol": args.rtol,
+                       "precision": args.precision, "l2": "inputs larger than L2, no flush"},
+            "systems_per_s": round(m * 1e3 / ms, 1),
+            "iterations_max": max(its), "iterations_mean": round(float(np.mean(its)), 2),
+            "worst_numpy_relres": worst, "levels": hi["n"],
+            "one_at_a_time_fp64_ms": round(solo_ms, 2), "speedup_vs_one_at_a_time": round(solo_ms / ms, 2),
+            "gpu_launches": int(launches), "clocks": clocks,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * ntot},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.serve:
         return serve_arm(args)
+    if args.many:
+        return many_arm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

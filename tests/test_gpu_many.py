@@ -154,3 +154,25 @@ def test_setup_many_rejects_bad_system():
     bad_col[3] = A.n + 7
     with pytest.raises(amg.AmgError):
         _setup_many([A, W.Csr(A.row_ptr, bad_col, A.val)], [np.ones(A.n), np.ones(A.n)])
+
+
+def test_solve_many_fp32_vcycle():
+    # FP32 V-cycle inside the per-system FP64 CG: every system still reaches
+    # the FP64 true residual bound, within a few iterations of the FP64 run
+    import torch
+    from paper_2006_16147_gb300 import amg
+    mats = _mats("mixed")
+    U, offs = W.block_diagonal(mats)
+    b = dev(np.random.default_rng(12).normal(size=U.n))
+    its = {}
+    for prec in (amg.AMG_FP64, amg.AMG_FP32_VCYCLE):
+        h = _setup_many(mats, [np.ones(M.n) for M in mats], precision=prec)
+        x = torch.zeros(U.n, dtype=torch.float64, device="cuda:0")
+        infos = amg.amg_solve_many(h, b, x, len(mats), rtol=1e-8)
+        xg, bh = x.cpu().numpy(), b.cpu().numpy()
+        for s, M in enumerate(mats):
+            bs = bh[offs[s]:offs[s + 1]]
+            assert np.linalg.norm(bs - M.scipy() @ xg[offs[s]:offs[s + 1]]) <= 1e-8 * np.linalg.norm(bs), (prec, s)
+        its[prec] = [i["iterations"] for i in infos]
+        h.close()
+    assert all(abs(a - c) <= 3 for a, c in zip(its[amg.AMG_FP64], its[amg.AMG_FP32_VCYCLE])), its
