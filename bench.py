@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--rtol", type=float, default=1e-6)
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
+                    help="1: autotuned launch shapes (timed once per shape, during warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-grid", type=int, default=128)
@@ -53,6 +55,9 @@ def _args():
     ap.add_argument("--many", action="store_true",
                     help="batched benchmark: 256 independent Poisson systems, grid edges uniform in 16..64")
     ap.add_argument("--many-systems", type=int, default=256)
+    ap.add_argument("--block", type=int, default=0,
+                    help="multi-RHS benchmark: K right-hand sides (N(0,1), seed 4) on one Poisson hierarchy")
+    ap.add_argument("--block-grid", type=int, default=128)
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="grid scale factor of the served problems (1.0 = 64^3/128^3/192^3/2048^2/128^3)")
     return ap.parse_args()
@@ -345,7 +350,8 @@ def many_arm(args):
 
     def step():
         d_x.zero_()
-        h = amg.amg_setup_many(systems, precision=prec, krylov=args.krylov, stream=stream.cuda_stream)
+        h = amg.amg_setup_many(systems, precision=prec, krylov=args.krylov, autotune=args.autotune,
+                               stream=stream.cuda_stream)
         infos = amg.amg_solve_many(h, d_b, d_x, m, rtol=args.rtol, maxit=1000)
         hi = amg.amg_hierarchy_info(h)
         h.close()
@@ -435,7 +441,8 @@ def many_arm(args):
             "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle", "data": "synthetic",
             "config": {"workload": f"{m}_poisson3d_edges16-64_seed5", "systems": m, "n": ntot, "nnz": nnz_tot,
                        "edges_min": min(edges), "edges_max": max(edges), "rtol": args.rtol,
-                       "precision": args.precision, "l2": "inputs larger than L2, no flush"},
+                       "precision": args.precision, "autotune": args.autotune,
+                       "l2": "inputs larger than L2, no flush"},
             "systems_per_s": round(m * 1e3 / ms, 1),
             "iterations_max": max(its), "iterations_mean": round(float(np.mean(its)), 2),
             "worst_numpy_relres": worst, "levels": hi["n"],
@@ -443,6 +450,125 @@ def many_arm(args):
             "gpu_launches": int(launches), "clocks": clocks,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * ntot},
             "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def block_arm(args):
+    """Multi-RHS block solve: 3D Poisson block-grid^3 with K columns.
+
+    Columns N(0, 1) (seed 4), row-major n x K, x0 = 0, rel-res 1e-6 per column.
+    One step = amg_setup + amg_solve_batch + amg_free with A and B resident in
+    HBM. Beside it: the K columns solved one after another on one hierarchy.
+    """
+    import torch
+    from paper_2006_16147_gb300 import amg
+    from paper_2006_16147_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    amg.lib()
+    K = args.block
+    A = W.poisson3d(args.block_grid)
+    B = W.rhs_normal(A.n, seed=4, k=K)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d_ptr, d_col, d_val = t(A.row_ptr), t(A.col), t(A.val)
+    d_w = torch.ones(A.n, dtype=torch.float64, device=dev)
+    d_B = t(B)
+    d_X = torch.zeros(A.n, K, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = amg.AMG_FP32_VCYCLE if args.precision == "fp32" else amg.AMG_FP64
+
+    def step(profile=0):
+        d_X.zero_()
+        h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov, autotune=args.autotune,
+                          profile=profile, stream=stream.cuda_stream)
+        infos = amg.amg_solve_batch(h, d_B, d_X, rtol=args.rtol, maxit=1000)
+        return h, infos
+
+    for _ in range(args.warmup):
+        h, _ = step()
+        h.close()
+    torch.cuda.synchronize()
+    launches0 = amg.amg_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kstats = {}
+    solve_ms = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            h, infos = step(profile=1)
+            solve_ms.append(infos[0]["solve_ms"])
+            for name, (sc, kms, by) in amg.amg_kernel_stats(h).items():
+                s_ = kstats.setdefault(name, [0, 0.0, 0.0])
+                s_[0] += sc
+                s_[1] += kms
+                s_[2] += by
+            hi = amg.amg_hierarchy_info(h)
+            h.close()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (amg.amg_launch_count() - launches0) // args.steps
+    clocks = clk.summary()
+    X = d_X.cpu().numpy()
+    R = B - A.scipy() @ X
+    worst = float(np.max(np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)))
+    its = [i["iterations"] for i in infos]
+
+    # the same columns one after another on one hierarchy (solve only), and
+    # the batch solve alone on that hierarchy
+    h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov, autotune=args.autotune,
+                      stream=stream.cuda_stream)
+    xc = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    cols = [d_B[:, c].contiguous() for c in range(K)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seq_its = []
+    e0.record(stream)
+    for c in range(K):
+        xc.zero_()
+        seq_its.append(amg.amg_solve(h, cols[c], xc, rtol=args.rtol, maxit=1000)["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    d_X.zero_()
+    e0.record(stream)
+    amg.amg_solve_batch(h, d_B, d_X, rtol=args.rtol, maxit=1000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_solve_ms = e0.elapsed_time(e1)
+    h.close()
+
+    peak, peak_kind = _peaks()
+    dom = max((k for k in kstats if not k.startswith("setup_")), key=lambda k: kstats[k][1])
+    nl, kms, by = kstats[dom]
+    achieved = (by / nl) / (kms / nl * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_launch": by / nl, "ms_per_launch": kms / nl}
+    kernel_table = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": round(v[1] / args.steps, 4),
+                        "GBps": round(v[2] / max(v[1], 1e-12) / 1e6, 1) if v[2] else None}
+                    for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+    if rank == 0:
+        line = {
+            "metric": f"multi-RHS AMG-PCG: {K} right-hand sides to rel-res 1e-6 (setup + block solve)",
+            "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle", "data": "synthetic",
+            "config": {"workload": f"poisson3d_{args.block_grid}^3_{K}rhs_seed4", "n": A.n, "nnz": A.nnz, "k": K,
+                       "rtol": args.rtol, "precision": args.precision, "autotune": args.autotune,
+                       "l2": "inputs larger than L2, no flush"},
+            "columns_per_s": round(K * 1e3 / ms, 1), "iterations_max": max(its),
+            "iterations_mean": round(float(np.mean(its)), 2), "worst_numpy_relres": worst,
+            "levels": hi["n"], "block_solve_ms": round(batch_solve_ms, 2),
+            "sequential_single_rhs_solve_ms": round(seq_ms, 2), "sequential_iterations_max": max(seq_its),
+            "sequential_iterations_mean": round(float(np.mean(seq_its)), 2),
+            "speedup_vs_sequential": round(seq_ms / batch_solve_ms, 2),
+            "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     return 0
@@ -456,6 +582,8 @@ def main():
         return serve_arm(args)
     if args.many:
         return many_arm(args)
+    if args.block:
+        return block_arm(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -483,7 +611,7 @@ def main():
     def step(profile=0, keep=False):
         d_x.zero_()
         h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, krylov=args.krylov,
-                          stream=stream.cuda_stream)
+                          autotune=args.autotune, stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
             return h, info
@@ -609,7 +737,8 @@ def main():
                        "grid": args.grid,
                        "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
                        "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",
-                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single"},
+                       "precision": args.precision, "autotune": args.autotune,
+                       "parallelism": "replicas" if world > 1 else "single"},
             "iterations": it[-1], "true_relres": infos[-1]["true_relres"], "numpy_relres": rel,
             "setup_ms": round(statistics.mean(h["setup_ms"] for h in hinfos), 3),
             "solve_ms": round(statistics.mean(i["solve_ms"] for i in infos), 3),

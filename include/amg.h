@@ -81,6 +81,9 @@ typedef struct {
     int match_kernel;  /* [0] matching rounds in one cooperative launch when possible; 1: a launch pair per round */
     int krylov;        /* [0] 0 = PCG; 1 = flexible CG keeping one direction (FCG(1), the paper's outer
                           solver, Section 5), robust to a V-cycle that is not exactly linear (FP32) */
+    int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
+                          per row and columns per lane of block solves) by timing candidates once per shape;
+                          results are cached per process (see amg_tune_save). 0: fixed heuristics */
     double min_ratio;  /* [1.5] stop coarsening after a level with n_l / n_{l+1} below this (stalled matching) */
     void* stream;      /* [NULL] cudaStream_t for every device operation; NULL = legacy default */
 } amg_options;
@@ -290,6 +293,22 @@ int amg_serve_poll(amg_server* s, int64_t* ids, int* statuses, double* latency_m
                    int max);
 amg_status amg_serve_stats_get(amg_server* s, amg_serve_stats* out);
 void amg_serve_free(amg_server* s);
+
+/*
+ * Launch-shape cache of the autotuner (options.autotune). Each entry maps a
+ * problem shape (kernel, value type, rows, nonzeros, SELL slices, column
+ * count, SM count) to the launch shape that timed fastest. The paper has no
+ * counterpart; the GPU kernels' shapes are tuned, not the method.
+ * amg_tune_save writes the cache as text (one "key value" per line) to a host
+ * file; amg_tune_load merges such a file into the cache (entries with the
+ * same key are replaced; malformed lines give AMG_ERR_ARG after the valid
+ * ones are read); amg_tune_clear empties it; amg_tune_size counts entries.
+ * File errors return AMG_ERR_ARG. Thread-safe.
+ */
+amg_status amg_tune_save(const char* path);
+amg_status amg_tune_load(const char* path);
+void amg_tune_clear(void);
+int amg_tune_size(void);
 
 /* Releases every device allocation of h. NULL is accepted. */
 void amg_free(amg_hierarchy* h);

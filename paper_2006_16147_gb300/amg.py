@@ -28,6 +28,7 @@ STATUS_NAMES = {
     -4: "AMG_ERR_OOM", -5: "AMG_ERR_CUDA", -6: "AMG_ERR_BREAKDOWN", -7: "AMG_ERR_TIMEOUT",
     -8: "AMG_ERR_TOO_LARGE", -9: "AMG_ERR_BUDGET",
 }
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 
 EXPORTED = [
     "amg_options_default", "amg_setup", "amg_setup_host", "amg_solve", "amg_solve_host", "amg_vcycle",
@@ -35,7 +36,7 @@ EXPORTED = [
     "amg_free", "amg_last_error", "amg_kernel_stats_count", "amg_kernel_stats", "amg_kernel_stats_reset",
     "amg_launch_count", "amg_match_noalloc", "amg_solve_batch", "amg_serve_create", "amg_serve_submit",
     "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free", "amg_setup_many",
-    "amg_solve_many", "amg_system_offsets",
+    "amg_solve_many", "amg_system_offsets", "amg_tune_save", "amg_tune_load", "amg_tune_clear", "amg_tune_size",
 ]
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_NNZ = 524288
@@ -51,7 +52,7 @@ class amg_options(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
                 ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("autotune", ctypes.c_int), ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):
@@ -155,6 +156,13 @@ def lib() -> ctypes.CDLL:
         L.amg_match_noalloc.restype = ctypes.c_int
         L.amg_launch_count.argtypes = []
         L.amg_launch_count.restype = ctypes.c_int64
+        for name in ("amg_tune_save", "amg_tune_load"):
+            getattr(L, name).argtypes = [ctypes.c_char_p]
+            getattr(L, name).restype = ctypes.c_int
+        L.amg_tune_clear.argtypes = []
+        L.amg_tune_clear.restype = None
+        L.amg_tune_size.argtypes = []
+        L.amg_tune_size.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -353,6 +361,24 @@ def amg_kernel_stats(h: Hierarchy) -> dict:
 
 def amg_kernel_stats_reset(h: Hierarchy) -> None:
     _check(lib().amg_kernel_stats_reset(h.handle))
+
+
+def amg_tune_save(path: str) -> None:
+    """Write the launch-shape cache of the autotuner to a text file."""
+    _check(lib().amg_tune_save(os.fsencode(path)))
+
+
+def amg_tune_load(path: str) -> None:
+    """Merge a launch-shape cache file into the process cache."""
+    _check(lib().amg_tune_load(os.fsencode(path)))
+
+
+def amg_tune_clear() -> None:
+    lib().amg_tune_clear()
+
+
+def amg_tune_size() -> int:
+    return int(lib().amg_tune_size())
 
 
 def amg_launch_count() -> int:

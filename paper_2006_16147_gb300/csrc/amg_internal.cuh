@@ -135,6 +135,9 @@ struct Level {
     int sweeps_done = 0;
     int rounds[AMG_MAX_SWEEPS] = {0};
     std::vector<SweepRecord> sweeps;
+    // launch shapes chosen by the autotuner, indexed by value type (0 FP64,
+    // 1 FP32); 0 = the fixed heuristic
+    int grid_pre[2] = {0, 0}, grid_post[2] = {0, 0}, grid_restrict[2] = {0, 0};
     // V-cycle work vectors (FP64 and FP32 copies)
     double *b = nullptr, *x = nullptr, *r = nullptr, *y = nullptr, *t = nullptr, *u = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *y32 = nullptr, *t32 = nullptr, *u32 = nullptr;
@@ -176,6 +179,7 @@ struct BlockScalars {
 struct BlockWork {
     int K = 0;
     bool fixed_width = false;           // 32 lanes per row whatever the column count
+    int tuned_G = 0;                    // lanes per row chosen by the autotuner (0: heuristic)
     DevArena mem;
     std::vector<void*> b, x, r, y;      // per level V-cycle vectors (float or double)
     double *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // level 0, FP64
@@ -250,6 +254,32 @@ size_t scan_scratch_ints(int n);
 // Setup and solve entry points used by the api translation unit.
 void setup_hierarchy(amg_hierarchy* h, const amg_csr* A, const double* w);
 void prepare_solve(amg_hierarchy* h);
+
+// Autotuner (tune.cu holds the cache): choose the V-cycle launch shapes of
+// every level by timing candidates (solve.cu).
+bool tune_get(const std::string& key, int* value);
+void tune_put(const std::string& key, int value);
+std::string tune_key(const char* kind, int vbytes, long long n, long long nnz, long long slices, int k, int sms);
+void autotune_vcycle(amg_hierarchy* h);
+
+// Mean time in ms of `reps` launches issued by `launch` on stream st, after
+// one untimed launch.
+template <typename F>
+double time_launches(cudaStream_t st, F&& launch, int reps) {
+    launch();
+    cudaEvent_t e0, e1;
+    CUDA_CHECK(cudaEventCreate(&e0));
+    CUDA_CHECK(cudaEventCreate(&e1));
+    CUDA_CHECK(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; ++i) launch();
+    CUDA_CHECK(cudaEventRecord(e1, st));
+    CUDA_CHECK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)ms / reps;
+}
 amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int maxit, amg_solve_info* info);
 void vcycle_apply(amg_hierarchy* h, const double* r, double* z);
 // Single-column coarsest CG solve on contiguous FP64 vectors (coarse_cg hierarchies).

@@ -62,7 +62,8 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     else amg_options_default(&o);
     if (o.sweeps < 1 || o.sweeps > AMG_MAX_SWEEPS || o.max_levels < 1 || o.max_coarse < 1 || o.pre < 0 ||
         o.post < 0 || !(o.omega > 0.0) || (o.precision != AMG_FP64 && o.precision != AMG_FP32_VCYCLE) ||
-        o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0))
+        o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0) || o.autotune < 0 ||
+        o.autotune > 1)
         return fail(AMG_ERR_ARG, "invalid options");
     amg_hierarchy* h = new amg_hierarchy;
     h->opt = o;
@@ -74,6 +75,7 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
         if (many) amg::setup_many(h, many, A, ws);
         else amg::setup_hierarchy(h, A, w);
         amg::prepare_solve(h);
+        if (o.autotune) amg::autotune_vcycle(h);
         return AMG_OK;
     });
     if (s != AMG_OK) {

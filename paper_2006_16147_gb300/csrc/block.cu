@@ -60,14 +60,39 @@ __device__ __forceinline__ Grp make_grp(int G) {
     return g;
 }
 
-// acc[m] += sum_e val_e * xv(col_e, c) for the row at SELL position ip.
+// acc[m] += sum_e val_e * xv(col_e, c) for the row at SELL position ip, in
+// entry order. Four entries at a time: their indices and values are loaded
+// first and the four gathered rows of X are in flight together, so a row
+// costs about two memory latencies per four entries instead of two per entry.
 template <typename T, int CPL, typename XV>
 __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__ val, int ip, const Grp& g, int k,
                                            XV&& xv, T (&acc)[CPL]) {
     const int s = ip >> 5, r = ip & 31;
-    long long base = (long long)__ldg(S.sptr + s) * 32 + r;
-    const int w = __ldg(S.sptr + s + 1) - __ldg(S.sptr + s);
-    for (int e = 0; e < w; ++e, base += 32) {
+    const int s0 = __ldg(S.sptr + s);
+    const int w = __ldg(S.sptr + s + 1) - s0;
+    long long base = (long long)s0 * 32 + r;
+    int e = 0;
+    for (; e + 4 <= w; e += 4, base += 128) {
+        int j[4];
+        T a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = __ldg(S.col + base + 32 * u);
+            a[u] = __ldg(val + base + 32 * u);
+        }
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) {
+            const int c = g.gl + m * g.G;
+            if (c < k) {
+                T xs[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xs[u] = xv(j[u], c);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[m] = fma(a[u], xs[u], acc[m]);
+            }
+        }
+    }
+    for (; e < w; ++e, base += 32) {
         const int j = __ldg(S.col + base);
         const T a = __ldg(val + base);
 #pragma unroll
@@ -156,6 +181,16 @@ __global__ void __launch_bounds__(TPB) bk_pre(SellV S, const T* __restrict__ val
             }
         }
     }
+}
+
+// FP32 copy of columns [0, k) of the level-0 residual (row-major, leading
+// dimension ld) for the FP32 V-cycle: one conversion per entry instead of one
+// per gathered matrix entry (the FP64 -> FP32 conversion runs at the FP64 rate).
+__global__ void __launch_bounds__(TPB) bk_to_f32(long long n, int k, int ld, const double* __restrict__ a,
+                                                 float* __restrict__ b) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * ld;
+         t += (long long)gridDim.x * blockDim.x)
+        if (k == ld || (int)(t % ld) < k) b[t] = (float)a[t];
 }
 
 template <typename T, int CPL>
@@ -717,7 +752,8 @@ int pow2_at_least(int v) {
 // (set by the slot count K, not by k) a column's arithmetic and reduction
 // order do not depend on how many columns are in flight.
 void group_shape(const BlockWork& W, int k, int* G, int* cpl) {
-    const int g = std::min(32, pow2_at_least(W.fixed_width ? W.K : k));
+    int g = std::min(32, pow2_at_least(W.fixed_width ? W.K : k));
+    if (W.tuned_G && !W.fixed_width) g = std::min(W.tuned_G, pow2_at_least(k));
     *G = g;
     *cpl = pow2_at_least((k + g - 1) / g);
 }
@@ -753,7 +789,12 @@ void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
         const int g = grid_rows(h, Lv.S.n, G);
         Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE,
                   (double)Lv.A.nnz * (sizeof(T) + 4) + (double)Lv.A.n * k * ((l == 0 ? 8 : sizeof(T)) + 2.0 * sizeof(T)));
-        if (l == 0)
+        if (l == 0 && f32) {
+            bk_to_f32<<<blocks_for((long long)Lv.A.n * ld, TPB, h->num_sms * 8), TPB, 0, st>>>(
+                Lv.A.n, k, ld, W.R, reinterpret_cast<float*>(W.b[0]));
+            KERNEL_CHECK();
+        }
+        if (l == 0 && !f32)
             DISPATCH_CPL(cpl, bk_pre<T, double, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, W.R, lv(W.x, 0),
                                                                        lv(W.r, 0), k, ld, G))
         else
@@ -816,6 +857,53 @@ void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
                                   flexible ? W.Q : nullptr, W.Z, k, ld, G, W.partial, W.ticket, W.sc, flexible))
         KERNEL_CHECK();
     }
+}
+
+// Lanes per row of the block V-cycle (G; each lane carries ceil(K/G)
+// columns, at most 8): the candidates are timed on one V-cycle of all K
+// columns, on zeroed work vectors, and the fastest is cached by shape.
+void block_autotune(amg_hierarchy* h, BlockWork& W) {
+    const bool f32 = h->opt.precision == AMG_FP32_VCYCLE;
+    const int V = f32 ? 4 : 8;
+    const Level& L0 = h->lev[0];
+    const std::string key = tune_key("block", V, L0.A.n, L0.A.nnz, (long long)h->lev.size(), W.K, h->num_sms);
+    int best = 0;
+    if (!tune_get(key, &best)) {
+        cudaStream_t st = h->stream;
+        for (size_t l = 0; l < h->lev.size(); ++l) {
+            const size_t m = (size_t)h->lev[l].A.n * W.K * V;
+            for (void* v : {W.b[l], W.x[l], W.r[l], W.y[l]}) CUDA_CHECK(cudaMemsetAsync(v, 0, m, st));
+        }
+        const size_t m0 = (size_t)L0.A.n * W.K * 8;
+        for (double* v : {W.R, W.Z, W.Q}) CUDA_CHECK(cudaMemsetAsync(v, 0, m0, st));
+        const bool prof_on = h->prof.on;
+        h->prof.on = false;
+        double tbest = 1e30;
+        try {
+            for (int G = std::min(32, pow2_at_least(W.K)); G >= 1; G /= 2) {
+                if (pow2_at_least((W.K + G - 1) / G) > 8) break;
+                W.tuned_G = G;
+                const double t = time_launches(st, [&]() {
+                    if (f32) block_vcycle<float>(h, W, W.K, 0);
+                    else block_vcycle<double>(h, W, W.K, 0);
+                }, 2);
+                if (t < tbest) {
+                    tbest = t;
+                    best = G;
+                }
+            }
+        } catch (...) {
+            h->prof.on = prof_on;
+            W.tuned_G = 0;
+            throw;
+        }
+        h->prof.on = prof_on;
+        CUDA_CHECK(cudaMemsetAsync(W.sc.mode, 0, sizeof(int) * W.K, st));
+        CUDA_CHECK(cudaMemsetAsync(W.sc.iters, 0, sizeof(int) * W.K, st));
+        CUDA_CHECK(cudaStreamSynchronize(st));
+        tune_put(key, best);
+    }
+    W.tuned_G = best;
 }
 
 void copy_state_async(amg_hierarchy* h, BlockWork& W) {
@@ -886,6 +974,7 @@ BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width) {
         CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk_coarse_cg<double, double, 8>, TPB, 0));
         if (per_sm < 1) AMG_THROW(AMG_ERR_CUDA, "multi-column coarsest CG kernel cannot be resident");
     }
+    if (h->opt.autotune && !fixed_width) block_autotune(h, *W);
     return *W;
 }
 

@@ -199,6 +199,20 @@ __global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict_
     if (DOT) reduce_and_finish(dot, dot2, red, sc, mode);
 }
 
+// FP32 copy of the level-0 residual for the FP32 V-cycle: one conversion per
+// row here instead of one per gathered matrix entry in the sweep (on this GPU
+// the FP64 -> FP32 conversion runs at the FP64 rate).
+__global__ void __launch_bounds__(TPB) k_to_f32(int n, const double* __restrict__ a, float* __restrict__ b) {
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + stride < n; i += 2 * stride) {
+        const double a0 = a[i], a1 = a[i + stride];
+        b[i] = (float)a0;
+        b[i + stride] = (float)a1;
+    }
+    if (i < n) b[i] = (float)a[i];
+}
+
 // Extra pre-smoothing sweep from (x, r = b - A x):
 //   x' = x + omega M^-1 r,  r' = b - A x'  (x' of neighbours recomputed).
 template <typename T, typename TB>
@@ -615,12 +629,17 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     for (int l = 0; l < L; ++l) {
         Level& Lv = h->lev[l];
         const SellView S = view(Lv);
-        const int g = sell_grid(h, S.nslices);
+        const int g = Lv.grid_pre[f32] ? Lv.grid_pre[f32] : sell_grid(h, S.nslices);
         T *xa = vec(Lv, VX), *ra = vec(Lv, VR), *xb = vec(Lv, VT), *rb = vec(Lv, VU);
         const int Vb = l == 0 ? 8 : V;
+        if (l == 0 && f32) {
+            Scope sc_(&h->prof, st, K_CONVERT, 12.0 * Lv.A.n);
+            k_to_f32<<<vec_grid(h, Lv.A.n), TPB, 0, st>>>(Lv.A.n, r, (float*)vec(Lv, VB));
+            KERNEL_CHECK();
+        }
         {
-            Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, Vb));
-            if (l == 0) k_pre<T, double><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, r, xa, ra);
+            Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 && !f32 ? 8 : V));
+            if (l == 0 && !f32) k_pre<T, double><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, r, xa, ra);
             else k_pre<T, T><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra);
             KERNEL_CHECK();
         }
@@ -637,7 +656,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         spare[l] = (xa == vec(Lv, VX)) ? vec(Lv, VT) : vec(Lv, VX);
         const int nc = h->lev[l + 1].A.n;
         Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(Lv.A.n, nc, V));
-        k_restrict<T><<<vec_grid(h, nc), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, pv(Lv), ra, vec(h->lev[l + 1], VB));
+        k_restrict<T><<<Lv.grid_restrict[f32] ? Lv.grid_restrict[f32] : vec_grid(h, nc), TPB, 0, st>>>(
+            nc, Lv.pt_ptr, Lv.pt_idx, pv(Lv), ra, vec(h->lev[l + 1], VB));
         KERNEL_CHECK();
     }
     // coarsest: FP64 dense solve
@@ -648,7 +668,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         Level& Lv = h->lev[l];
         const SellView S = view(Lv);
         const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col, Lv.AP.perm};
-        const int g = sell_grid(h, S.nslices);
+        const int g = Lv.grid_post[f32] ? Lv.grid_post[f32] : sell_grid(h, S.nslices);
         const T* e = out[l + 1];
         const int nc = h->lev[l + 1].A.n;
         if (l > 0) {
@@ -713,6 +733,110 @@ void vcycle_dispatch(amg_hierarchy* h, const double* r, double* z, int rz_mode) 
     else vcycle_typed<double>(h, r, z, rz_mode);
 }
 
+// Launch-shape candidates of a grid-stride kernel that needs at most `need`
+// blocks: 1, 2, 4, ..., 32 blocks per SM, capped at `need`.
+std::vector<int> grid_candidates(const amg_hierarchy* h, long long need) {
+    std::vector<int> c;
+    for (int m = 1; m <= 32; m *= 2) {
+        long long g = (long long)h->num_sms * m;
+        if (g > need) g = need;
+        if (g < 1) g = 1;
+        if (c.empty() || c.back() != (int)g) c.push_back((int)g);
+        if (g == need) break;
+    }
+    return c;
+}
+
+// Fastest candidate grid for `launch(g)`, from the cache or timed now.
+template <typename F>
+int tune_grid(amg_hierarchy* h, const std::string& key, const std::vector<int>& cand, F&& launch) {
+    int best = 0;
+    if (tune_get(key, &best)) return best;
+    double tbest = 1e30;
+    for (int g : cand) {
+        const double t = time_launches(h->stream, [&]() { launch(g); }, 3);
+        if (t < tbest) {
+            tbest = t;
+            best = g;
+        }
+    }
+    tune_put(key, best);
+    return best;
+}
+
+// Times the SELL sweeps and the restriction of every level for value type T
+// on the hierarchy's own work vectors (zeroed first) and records the fastest
+// grids in the levels.
+template <typename T>
+void autotune_levels(amg_hierarchy* h) {
+    cudaStream_t st = h->stream;
+    const bool f32 = sizeof(T) == 4;
+    const int V = sizeof(T);
+    const T omega = (T)h->opt.omega;
+    const int L = (int)h->lev.size() - 1;
+    auto zero = [&](void* p, size_t bytes) {
+        if (p) CUDA_CHECK(cudaMemsetAsync(p, 0, bytes, st));
+    };
+    for (auto& Lv : h->lev) {
+        const size_t n = (size_t)Lv.A.n;
+        if (f32) {
+            for (float* v : {Lv.b32, Lv.x32, Lv.r32, Lv.y32}) zero(v, n * 4);
+        } else {
+            for (double* v : {Lv.b, Lv.x, Lv.r, Lv.y}) zero(v, n * 8);
+        }
+    }
+    const size_t n0 = (size_t)h->lev[0].A.n;
+    zero(h->r, n0 * 8);
+    zero(h->z, n0 * 8);
+    auto vb = [&](Level& Lv) -> T* { return f32 ? (T*)Lv.b32 : (T*)Lv.b; };
+    auto vx = [&](Level& Lv) -> T* { return f32 ? (T*)Lv.x32 : (T*)Lv.x; };
+    auto vr = [&](Level& Lv) -> T* { return f32 ? (T*)Lv.r32 : (T*)Lv.r; };
+    auto vy = [&](Level& Lv) -> T* { return f32 ? (T*)Lv.y32 : (T*)Lv.y; };
+    for (int l = 0; l < L; ++l) {
+        Level& Lv = h->lev[l];
+        Level& Ln = h->lev[l + 1];
+        const SellView S = view(Lv);
+        const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col, Lv.AP.perm};
+        const T* valm = f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm;
+        const T* apv = f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val;
+        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
+        const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
+        const long long need = (S.nslices + WARPS - 1) / WARPS;
+        const auto cand = grid_candidates(h, need);
+        const int z0 = l == 0;
+        Lv.grid_pre[f32] = tune_grid(h, tune_key(z0 ? "pre0" : "pre", V, S.n, Lv.A.nnz, S.nslices, 1, h->num_sms),
+                                     cand, [&](int g) {
+                                         if (z0 && !f32)
+                                             k_pre<T, double><<<g, TPB, 0, st>>>(S, valm, minv, omega, h->r, vx(Lv),
+                                                                                 vr(Lv));
+                                         else
+                                             k_pre<T, T><<<g, TPB, 0, st>>>(S, valm, minv, omega, vb(Lv), vx(Lv),
+                                                                            vr(Lv));
+                                         KERNEL_CHECK();
+                                     });
+        Lv.grid_post[f32] = tune_grid(
+            h, tune_key(z0 ? "post0" : "post", V, SAP.n, Lv.ap_nnz, SAP.nslices, 1, h->num_sms), cand, [&](int g) {
+                if (z0)
+                    k_post<T, double, double, false><<<g, TPB, 0, st>>>(SAP, apv, minv, omega, Lv.agg, p, vx(Ln),
+                                                                        vx(Lv), vr(Lv), h->r, h->z, h->red, h->sc,
+                                                                        FIN_NONE, nullptr);
+                else
+                    k_post<T, T, T, false><<<g, TPB, 0, st>>>(SAP, apv, minv, omega, Lv.agg, p, vx(Ln), vx(Lv),
+                                                              vr(Lv), (const T*)nullptr, vy(Lv), h->red, h->sc,
+                                                              FIN_NONE, nullptr);
+                KERNEL_CHECK();
+            });
+        const int nc = Ln.A.n;
+        Lv.grid_restrict[f32] = tune_grid(h, tune_key("restrict", V, nc, Lv.A.n, 0, 1, h->num_sms),
+                                          grid_candidates(h, (nc + TPB - 1) / TPB), [&](int g) {
+                                              k_restrict<T><<<g, TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, p, vr(Lv),
+                                                                               vb(Ln));
+                                              KERNEL_CHECK();
+                                          });
+    }
+    CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
 void read_scalars(amg_hierarchy* h) {
     CUDA_CHECK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->stream));
     CUDA_CHECK(cudaStreamSynchronize(h->stream));
@@ -768,6 +892,20 @@ void prepare_solve(amg_hierarchy* h) {
     h->red.ticket = h->mem.alloc<unsigned>(1);
     CUDA_CHECK(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
     CUDA_CHECK(cudaStreamSynchronize(h->stream));
+}
+
+void autotune_vcycle(amg_hierarchy* h) {
+    if (h->lev.size() < 2) return;
+    const bool prof_on = h->prof.on;
+    h->prof.on = false;
+    try {
+        if (h->opt.precision == AMG_FP32_VCYCLE) autotune_levels<float>(h);
+        else autotune_levels<double>(h);
+    } catch (...) {
+        h->prof.on = prof_on;
+        throw;
+    }
+    h->prof.on = prof_on;
 }
 
 void coarse_cg_solve(amg_hierarchy* h, const double* b, double* x) { coarse_solve_launch(h, b, x, false, true); }
