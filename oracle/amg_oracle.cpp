@@ -21,6 +21,10 @@
 //                                      ratio 8.00, coarsest 125; opc 1.141; stall rule
 //                                      by construction on a star graph
 //   coarsest CG (large coarsest)     -- residual of the returned x vs 1e-4 / 30 it
+//   batch of independent systems     -- each system's rows of the union equal
+//   (block-diagonal union)              the system built alone, bit for bit;
+//                                       V-cycle block diagonal; size rule on
+//                                       the largest system
 //   l1-Jacobi (Eq. 5-6, nb = 1)      -- two-level constant K = 5.6220 (Table 1)
 //   V-cycle (Eq. 2)                  -- dense error-propagation product; SPD
 //   PCG                              -- dense Cholesky solve of A
