@@ -63,6 +63,45 @@ def _args():
     return ap.parse_args()
 
 
+# DRAM traffic per row of the level-0 FP64 V-cycle kernels, from one ncu
+# capture on 3D Poisson 160^3 (profiles/ncu_traffic_pre_post_poisson160_fp64.md),
+# valid for the 7-point Poisson workload in FP64 and only while the kernel
+# source it was taken on is unchanged (checked by hash).
+_TRAFFIC = {
+    "post_smooth_l0": {"kernel": "k_post", "bytes_per_row": (381690368 + 27548672) / 4096000},
+    "pre_residual_l0": {"kernel": "k_pre", "bytes_per_row": (408898560 + 53249024) / 4096000},
+}
+_TRAFFIC_SRC_HASH = "964387251ef6aa9b"
+
+
+def _kernel_source_hash(names):
+    """sha256 (16 hex) of the named kernels' and sell_row's source in solve.cu."""
+    import hashlib
+    lines = open(os.path.join(ROOT, "paper_2006_16147_gb300", "csrc", "solve.cu")).read().splitlines()
+    parts = []
+    for name in list(names) + ["sell_row"]:
+        for i, line in enumerate(lines):
+            if f" {name}(" in line and ("__global__" in line or "__device__" in line):
+                j = i
+                while not lines[j].startswith("template"):
+                    j -= 1
+                k = i
+                while lines[k] != "}":
+                    k += 1
+                parts.append("\n".join(lines[j:k + 1]))
+                break
+    return hashlib.sha256("\n\n".join(parts).encode()).hexdigest()[:16]
+
+
+def _traffic(kernel_name, n, workload, precision):
+    t = _TRAFFIC.get(kernel_name)
+    if t is None or workload != "poisson" or precision != "fp64":
+        return None
+    if _kernel_source_hash(["k_post", "k_pre"]) != _TRAFFIC_SRC_HASH:
+        return None
+    return t["bytes_per_row"] * n
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -684,8 +723,10 @@ def main():
     nl, ms_tot, by_tot = solve_k[dom]
     per_launch_ms = ms_tot / nl
     achieved = (by_tot / nl) / (per_launch_ms * 1e-3) / 1e9
+    traffic = _traffic(dom, A.n, args.workload, args.precision)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "traffic_source": ("ncu DRAM bytes on 160^3 scaled by rows" if traffic else None),
                 "bytes_per_launch": by_tot / nl, "ms_per_launch": per_launch_ms, "launches": nl // args.steps}
     kernel_table = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": round(v[1] / args.steps, 4),
                         "GBps": round(v[2] / max(v[1], 1e-12) / 1e6, 1) if v[2] else None}
