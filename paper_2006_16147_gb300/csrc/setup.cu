@@ -464,11 +464,16 @@ __global__ void k_rap_bound(int nc, const int* __restrict__ heads, const int* __
 // Expands coarse row q into scratch (coarse column, term) in member order
 // then column order, sorts the segment stably by coarse column and sums each
 // run left to right starting from its first term. cnt[q] = distinct columns.
+// With `list` set, only the rows list[0 .. *nlist) are done (the rows the
+// warp-cooperative kernel below leaves out).
 __global__ void k_rap_rows(int nc, const int* __restrict__ heads, const int* __restrict__ mate,
                            const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
                            const int* __restrict__ agg, const double* __restrict__ p, const int* __restrict__ off,
-                           int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+                           int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt,
+                           const int* __restrict__ list, const int* __restrict__ nlist) {
+    const int nr = list ? *nlist : nc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
+        const int q = list ? list[t] : t;
         const int h = heads[q];
         const int m = mate[h];
         int* K = skey + off[q];
@@ -512,16 +517,140 @@ __global__ void k_rap_rows(int nc, const int* __restrict__ heads, const int* __r
     }
 }
 
-__global__ void k_rap_copy(int nc, const int* __restrict__ off, const int* __restrict__ cptr,
-                           const int* __restrict__ skey, const double* __restrict__ sval, int* __restrict__ ccol,
-                           double* __restrict__ cval) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+// Compacts the per-row results from scratch (row q at off[q]) into the CSR
+// arrays; a group of G lanes per row, lanes over the row's entries.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_rap_copy(int nc, const int* __restrict__ off, const int* __restrict__ cptr,
+                                                 const int* __restrict__ skey, const double* __restrict__ sval,
+                                                 int* __restrict__ ccol, double* __restrict__ cval) {
+    const int gl = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / G; q < nc; q += ng) {
         const int s = off[q], d = cptr[q], e = cptr[q + 1];
-        for (int k = 0; k < e - d; ++k) {
+        for (int k = gl; k < e - d; k += G) {
             ccol[d + k] = skey[s + k];
             cval[d + k] = sval[s + k];
         }
     }
+}
+
+// Pairwise Galerkin rows (RAP = true: row q of P^T A P from the members h, m
+// of aggregate q, term (p_i a_ij) p_j) or rows of A P (RAP = false: row i,
+// term a_ij p_j), one group of G lanes per row (32 / G rows per warp at a
+// time): lane t of the group holds term t in member order then column order,
+// its stable rank by coarse column comes from a shuffle sweep, the terms are
+// placed in rank order in shared memory, and the first lane of every run of
+// equal columns sums the run left to right from its first term. This is the
+// canonical order of the thread-per-row kernels, bit for bit. Rows with more
+// than G terms are listed in long_list for those kernels.
+template <bool RAP, int G>
+__global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restrict__ heads,
+                                                  const int* __restrict__ mate, const int* __restrict__ ptr,
+                                                  const int* __restrict__ col, const double* __restrict__ val,
+                                                  const int* __restrict__ agg, const double* __restrict__ p,
+                                                  const int* __restrict__ off, int* __restrict__ skey,
+                                                  double* __restrict__ sval, int* __restrict__ cnt,
+                                                  int* __restrict__ long_list, int* __restrict__ nlong) {
+    __shared__ int sk[TPB];
+    __shared__ double sv[TPB];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);                 // lane in the group
+    const int gbase = threadIdx.x - gl;            // group's first slot in shared memory
+    const int gshift = lane - gl;                  // group's first lane in the warp
+    const unsigned gmask = G == 32 ? FULL_MASK : (((1u << G) - 1u) << gshift);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int q0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    // every lane of a warp runs the same number of iterations (shuffles)
+    const int warp_first = q0 - (gshift / G);
+    for (int it = 0; warp_first + it * ng < nrows; ++it) {
+        const int q = q0 + it * ng;
+        int len = 0, l0 = 0, b0 = 0, b1 = 0, h = q, m = -1;
+        if (q < nrows) {
+            if (RAP) {
+                h = heads[q];
+                m = mate[h];
+            }
+            b0 = ptr[h];
+            l0 = ptr[h + 1] - b0;
+            int l1 = 0;
+            if (RAP && m > h) {
+                b1 = ptr[m];
+                l1 = ptr[m + 1] - b1;
+            }
+            len = l0 + l1;
+            if (len > G) {
+                if (gl == 0) long_list[atomicAdd(nlong, 1)] = q;
+                len = -1;                           // left to the thread-per-row kernel
+            }
+        }
+        int key = 0x7fffffff;
+        double v = 0.0;
+        if (gl < len) {
+            const bool first = gl < l0;
+            const int k = first ? b0 + gl : b1 + gl - l0;
+            const int j = col[k];
+            key = agg[j];
+            if (RAP) v = __dmul_rn(__dmul_rn(p[first ? h : m], val[k]), p[j]);
+            else v = __dmul_rn(val[k], p[j]);
+        }
+        int rank = 0;
+#pragma unroll 8
+        for (int t = 0; t < G; ++t) {
+            const int kt = __shfl_sync(FULL_MASK, key, t, G);
+            rank += (kt < key) || (kt == key && t < gl);
+        }
+        if (gl < len) {
+            sk[gbase + rank] = key;
+            sv[gbase + rank] = v;
+        }
+        __syncwarp();
+        const bool head = gl < len && (gl == 0 || sk[threadIdx.x - 1] != sk[threadIdx.x]);
+        const unsigned hm = __ballot_sync(FULL_MASK, head) & gmask;
+        if (head) {
+            const int kk = sk[threadIdx.x];
+            double sum = sv[threadIdx.x];
+            for (int e = gl + 1; e < len && sk[gbase + e] == kk; ++e) sum = __dadd_rn(sum, sv[gbase + e]);
+            const int u = __popc(hm & ((1u << lane) - 1u));
+            skey[off[q] + u] = kk;
+            sval[off[q] + u] = sum;
+        }
+        if (gl == 0 && len >= 0 && q < nrows) cnt[q] = __popc(hm);
+        __syncwarp();
+    }
+}
+
+// Lanes per row for the warp-cooperative row products: the power of two that
+// covers the typical row (longer rows go to the thread-per-row kernels).
+int rows_group(long long terms, long long rows) {
+    const double avg = rows > 0 ? (double)terms / (double)rows : 0.0;
+    return avg <= 7.0 ? 8 : (avg <= 14.0 ? 16 : 32);
+}
+
+template <bool RAP>
+void launch_rows(amg_hierarchy* h, int G, int nrows, const int* heads, const int* mate, const int* ptr,
+                 const int* col, const double* val, const int* agg, const double* p, const int* off, int* skey,
+                 double* sval, int* cnt, int* long_list, int* nlong, cudaStream_t st) {
+    const int blocks = blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
+    if (G == 8)
+        k_rows_warp<RAP, 8><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
+                                                    long_list, nlong);
+    else if (G == 16)
+        k_rows_warp<RAP, 16><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
+                                                     long_list, nlong);
+    else
+        k_rows_warp<RAP, 32><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
+                                                     long_list, nlong);
+    KERNEL_CHECK();
+}
+
+void launch_copy(amg_hierarchy* h, long long nnz, int nrows, const int* off, const int* cptr, const int* skey,
+                 const double* sval, int* ccol, double* cval, cudaStream_t st) {
+    const int G = rows_group(nnz, nrows);
+    const int blocks = blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
+    if (G == 8) k_rap_copy<8><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
+    else if (G == 16) k_rap_copy<16><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
+    else k_rap_copy<32><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
+    KERNEL_CHECK();
 }
 
 // P_l <- P_l P_s: agg_l = agg_s o agg_l, p_l = p_l * p_s(agg_l).
@@ -757,15 +886,18 @@ __global__ void k_scale_cols(long long m, const int* __restrict__ col, const dou
 // summed per key in column order, in scratch at row i's own CSR segment.
 __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                           const double* __restrict__ val, const int* __restrict__ agg, const double* __restrict__ p,
-                          int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+                          int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt,
+                          const int* __restrict__ list, const int* __restrict__ nlist) {
+    const int nr = list ? *nlist : n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
+        const int i = list ? list[t] : t;
         const int b = ptr[i], len = ptr[i + 1] - b;
         int* K = skey + b;
         double* V = sval + b;
         for (int k = 0; k < len; ++k) {
             const int j = col[b + k];
             K[k] = agg[j];
-            V[k] = val[b + k] * p[j];
+            V[k] = __dmul_rn(val[b + k], p[j]);
         }
         for (int a = 1; a < len; ++a) {
             const int key = K[a];
@@ -780,7 +912,7 @@ __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restr
             const int key = K[a];
             double sum = V[a];
             int e = a + 1;
-            while (e < len && K[e] == key) { sum += V[e]; ++e; }
+            while (e < len && K[e] == key) { sum = __dadd_rn(sum, V[e]); ++e; }
             K[u] = key;
             V[u] = sum;
             ++u;
@@ -796,7 +928,8 @@ struct Scratch {
     double* diag = nullptr;
     double* c = nullptr;
     int *mate = nullptr, *cand = nullptr, *list0 = nullptr, *list1 = nullptr, *mlist = nullptr;
-    int* cnt = nullptr;       // [0,1] list counters, [2,3] match counters, [4] rounds, [5] flags, [6..7] totals
+    int* cnt = nullptr;       // [0,1] list counters, [2,3] match counters, [4] rounds, [5] flags, [6..7] totals,
+                              // [8] rows left to the thread-per-row product kernels
     int* flag = nullptr;      // n
     int* qid = nullptr;       // n
     int* heads = nullptr;     // n
@@ -889,8 +1022,11 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     k_rap_bound<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, S.ub);
     KERNEL_CHECK();
     scan_exclusive(S.ub, S.off, nc, S.cnt + 6, st, S.scan_tmp);
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
+    launch_rows<true>(h, rows_group(2LL * A.nnz, A.n), nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
+                      S.skey, S.sval, S.ub, S.list1, S.cnt + 8, st);
     k_rap_rows<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
-                                                S.skey, S.sval, S.ub);
+                                                S.skey, S.sval, S.ub, S.list1, S.cnt + 8);
     KERNEL_CHECK();
     DevCsr C;
     C.n = nc;
@@ -899,8 +1035,7 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     C.nnz = read_int(C.ptr + nc, S.host, st);
     C.col = owner.alloc<int>(C.nnz);
     C.val = owner.alloc<double>(C.nnz);
-    k_rap_copy<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val);
-    KERNEL_CHECK();
+    launch_copy(h, C.nnz, nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val, st);
     return C;
 }
 
@@ -987,7 +1122,11 @@ void build_scaled(amg_hierarchy* h, Level& L, bool fp32) {
 void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     cudaStream_t st = h->stream;
     const int n = L.A.n;
-    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, S.skey, S.sval, S.ub);
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
+    launch_rows<false>(h, rows_group(L.A.nnz, n), n, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
+                       L.A.ptr, S.skey, S.sval, S.ub, S.list1, S.cnt + 8, st);
+    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, S.skey, S.sval, S.ub,
+                                              S.list1, S.cnt + 8);
     KERNEL_CHECK();
     DevCsr AP;
     AP.n = n;
@@ -996,8 +1135,7 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     AP.nnz = read_int(AP.ptr + n, S.host, st);
     AP.col = S.mem.alloc<int>(AP.nnz);
     AP.val = S.mem.alloc<double>(AP.nnz);
-    k_rap_copy<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val);
-    KERNEL_CHECK();
+    launch_copy(h, AP.nnz, n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val, st);
     L.ap_nnz = AP.nnz;
     build_sell(h, AP, L.AP, S, fp32);
     CUDA_CHECK(cudaStreamSynchronize(st));
