@@ -85,7 +85,8 @@ typedef struct {
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */
     double min_ratio;  /* [1.5] stop coarsening after a level with n_l / n_{l+1} below this (stalled matching) */
-    void* stream;      /* [NULL] cudaStream_t for every device operation; NULL = legacy default */
+    void* stream;      /* [NULL] cudaStream_t for every device operation and for the hierarchy's stream-ordered
+                          allocations; NULL = legacy default. Must stay valid until amg_free */
 } amg_options;
 
 /* Per-solve report. */

@@ -48,14 +48,26 @@ void set_last_error(const std::string& m);
 
 // ------------------------------------------------------ device memory ------
 // Owner of a set of device allocations, released together.
+// Keeps memory freed to the device's default stream-ordered pool reserved for
+// the process (release threshold at its maximum), so a later setup reuses it
+// without new page mappings. Once per device; a process-local setting.
+void keep_pool_reserved();
+
+// Device allocations of one owner, stream-ordered on `stream` (cudaMallocAsync
+// / cudaFreeAsync from the device's default pool): allocation and release cost
+// no device synchronisation. Work that uses an allocation on another stream
+// must be ordered after the allocating stream (a synchronisation or event),
+// and `stream` must stay valid until the arena releases its memory.
 struct DevArena {
+    cudaStream_t stream = nullptr;
     std::vector<void*> ptrs;
     size_t bytes = 0;
     template <typename T>
     T* alloc(size_t count) {
         if (count == 0) count = 1;
+        keep_pool_reserved();
         void* p = nullptr;
-        CUDA_CHECK(cudaMalloc(&p, count * sizeof(T)));
+        CUDA_CHECK(cudaMallocAsync(&p, count * sizeof(T), stream));
         ptrs.push_back(p);
         bytes += count * sizeof(T);
         return static_cast<T*>(p);
@@ -63,14 +75,14 @@ struct DevArena {
     void release(void* p) {
         for (size_t i = 0; i < ptrs.size(); ++i)
             if (ptrs[i] == p) {
-                cudaFree(p);
+                cudaFreeAsync(p, stream);
                 ptrs[i] = ptrs.back();
                 ptrs.pop_back();
                 return;
             }
     }
     void free_all() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) cudaFreeAsync(p, stream);
         ptrs.clear();
         bytes = 0;
     }

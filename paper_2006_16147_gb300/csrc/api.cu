@@ -68,6 +68,7 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     amg_hierarchy* h = new amg_hierarchy;
     h->opt = o;
     h->stream = static_cast<cudaStream_t>(o.stream);
+    h->mem.stream = h->stream;
     h->prof.on = o.profile != 0;
     s = guarded([&]() -> amg_status {
         CUDA_CHECK(cudaGetDevice(&h->device));

@@ -928,6 +928,7 @@ BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width) {
         h->blk = nullptr;
     }
     BlockWork* W = new BlockWork;
+    W->mem.stream = h->stream;
     h->blk = W;
     W->K = K;
     W->fixed_width = fixed_width;

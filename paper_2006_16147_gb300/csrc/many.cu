@@ -209,6 +209,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
     const int n = L0.A.n;
     const SellM S{L0.S.n, L0.S.nslices, L0.S.sptr, L0.S.col, L0.S.perm};
     ManyWork M;
+    M.mem.stream = h->stream;
     M.sc.mode = M.mem.alloc<int>(m);
     M.sc.iters = M.mem.alloc<int>(m);
     M.sc.rho = M.mem.alloc<double>(m);

@@ -91,17 +91,21 @@ amg_server* serve_create(int nh, amg_hierarchy* const* hs, int K, size_t budget,
             sv.old_stream = hs[i]->stream;
             CUDA_CHECK(cudaStreamCreateWithFlags(&sv.stream, cudaStreamNonBlocking));
             hs[i]->stream = sv.stream;
-            block_ensure(hs[i], K, true);
-            sv.B = hs[i]->blk->mem.alloc<double>((size_t)sv.n * K);
-            sv.X = hs[i]->blk->mem.alloc<double>((size_t)sv.n * K);
-            CUDA_CHECK(cudaHostAlloc(&sv.rtol_host, sizeof(double) * K, cudaHostAllocDefault));
-            for (int c = 0; c < K; ++c) sv.rtol_host[c] = rtol;
-            sv.owner.assign(K, -1);
-            sv.bytes_per_col = block_bytes_per_column(hs[i]);
             S->hs.push_back(sv);
+            Served& cur = S->hs.back();
+            block_ensure(hs[i], K, true);
+            cur.B = hs[i]->blk->mem.alloc<double>((size_t)cur.n * K);
+            cur.X = hs[i]->blk->mem.alloc<double>((size_t)cur.n * K);
+            CUDA_CHECK(cudaHostAlloc(&cur.rtol_host, sizeof(double) * K, cudaHostAllocDefault));
+            for (int c = 0; c < K; ++c) cur.rtol_host[c] = rtol;
+            cur.owner.assign(K, -1);
+            cur.bytes_per_col = block_bytes_per_column(hs[i]);
+            CUDA_CHECK(cudaStreamSynchronize(cur.stream));
         }
     } catch (...) {
         for (auto& sv : S->hs) {
+            cudaStreamSynchronize(sv.stream);
+            block_free(sv.h);           // its memory is ordered on sv.stream: release before that stream goes
             sv.h->stream = sv.old_stream;
             if (sv.rtol_host) cudaFreeHost(sv.rtol_host);
             if (sv.stream) cudaStreamDestroy(sv.stream);

@@ -1169,6 +1169,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     const int n0 = Ain->n, nnz0 = Ain->nnz;
 
     Scratch S;
+    S.mem.stream = h->stream;
     CUDA_CHECK(cudaHostAlloc(&S.host, 64, cudaHostAllocDefault));
     {
         int coop = 0, per_sm = 0;
@@ -1603,6 +1604,7 @@ void setup_many(amg_hierarchy* h, int m, const amg_csr* As, const double* const*
         if (n > 0x7ffffffe || nnz > 0x7ffffffe) AMG_THROW(AMG_ERR_TOO_LARGE, "the union exceeds int32 sizes");
     }
     DevArena tmp;
+    tmp.stream = st;
     int* ptr = tmp.alloc<int>(n + 1);
     int* col = tmp.alloc<int>(nnz);
     double* val = tmp.alloc<double>(nnz);
