@@ -133,11 +133,13 @@ struct Level {
     DevSell S;                  // A_l in SELL-32 (PCG product, extra smoothing sweeps)
     double* valm = nullptr;     // A_l M_l^{-1} values in S's layout (first pre-smoothing sweep)
     float* valm32 = nullptr;
-    DevSell AP;                 // A_l P_l in SELL-32 (coarse-correction residual update)
+    DevSell AP;                 // omega M_l^{-1} A_l P_l in SELL-32 (coarse-correction residual update)
     int64_t ap_nnz = 0;
     double* w = nullptr;        // smooth vector on this level
     double* minv = nullptr;     // l1-Jacobi inverse diagonal
     float* minv32 = nullptr;
+    double* wminv = nullptr;    // omega M_l^{-1} (the same array as minv when omega = 1)
+    float* wminv32 = nullptr;
     // prolongator to the next level (one nonzero per row) and its transpose
     int* agg = nullptr;
     double* p = nullptr;

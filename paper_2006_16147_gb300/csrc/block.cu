@@ -261,7 +261,8 @@ __device__ __forceinline__ void fin_rz(const BlockScalars& sc, int c, double rz,
     }
 }
 
-// out = x + P e + omega M^-1 (r - (A P) e); on level 0 also r_cg . out and
+// out = x + P e + omega M^-1 r - (omega M^-1 A P) e (the stored A P values
+// carry the row scaling); on level 0 also r_cg . out and
 // (flexible CG) q . out per column.
 template <typename T, typename TO, int CPL, bool DOT>
 __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ apval, const T* __restrict__ minv,
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
             if (c < k) {
                 const size_t o = (size_t)i * ld + c;
                 const T y = fma(pi, E[(size_t)a * ld + c], X[o]);
-                const T v = fma(mi, R[o] - acc[m], y);
+                const T v = fma(mi, R[o], y) - acc[m];          // acc: rows of omega M^-1 A P
                 Out[o] = (TO)v;
                 if (DOT) {
                     d0[m] = fma(Bdot[o], (double)(TO)v, d0[m]);

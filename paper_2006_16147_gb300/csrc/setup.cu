@@ -873,6 +873,25 @@ __global__ void k_gram(int n, const double* __restrict__ Y, double* __restrict__
 }
 
 // Column scaling for the pre-smoother: valm_k = val_k * minv[col_k].
+// Rows of a CSR matrix scaled in place: row i times omega / M_ii.
+__global__ void k_scale_rows(int n, const int* __restrict__ ptr, double* __restrict__ val,
+                             const double* __restrict__ minv, double omega) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double s = omega * minv[i];
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) val[k] = s * val[k];
+    }
+}
+
+// omega M^{-1} when omega != 1.
+__global__ void k_scale_vec(int n, double omega, const double* __restrict__ a, double* __restrict__ b,
+                            float* __restrict__ b32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = omega * a[i];
+        b[i] = v;
+        if (b32) b32[i] = (float)v;
+    }
+}
+
 __global__ void k_scale_cols(long long m, const int* __restrict__ col, const double* __restrict__ val,
                              const double* __restrict__ minv, double* __restrict__ valm, float* __restrict__ valm32) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
@@ -1118,7 +1137,9 @@ void build_scaled(amg_hierarchy* h, Level& L, bool fp32) {
     KERNEL_CHECK();
 }
 
-// A_l P_l in SELL (rows of A_l, columns the aggregates of level l+1).
+// omega M_l^{-1} A_l P_l in SELL (rows of A_l scaled by omega / M_ii, columns
+// the aggregates of level l+1): the coarse-correction term of the fused
+// post-smoother needs no per-row scaling in the solve.
 void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     cudaStream_t st = h->stream;
     const int n = L.A.n;
@@ -1136,6 +1157,8 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     AP.col = S.mem.alloc<int>(AP.nnz);
     AP.val = S.mem.alloc<double>(AP.nnz);
     launch_copy(h, AP.nnz, n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val, st);
+    k_scale_rows<<<grid_for(h, n), TPB, 0, st>>>(n, AP.ptr, AP.val, L.minv, h->opt.omega);
+    KERNEL_CHECK();
     L.ap_nnz = AP.nnz;
     build_sell(h, AP, L.AP, S, fp32);
     CUDA_CHECK(cudaStreamSynchronize(st));
@@ -1368,6 +1391,15 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             Scope sc_(&h->prof, st, S_SMOOTHER, 12.0 * L.A.nnz + 12.0 * n);
             k_l1_jacobi<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.minv, L.minv32);
             KERNEL_CHECK();
+            if (o.omega == 1.0) {
+                L.wminv = L.minv;
+                L.wminv32 = L.minv32;
+            } else {
+                L.wminv = h->mem.alloc<double>(n);
+                if (fp32) L.wminv32 = h->mem.alloc<float>(n);
+                k_scale_vec<<<grid_for(h, n), TPB, 0, st>>>(n, o.omega, L.minv, L.wminv, L.wminv32);
+                KERNEL_CHECK();
+            }
         }
         Scope sc_(&h->prof, st, S_FORMAT, 24.0 * L.A.nnz);
         const bool coarsest_cg = l == nlev - 1 && L.A.n > o.max_dense;

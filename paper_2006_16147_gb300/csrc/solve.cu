@@ -106,9 +106,12 @@ template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
 // Row dot product of one SELL slice lane: sum_k val[k] * xv(col[k]). The
-// loop is unrolled by four with two accumulators so that the column, value
-// and gather loads of four entries are in flight together.
-template <typename T, typename F>
+// loop is unrolled by four so that the column, value and gather loads of four
+// entries are in flight together. Two accumulators shorten the FMA chain
+// (latency-bound kernels); one accumulator saves the final add, which pays in
+// the fused smoothers, where the FP64 pipe (this GPU's FP64 rate is 1/64 of
+// its FP32 rate) is the bound.
+template <typename T, int NACC = 2, typename F>
 __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __restrict__ val, long long base, int w,
                                       F&& xv) {
     T a0 = 0, a1 = 0;
@@ -117,13 +120,20 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __re
         const int j0 = ld(col + base), j1 = ld(col + base + 32), j2 = ld(col + base + 64), j3 = ld(col + base + 96);
         const T v0 = ld(val + base), v1 = ld(val + base + 32), v2 = ld(val + base + 64), v3 = ld(val + base + 96);
         const T x0 = xv(j0), x1 = xv(j1), x2 = xv(j2), x3 = xv(j3);
-        a0 = fma(v0, x0, a0);
-        a1 = fma(v1, x1, a1);
-        a0 = fma(v2, x2, a0);
-        a1 = fma(v3, x3, a1);
+        if (NACC == 1) {
+            a0 = fma(v0, x0, a0);
+            a0 = fma(v1, x1, a0);
+            a0 = fma(v2, x2, a0);
+            a0 = fma(v3, x3, a0);
+        } else {
+            a0 = fma(v0, x0, a0);
+            a1 = fma(v1, x1, a1);
+            a0 = fma(v2, x2, a0);
+            a1 = fma(v3, x3, a1);
+        }
     }
     for (; k < w; ++k, base += 32) a0 = fma(ld(val + base), xv(ld(col + base)), a0);
-    return a0 + a1;
+    return NACC == 1 ? a0 : a0 + a1;
 }
 
 #define SELL_LOOP(S)                                                                 \
@@ -136,20 +146,24 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __re
 // --------------------------------------------------------- V-cycle ---------
 // First pre-smoothing sweep from a zero guess, fused with the residual:
 //   x = omega M^-1 b,  r = b - omega (A M^-1) b,
-// with the column-scaled values valm = A M^-1 (one FMA per stored entry).
-template <typename T, typename TB>
-__global__ void __launch_bounds__(TPB) k_pre(SellView S, const T* __restrict__ valm, const T* __restrict__ minv,
+// with the column-scaled values valm = A M^-1 (one FMA per stored entry) and
+// wm = omega M^-1. With U (one pre-smoothing sweep), x is not stored but
+// u = x + omega M^-1 r = omega M^-1 (b + r), the part of the post-smoother
+// that does not depend on the coarse correction.
+template <typename T, typename TB, bool U>
+__global__ void __launch_bounds__(TPB) k_pre(SellView S, const T* __restrict__ valm, const T* __restrict__ wm,
                                              T omega, const TB* __restrict__ b, T* __restrict__ x,
                                              T* __restrict__ r) {
     SELL_LOOP(S) {
-        const T acc = sell_row(S.col, valm, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+        const T acc = sell_row<T, 1>(S.col, valm, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                [&](int j) { return (T)ld(b + j); });
         const int ip = s * 32 + lane;
         if (ip < S.n) {
             const int i = sell_rowid(S, ip);
             const T bi = (T)b[i];
-            x[i] = (omega * minv[i]) * bi;
-            r[i] = fma(-omega, acc, bi);
+            const T ri = fma(-omega, acc, bi);
+            r[i] = ri;
+            x[i] = U ? wm[i] * (bi + ri) : wm[i] * bi;
         }
     }
 }
@@ -169,26 +183,30 @@ __global__ void __launch_bounds__(TPB) k_restrict(int nc, const int* __restrict_
 
 // Coarse correction and first post-smoothing sweep, fused:
 //   y = x + P e,  out = y + omega M^-1 (b - A y),
-// evaluated as out = y + omega M^-1 (r - (A P) e) since b - A y = r - A P e
-// with r = b - A x from the pre-smoother; A P has about half the entries of A
-// and gathers only the short coarse vector e. With DOT, also bdot . out
-// (r . z of CG on level 0), finished into the CG scalars.
-template <typename T, typename TB, typename TO, bool DOT>
-__global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict__ apval, const T* __restrict__ minv,
-                                              T omega, const int* __restrict__ agg, const T* __restrict__ p,
+// evaluated as out = (x + omega M^-1 r) + P e - (omega M^-1 A P) e, since
+// b - A y = r - A P e with r = b - A x from the pre-smoother. The stored
+// apw = omega M^-1 A P has about half the entries of A and gathers only the
+// short coarse vector e. With U the first term u = x + omega M^-1 r comes
+// ready from the pre-smoother; otherwise it is formed here from x, r and
+// wm = omega M^-1. With DOT, also bdot . out (r . z of CG on level 0),
+// finished into the CG scalars. FP64 work per row: one FMA per entry of
+// apw, two more, and the dot.
+template <typename T, typename TB, typename TO, bool DOT, bool U>
+__global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict__ apw, const T* __restrict__ wm,
+                                              const int* __restrict__ agg, const T* __restrict__ p,
                                               const T* __restrict__ e, const T* __restrict__ x,
                                               const T* __restrict__ r, const TB* __restrict__ bdot,
                                               TO* __restrict__ out, Reducer red, PcgScalars* sc, int mode,
                                               const double* __restrict__ q2) {
     double dot = 0.0, dot2 = 0.0;
     SELL_LOOP(SAP) {
-        const T acc = sell_row(SAP.col, apval, (long long)SAP.sptr[s] * 32 + lane, SAP.sptr[s + 1] - SAP.sptr[s],
+        const T acc = sell_row<T, 1>(SAP.col, apw, (long long)SAP.sptr[s] * 32 + lane, SAP.sptr[s + 1] - SAP.sptr[s],
                                [&](int q) { return ld(e + q); });
         const int ip = s * 32 + lane;
         if (ip < SAP.n) {
             const int i = sell_rowid(SAP, ip);
-            const T yi = fma(p[i], e[agg[i]], x[i]);
-            const T o = fma(omega * minv[i], r[i] - acc, yi);
+            const T ui = U ? x[i] : fma(wm[i], r[i], x[i]);
+            const T o = fma(p[i], e[agg[i]], ui) - acc;
             out[i] = (TO)o;
             if (DOT) {
                 dot = fma((double)bdot[i], (double)(TO)o, dot);
@@ -197,6 +215,23 @@ __global__ void __launch_bounds__(TPB) k_post(SellView SAP, const T* __restrict_
         }
     }
     if (DOT) reduce_and_finish(dot, dot2, red, sc, mode);
+}
+
+template <typename T, typename TB>
+void launch_pre(bool u, int grid, cudaStream_t st, SellView S, const T* valm, const T* wm, T omega, const TB* b, T* x,
+                T* r) {
+    if (u) k_pre<T, TB, true><<<grid, TPB, 0, st>>>(S, valm, wm, omega, b, x, r);
+    else k_pre<T, TB, false><<<grid, TPB, 0, st>>>(S, valm, wm, omega, b, x, r);
+    KERNEL_CHECK();
+}
+
+template <typename T, typename TB, typename TO, bool DOT>
+void launch_post(bool u, int grid, cudaStream_t st, SellView SAP, const T* apw, const T* wm, const int* agg,
+                 const T* p, const T* e, const T* x, const T* r, const TB* bdot, TO* out, Reducer red, PcgScalars* sc,
+                 int mode, const double* q2) {
+    if (u) k_post<T, TB, TO, DOT, true><<<grid, TPB, 0, st>>>(SAP, apw, wm, agg, p, e, x, r, bdot, out, red, sc, mode, q2);
+    else k_post<T, TB, TO, DOT, false><<<grid, TPB, 0, st>>>(SAP, apw, wm, agg, p, e, x, r, bdot, out, red, sc, mode, q2);
+    KERNEL_CHECK();
 }
 
 // FP32 copy of the level-0 residual for the FP32 V-cycle: one conversion per
@@ -469,13 +504,15 @@ __global__ void __launch_bounds__(TPB) k_spmv_dot(SellView S, const double* __re
                                                   PcgScalars* sc) {
     double pq = 0.0;
     SELL_LOOP(S) {
+        const int ip = s * 32 + lane;
+        const bool live = ip < S.n;
+        const int i = live ? sell_rowid(S, ip) : 0;
+        const double pi = live ? ld(p + i) : 0.0;
         const double acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
                                     [&](int j) { return ld(p + j); });
-        const int ip = s * 32 + lane;
-        if (ip < S.n) {
-            const int i = sell_rowid(S, ip);
+        if (live) {
             q[i] = acc;
-            pq = fma(p[i], acc, pq);
+            pq = fma(pi, acc, pq);
         }
     }
     reduce_and_finish(pq, 0.0, red, sc, FIN_PQ);
@@ -508,9 +545,11 @@ __global__ void __launch_bounds__(TPB) k_update_p(int n, const double* __restric
 // or written once (index 4 B, value V B, the level-0 input/output in FP64);
 // matrix entries counted without SELL padding.
 double by_pre(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 3.0 * V); }
-// post: A P entries + x, r, p, minv (V) + agg (4) + out (Vo) [+ CG r for the dot] + e (n_c)
-double by_post2(const Level& L, int nc, int V, int Vo, bool dot) {
-    return (double)L.ap_nnz * (V + 4) + (double)L.A.n * (4.0 * V + 4 + Vo + (dot ? 8 : 0)) + (double)nc * V;
+// post: omega M^-1 A P entries + u, p (V) [x, r, omega M^-1 instead of u without
+// the fused u: 3V] + agg (4) + out (Vo) [+ CG r for the dot] + e (n_c)
+double by_post2(const Level& L, int nc, int V, int Vo, bool dot, bool u) {
+    return (double)L.ap_nnz * (V + 4) + (double)L.A.n * ((u ? 2.0 : 4.0) * V + 4 + Vo + (dot ? 8 : 0)) +
+           (double)nc * V;
 }
 double by_pre_step(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 5.0 * V); }
 double by_restrict(int n, int nc, int V) { return (double)n * (4 + 2.0 * V) + (double)nc * (4 + V); }
@@ -610,6 +649,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     auto valm = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm; };
     auto apv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val; };
     auto minv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv; };
+    auto wm = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.wminv32 : (const T*)Lv.wminv; };
     auto pv = [&](Level& Lv) -> const T* { return f32 ? (const T*)Lv.p32 : (const T*)Lv.p; };
     auto vec = [&](Level& Lv, int which) -> T* {
         if (f32) {
@@ -623,6 +663,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     const int V = sizeof(T);
     const int pre = h->opt.pre < 1 ? 1 : h->opt.pre;
     const int post = h->opt.post < 1 ? 1 : h->opt.post;
+    const bool U = pre == 1;     // the pre-smoother hands u = x + omega M^-1 r to the post-smoother
     std::vector<T*> xcur(L + 1), rcur(L + 1), out(L + 1), spare(L + 1);
 
     // downward: level 0 reads the FP64 r directly
@@ -639,9 +680,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         }
         {
             Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 && !f32 ? 8 : V));
-            if (l == 0 && !f32) k_pre<T, double><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, r, xa, ra);
-            else k_pre<T, T><<<g, TPB, 0, st>>>(S, valm(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra);
-            KERNEL_CHECK();
+            if (l == 0 && !f32) launch_pre<T, double>(U, g, st, S, valm(Lv), wm(Lv), omega, r, xa, ra);
+            else launch_pre<T, T>(U, g, st, S, valm(Lv), wm(Lv), omega, vec(Lv, VB), xa, ra);
         }
         for (int k = 1; k < pre; ++k) {
             Scope sc_(&h->prof, st, K_PRE_STEP, by_pre_step(Lv, V, Vb));
@@ -674,11 +714,9 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         if (l > 0) {
             T *ya = vec(Lv, VY), *yb = spare[l];
             {
-                Scope sc_(&h->prof, st, K_POST, by_post2(Lv, nc, V, V, false));
-                k_post<T, T, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[l],
-                                                          rcur[l], (const T*)nullptr, ya, h->red, h->sc, FIN_NONE,
-                                                          nullptr);
-                KERNEL_CHECK();
+                Scope sc_(&h->prof, st, K_POST, by_post2(Lv, nc, V, V, false, U));
+                launch_post<T, T, T, false>(U, g, st, SAP, apv(Lv), wm(Lv), Lv.agg, pv(Lv), e, xcur[l], rcur[l],
+                                            (const T*)nullptr, ya, h->red, h->sc, FIN_NONE, nullptr);
             }
             for (int k = 1; k < post; ++k) {
                 Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
@@ -690,23 +728,19 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             continue;
         }
         if (post == 1) {
-            Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, 8, rz_mode != FIN_NONE));
+            Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, 8, rz_mode != FIN_NONE, U));
             if (rz_mode != FIN_NONE)
-                k_post<T, double, double, true><<<red_grid(h), TPB, 0, st>>>(
-                    SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e, xcur[0], rcur[0], r, z, h->red, h->sc, rz_mode, q2);
+                launch_post<T, double, double, true>(U, red_grid(h), st, SAP, apv(Lv), wm(Lv), Lv.agg, pv(Lv), e,
+                                                     xcur[0], rcur[0], r, z, h->red, h->sc, rz_mode, q2);
             else
-                k_post<T, double, double, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
-                                                                   xcur[0], rcur[0], r, z, h->red, h->sc, FIN_NONE,
-                                                                   nullptr);
-            KERNEL_CHECK();
+                launch_post<T, double, double, false>(U, g, st, SAP, apv(Lv), wm(Lv), Lv.agg, pv(Lv), e, xcur[0],
+                                                      rcur[0], r, z, h->red, h->sc, FIN_NONE, nullptr);
         } else {
             T *ya = vec(Lv, VY), *yb = spare[0];
             {
-                Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, V, false));
-                k_post<T, double, T, false><<<g, TPB, 0, st>>>(SAP, apv(Lv), minv(Lv), omega, Lv.agg, pv(Lv), e,
-                                                              xcur[0], rcur[0], r, ya, h->red, h->sc, FIN_NONE,
-                                                              nullptr);
-                KERNEL_CHECK();
+                Scope sc_(&h->prof, st, K_POST_L0, by_post2(Lv, nc, V, V, false, U));
+                launch_post<T, double, T, false>(U, g, st, SAP, apv(Lv), wm(Lv), Lv.agg, pv(Lv), e, xcur[0], rcur[0],
+                                                 r, ya, h->red, h->sc, FIN_NONE, nullptr);
             }
             for (int k = 1; k < post - 1; ++k) {
                 Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, V));
@@ -799,32 +833,27 @@ void autotune_levels(amg_hierarchy* h) {
         const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col, Lv.AP.perm};
         const T* valm = f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm;
         const T* apv = f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val;
-        const T* minv = f32 ? (const T*)Lv.minv32 : (const T*)Lv.minv;
+        const T* wm = f32 ? (const T*)Lv.wminv32 : (const T*)Lv.wminv;
         const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
+        const bool U = h->opt.pre <= 1;
         const long long need = (S.nslices + WARPS - 1) / WARPS;
         const auto cand = grid_candidates(h, need);
         const int z0 = l == 0;
         Lv.grid_pre[f32] = tune_grid(h, tune_key(z0 ? "pre0" : "pre", V, S.n, Lv.A.nnz, S.nslices, 1, h->num_sms),
                                      cand, [&](int g) {
                                          if (z0 && !f32)
-                                             k_pre<T, double><<<g, TPB, 0, st>>>(S, valm, minv, omega, h->r, vx(Lv),
-                                                                                 vr(Lv));
+                                             launch_pre<T, double>(U, g, st, S, valm, wm, omega, h->r, vx(Lv), vr(Lv));
                                          else
-                                             k_pre<T, T><<<g, TPB, 0, st>>>(S, valm, minv, omega, vb(Lv), vx(Lv),
-                                                                            vr(Lv));
-                                         KERNEL_CHECK();
+                                             launch_pre<T, T>(U, g, st, S, valm, wm, omega, vb(Lv), vx(Lv), vr(Lv));
                                      });
         Lv.grid_post[f32] = tune_grid(
             h, tune_key(z0 ? "post0" : "post", V, SAP.n, Lv.ap_nnz, SAP.nslices, 1, h->num_sms), cand, [&](int g) {
                 if (z0)
-                    k_post<T, double, double, false><<<g, TPB, 0, st>>>(SAP, apv, minv, omega, Lv.agg, p, vx(Ln),
-                                                                        vx(Lv), vr(Lv), h->r, h->z, h->red, h->sc,
-                                                                        FIN_NONE, nullptr);
+                    launch_post<T, double, double, false>(U, g, st, SAP, apv, wm, Lv.agg, p, vx(Ln), vx(Lv), vr(Lv),
+                                                          h->r, h->z, h->red, h->sc, FIN_NONE, nullptr);
                 else
-                    k_post<T, T, T, false><<<g, TPB, 0, st>>>(SAP, apv, minv, omega, Lv.agg, p, vx(Ln), vx(Lv),
-                                                              vr(Lv), (const T*)nullptr, vy(Lv), h->red, h->sc,
-                                                              FIN_NONE, nullptr);
-                KERNEL_CHECK();
+                    launch_post<T, T, T, false>(U, g, st, SAP, apv, wm, Lv.agg, p, vx(Ln), vx(Lv), vr(Lv),
+                                                (const T*)nullptr, vy(Lv), h->red, h->sc, FIN_NONE, nullptr);
             });
         const int nc = Ln.A.n;
         Lv.grid_restrict[f32] = tune_grid(h, tune_key("restrict", V, nc, Lv.A.n, 0, 1, h->num_sms),
