@@ -106,9 +106,9 @@ __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__
 // Per-column sums of (v0, v1) over the rows of the whole grid in a fixed
 // order (groups of a warp, warps of a block, then blocks); the last block to
 // finish calls fin(c, sum0, sum1) for every column. Deterministic for a fixed
-// (grid, k).
+// (grid, lanes per row, block width ld): a column's sum never depends on the other columns.
 template <int CPL, typename FIN>
-__device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], const Grp& g, int k, double* partial,
+__device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], const Grp& g, int k, int ld, double* partial,
                                         unsigned* ticket, FIN&& fin) {
     __shared__ double sm[WARPS][2][MAXK];
     __shared__ bool last;
@@ -145,13 +145,29 @@ __device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], co
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    // tpc consecutive lanes per column (a power of two <= 32, set by the
+    // block width ld so that it does not depend on how many columns are
+    // live): lane j sums the blocks j, j + tpc, ... in order, then the lanes
+    // combine by a shuffle tree; a fixed order for a fixed (grid, ld).
+    int tpc = 1;
+    while (tpc < 32 && tpc * 2 * ld <= (int)blockDim.x) tpc *= 2;
+    const int cpb = (int)blockDim.x / tpc;               // columns per pass
+    const int j = threadIdx.x & (tpc - 1);
+    for (int c0 = 0; c0 < k; c0 += cpb) {
+        const int c = c0 + (int)threadIdx.x / tpc;
         double a = 0.0, b = 0.0;
-        for (int blk = 0; blk < (int)gridDim.x; ++blk) {
-            a += __ldcg(partial + ((size_t)blk * 2 + 0) * k + c);
-            b += __ldcg(partial + ((size_t)blk * 2 + 1) * k + c);
+        if (c < k) {
+#pragma unroll 4
+            for (int blk = j; blk < (int)gridDim.x; blk += tpc) {
+                a += __ldcg(partial + ((size_t)blk * 2 + 0) * k + c);
+                b += __ldcg(partial + ((size_t)blk * 2 + 1) * k + c);
+            }
         }
-        fin(c, a, b);
+        for (int o = tpc >> 1; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(FULL_MASK, a, o);
+            b += __shfl_xor_sync(FULL_MASK, b, o);
+        }
+        if (c < k && j == 0) fin(c, a, b);
     }
     __syncthreads();
     if (threadIdx.x == 0) *ticket = 0u;
@@ -299,7 +315,7 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
             }
         }
     }
-    if (DOT) colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double a, double b) { fin_rz(sc, c, a, b, flexible); });
+    if (DOT) colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double a, double b) { fin_rz(sc, c, a, b, flexible); });
 }
 
 
@@ -572,7 +588,7 @@ __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __rest
             }
         }
     }
-    colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double pq, double) {
+    colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double pq, double) {
         sc.pq[c] = pq;
         if (sc.mode[c] == COL_ACTIVE) {
             const double alpha = sc.rho[c] / pq;
@@ -616,7 +632,7 @@ __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restr
             d0[m] = fma(ri, ri, d0[m]);
         }
     }
-    colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double rr, double) {
+    colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double rr, double) {
         if (sc.mode[c] != COL_ACTIVE) return;
         sc.rr[c] = rr;
         sc.iters[c] += 1;
@@ -686,7 +702,7 @@ __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __rest
             d1[m] = fma(bi, bi, d1[m]);
         }
     }
-    colsum2<CPL>(d0, d1, g, k, partial, ticket, [&](int c, double rr, double bb) {
+    colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double rr, double bb) {
         const int md = sc.mode[c];
         if (stage == 0) {
             if (md != COL_INIT) return;
