@@ -784,6 +784,7 @@ def main():
             "setup_ms": round(statistics.mean(h["setup_ms"] for h in hinfos), 3),
             "solve_ms": round(statistics.mean(i["solve_ms"] for i in infos), 3),
             "levels": hi["n"], "opc": round(hi["opc"], 4), "solves_per_s": round(world * 1e3 / ms, 3),
+            "match_rounds": int(sum(sum(r) for r in hi["rounds"])),
             "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches), "accuracy": accuracy,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }

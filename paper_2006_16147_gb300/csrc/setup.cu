@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
     unsigned* bar = reinterpret_cast<unsigned*>(cnt + 6);
     int* err = cnt + 7;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-    __shared__ int s_chunks;
     unsigned epoch = 0;
     int items[BA_MAX];
     // round 0: mutual initial candidates
@@ -351,7 +350,6 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
     if (__ldcg(err)) return;
     if (leader && __ldcg(cnt + 0) > 0) cnt[8] += 1;
     constexpr int NG = 8;
-    const int gpb = blockDim.x / NG, grp = threadIdx.x / NG, gl = threadIdx.x % NG;
     for (long long r = 1;; ++r) {
         const int* M = lists[(r - 1) & 1];
         const int m_cnt = min(__ldcg(cnt + (int)((r - 1) % 3)), n);
@@ -364,48 +362,42 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
         int* nc = cnt + (int)(r % 3);
         // slot (r+1) % 3 was last read at the start of round r-1; it collects round r+1's pairs
         if (leader) cnt[(int)((r + 1) % 3)] = 0;
-        // one group of NG lanes per matched vertex, one lane per neighbour
-        for (int base = blockIdx.x * gpb; base < m_cnt; base += gridDim.x * gpb) {   // block-uniform trip count
-            const int t = base + grp;
-            int kb = 0, ke = 0, m = -1;
-            if (t < m_cnt) {
-                m = __ldcg(M + t);
-                kb = __ldg(ptr + m);
-                ke = __ldg(ptr + m + 1);
-            }
-            if (threadIdx.x == 0) s_chunks = 0;
-            __syncthreads();
-            const int my_chunks = (ke - kb + NG - 1) / NG;
-            if (gl == 0 && my_chunks > 0) atomicMax(&s_chunks, my_chunks);
-            __syncthreads();
-            const int chunks = s_chunks;
-            for (int ch = 0; ch < chunks; ++ch) {
-                int k = 0;
-                const int q = kb + ch * NG + gl;
-                if (q < ke) {
-                    const int x = __ldg(col + q);
-                    if (x != m && __ldcg(mate + x) == -1 && __ldcg(cand + x) == m) {
-                        const int b = best_free_sorted(x, ptr, nbr, pos, mate);
-                        cand[x] = b;
-                        if (b < 0) {
-                            mate[x] = -2;
-                        } else {
-                            fence_sc_gpu();
-                            if (__ldcg(cand + b) == x) {
-                                const int lo = min(x, b), hi = max(x, b);
-                                if (atomicCAS(&mate[lo], -1, hi) == -1) {
-                                    mate[hi] = lo;
-                                    items[0] = lo;
-                                    items[1] = hi;
-                                    k = 2;
-                                }
-                            }
-                        }
-                    }
+        // NG consecutive lanes per matched vertex, lane gl taking neighbours
+        // gl, gl + NG, ...; no block-wide synchronisation inside the round,
+        // so the work items of a thread overlap. Pairs are collected per
+        // thread (beyond BA_MAX straight into the list) and appended once.
+        int k = 0;
+        const long long total = (long long)m_cnt * NG;
+        for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+             u += (long long)gridDim.x * blockDim.x) {
+            const int t = (int)(u / NG), gl = (int)(u % NG);
+            const int m = __ldcg(M + t);
+            const int ke = __ldg(ptr + m + 1);
+            for (int q = __ldg(ptr + m) + gl; q < ke; q += NG) {
+                const int x = __ldg(col + q);
+                if (x == m || __ldcg(mate + x) != -1 || __ldcg(cand + x) != m) continue;
+                const int b = best_free_sorted(x, ptr, nbr, pos, mate);
+                cand[x] = b;
+                if (b < 0) {
+                    mate[x] = -2;
+                    continue;
                 }
-                block_append(k, items, nl, nc, n);
+                fence_sc_gpu();
+                if (__ldcg(cand + b) != x) continue;
+                const int lo = min(x, b), hi = max(x, b);
+                if (atomicCAS(&mate[lo], -1, hi) != -1) continue;
+                mate[hi] = lo;
+                if (k + 2 <= BA_MAX) {
+                    items[k++] = lo;
+                    items[k++] = hi;
+                } else {
+                    const int at = atomicAdd(nc, 2);
+                    if (at < n) nl[at] = lo;
+                    if (at + 1 < n) nl[at + 1] = hi;
+                }
             }
         }
+        block_append(k, items, nl, nc, n);
         grid_sync(bar, ++epoch, err);
         if (__ldcg(err)) return;
         if (leader && __ldcg(nc) > 0) cnt[8] += 1;
