@@ -68,10 +68,10 @@ def _args():
 # valid for the 7-point Poisson workload in FP64 and only while the kernel
 # source it was taken on is unchanged (checked by hash).
 _TRAFFIC = {
-    "post_smooth_l0": {"kernel": "k_post", "bytes_per_row": (381690368 + 27548672) / 4096000},
-    "pre_residual_l0": {"kernel": "k_pre", "bytes_per_row": (408898560 + 53249024) / 4096000},
+    "post_smooth_l0": {"kernel": "k_post", "bytes_per_row": (314713600 + 22986240) / 4096000},
+    "pre_residual_l0": {"kernel": "k_pre", "bytes_per_row": (408948992 + 53501184) / 4096000},
 }
-_TRAFFIC_SRC_HASH = "964387251ef6aa9b"
+_TRAFFIC_SRC_HASH = "e5fe5e8b08565c47"
 
 
 def _kernel_source_hash(names):
@@ -177,16 +177,14 @@ def _workload(grid, kind="poisson"):
     return A, b
 
 
-def _oracle_sample(grid, rtol):
-    """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance."""
+def _oracle_sample(grid, rtol, kind="poisson", flexible=False):
+    """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance of the workload."""
     import oracle
-    from paper_2006_16147_gb300 import workloads as W
-    A = W.poisson3d(grid)
-    b, _ = W.rhs_uniform(A, 1)
+    A, b = _workload(grid, kind)
     t0 = time.perf_counter()
     H = oracle.Hierarchy(A)
     t1 = time.perf_counter()
-    x, info = H.pcg(b, rtol=rtol)
+    x, info = H.pcg(b, rtol=rtol, flexible=flexible)
     t2 = time.perf_counter()
     return dict(setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"], n=A.n)
 
@@ -197,11 +195,11 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    grid = min(args.grid, 64)
+    grid = min(args.grid, 64 if args.workload == "poisson" else 48)
     n_full = args.grid ** 3
     times = []
     for k in range(args.warmup + args.steps):
-        r = _oracle_sample(grid, args.rtol)
+        r = _oracle_sample(grid, args.rtol, args.workload, args.krylov == 1)
         if k >= args.warmup:
             times.append((r["setup_s"] + r["solve_s"]) * 1e3 * n_full / r["n"])
     v = statistics.mean(times)
@@ -758,8 +756,8 @@ def main():
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
         oracle.build()
-        g = min(args.cpu_sample_grid, args.grid)
-        r = _oracle_sample(g, args.rtol)
+        g = min(args.cpu_sample_grid if args.workload == "poisson" else 48, args.grid)
+        r = _oracle_sample(g, args.rtol, args.workload, args.krylov == 1)
         scale = A.n / r["n"]
         cpu = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": (f"oracle setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s ({r['iterations']} it) "
