@@ -271,19 +271,35 @@ __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __re
     }
 }
 
-// Best free neighbour of v from its sorted list; advances pos[v].
-__device__ __forceinline__ int best_free_sorted(int v, const int* __restrict__ ptr, const int* __restrict__ nbr,
-                                                int* pos, const int* mate) {
-    const int e = __ldg(ptr + v + 1);
-    int k = __ldcg(pos + v);
+// Best free neighbour of v from its sorted list starting at k = pos[v]
+// (e = end of v's row); advances pos[v]. Four list entries and their mate
+// words are loaded together, so skipping matched neighbours costs two memory
+// latencies per four entries rather than two per entry.
+__device__ __forceinline__ int best_free_sorted(int v, int k, int e, const int* __restrict__ nbr, int* pos,
+                                                const int* mate) {
+    int found = -1;
     while (k < e) {
-        const int u = __ldg(nbr + k);
-        if (u < 0) { k = e; break; }
-        if (__ldcg(mate + u) == -1) break;
-        ++k;
+        int u[4], ms[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) u[t] = k + t < e ? __ldg(nbr + k + t) : -1;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) ms[t] = u[t] >= 0 ? __ldcg(mate + u[t]) : 0;
+        int t = 0;
+        for (; t < 4; ++t) {
+            if (u[t] < 0) {          // past the row or into its non-edges: nothing free
+                k = e;
+                break;
+            }
+            if (ms[t] == -1) {
+                found = u[t];
+                break;
+            }
+            ++k;
+        }
+        if (t < 4) break;
     }
     pos[v] = k;
-    return k < e ? __ldg(nbr + k) : -1;
+    return k < e ? found : -1;
 }
 
 // Appends each thread's k items (k <= BA_MAX) to list[*cnt...] with one
@@ -375,8 +391,11 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
             const int ke = __ldg(ptr + m + 1);
             for (int q = __ldg(ptr + m) + gl; q < ke; q += NG) {
                 const int x = __ldg(col + q);
-                if (x == m || __ldcg(mate + x) != -1 || __ldcg(cand + x) != m) continue;
-                const int b = best_free_sorted(x, ptr, nbr, pos, mate);
+                // x's state and its list position together (one latency)
+                const int mx = __ldcg(mate + x), cx = __ldcg(cand + x);
+                const int kx = __ldcg(pos + x), ex = __ldg(ptr + x + 1);
+                if (x == m || mx != -1 || cx != m) continue;
+                const int b = best_free_sorted(x, kx, ex, nbr, pos, mate);
                 cand[x] = b;
                 if (b < 0) {
                     mate[x] = -2;
