@@ -109,8 +109,19 @@ __global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restr
 // mate[v]: -1 free, -2 free without free neighbours, >= 0 partner.
 // cand[v]: best free neighbour of a free v under the strict edge order
 // (weight descending, lower end ascending, upper end ascending).
+// The weight comparison runs on integers: the bits of a non-NaN double,
+// with the magnitude bits flipped when the sign is set (and -0 taken as +0),
+// order like the double itself. On this GPU a double compare issues on the
+// FP64 pipe, which runs at 1/64 of the FP32 rate; integer compares do not.
+__device__ __forceinline__ long long weight_order(double c) {
+    const long long b = __double_as_longlong(c);
+    if (b == (long long)0x8000000000000000ULL) return 0;
+    return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+
 __device__ __forceinline__ bool key_better(double c1, int lo1, int hi1, double c2, int lo2, int hi2) {
-    if (c1 != c2) return c1 > c2;
+    const long long k1 = weight_order(c1), k2 = weight_order(c2);
+    if (k1 != k2) return k1 > k2;
     if (lo1 != lo2) return lo1 < lo2;
     return hi1 < hi2;
 }
@@ -242,11 +253,16 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned epoch, int* 
 
 // Sorts row v's edges by the strict order into (sc, nbr) at the row's own
 // CSR segment; entries that are not edges go last with nbr = -1.
+// With `list` set, only the rows list[0 .. *nlist) (those the group kernel
+// below leaves out).
 __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                              const double* __restrict__ c, double* __restrict__ sc, int* __restrict__ nbr,
-                             int* __restrict__ pos, int* __restrict__ cand, int* mate) {
+                             int* __restrict__ pos, int* __restrict__ cand, int* mate, const int* __restrict__ list,
+                             const int* __restrict__ nlist) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int nr = list ? *nlist : n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
+        const int v = list ? list[t] : t;
         const int b = ptr[v], e = ptr[v + 1];
         int m = b;
         for (int k = b; k < e; ++k) {
@@ -268,6 +284,69 @@ __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __re
         pos[v] = b;
         cand[v] = m > b ? nbr[b] : -1;
         if (m == b) mate[v] = -2;
+    }
+}
+
+// The same for rows of at most G entries, one group of G lanes per row: lane
+// t holds entry t, its rank among the row's edges under the strict order comes
+// from a shuffle sweep (edges have distinct keys), non-edges follow the edges
+// in position order; entries are written to their ranks. Longer rows are
+// listed in long_list for k_sort_edges.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __restrict__ ptr,
+                                                         const int* __restrict__ col, const double* __restrict__ c,
+                                                         int* __restrict__ nbr, int* __restrict__ pos,
+                                                         int* __restrict__ cand, int* mate, int* __restrict__ long_list,
+                                                         int* __restrict__ nlong) {
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int v0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int warp_first = v0 - (lane - gl) / G;     // every lane of a warp runs the same iterations
+    for (int it = 0; warp_first + it * ng < n; ++it) {
+        const int v = v0 + it * ng;
+        int b = 0, len = 0;
+        if (v < n) {
+            b = ptr[v];
+            len = ptr[v + 1] - b;
+            if (len > G) {
+                if (gl == 0) long_list[atomicAdd(nlong, 1)] = v;
+                len = -1;
+            }
+        }
+        double cw = NEG_INF;
+        int u = -1, lo = 0x7fffffff, hi = 0x7fffffff, edge = 0;
+        if (gl < len) {
+            cw = c[b + gl];
+            u = col[b + gl];
+            edge = cw != NEG_INF;
+            lo = min(u, v);
+            hi = max(u, v);
+        }
+        int better = 0, nedge = 0, nonedge_before = 0;
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            const double ct = __shfl_sync(FULL_MASK, cw, t, G);
+            const int lot = __shfl_sync(FULL_MASK, lo, t, G);
+            const int hit = __shfl_sync(FULL_MASK, hi, t, G);
+            const int et = __shfl_sync(FULL_MASK, edge, t, G);
+            nedge += et;
+            better += et && key_better(ct, lot, hit, cw, lo, hi);
+            nonedge_before += (t < gl && t < len && !et);
+        }
+        if (gl < len) {
+            const int rank = edge ? better : nedge + nonedge_before;
+            nbr[b + rank] = edge ? u : -1;
+            if (edge && rank == 0) cand[v] = u;
+        }
+        if (gl == 0 && len >= 0 && v < n) {
+            pos[v] = b;
+            if (nedge == 0) {
+                cand[v] = -1;
+                mate[v] = -2;
+            }
+        }
     }
 }
 
@@ -994,7 +1073,21 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
         double* sc = S.sval;
         int* pos = S.flag;
         CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 16, st));
-        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate);
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 9, 0, sizeof(int), st));
+        const int G = rows_group(A.nnz, n);
+        const int gblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
+        if (G == 8)
+            k_sort_edges_group<8><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                           S.cnt + 9);
+        else if (G == 16)
+            k_sort_edges_group<16><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                            S.cnt + 9);
+        else
+            k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                            S.cnt + 9);
+        KERNEL_CHECK();
+        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate, S.list1,
+                                                     S.cnt + 9);
         KERNEL_CHECK();
         int nn = n;
         const int* ptr = A.ptr;
