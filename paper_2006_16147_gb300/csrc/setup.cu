@@ -67,12 +67,21 @@ __global__ void k_check_rows(int n, const int* __restrict__ ptr, const int* __re
     }
 }
 
+// dww[i] = (a_ii w_i) w_i, the per-vertex half of the weight denominator
+// (the same rounded value in every edge of i).
 __global__ void k_diag(int n, const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
-                       double* __restrict__ diag) {
+                       const double* __restrict__ w, double* __restrict__ dww) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int k = find_in_row(ptr, col, i, i);
-        diag[i] = k >= 0 ? val[k] : 0.0;
+        const double d = k >= 0 ? val[k] : 0.0;
+        dww[i] = __dmul_rn(__dmul_rn(d, w[i]), w[i]);
     }
+}
+
+// In place: diag[i] <- (diag[i] w_i) w_i.
+__global__ void k_dww(int n, double* __restrict__ diag, const double* __restrict__ w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        diag[i] = __dmul_rn(__dmul_rn(diag[i], w[i]), w[i]);
 }
 
 // --------------------------------------------------- Eq. 3 edge weights ----
@@ -80,12 +89,18 @@ __global__ void k_diag(int n, const int* __restrict__ ptr, const int* __restrict
 // from the upper entry a_{lo,hi}; written at both stored positions of the
 // pair. Diagonal entries and pairs whose upper entry is 0 are not edges and
 // get -inf.
+// dww = (a_ii w_i) w_i per vertex (k_diag / k_dww): the denominator is
+// dww_i + dww_j, the same rounded terms as evaluated per edge; the numerator
+// (2 a) w_i w_j is formed as (a (2 w_i)) w_j, the same single rounding of
+// the same exact product. FP64 work per edge: one add, two multiplies, the
+// division and the subtraction (this GPU's FP64 pipe bounds this kernel).
 __global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                          const double* __restrict__ val, const double* __restrict__ diag,
+                          const double* __restrict__ val, const double* __restrict__ dww,
                           const double* __restrict__ w, double* __restrict__ c) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double wi = w[i], di = diag[i];
+        const double wi = w[i], si = dww[i];
+        const double w2i = wi + wi;
         for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
             const int j = col[k];
             if (j < i) continue;                 // written by the thread of row j
@@ -93,9 +108,8 @@ __global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restr
             const double a = val[k];
             double cw = NEG_INF;
             if (a != 0.0) {
-                const double wj = w[j];
-                double den = __dadd_rn(__dmul_rn(__dmul_rn(di, wi), wi), __dmul_rn(__dmul_rn(diag[j], wj), wj));
-                double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, a), wi), wj);
+                const double den = __dadd_rn(si, dww[j]);
+                const double num = __dmul_rn(__dmul_rn(a, w2i), w[j]);
                 cw = __dsub_rn(1.0, __ddiv_rn(num, den));
             }
             c[k] = cw;
@@ -1389,7 +1403,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             const int n = A.n;
             {
                 Scope sc_(&h->prof, st, S_WEIGHTS, 20.0 * A.nnz + 24.0 * n);
-                k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag);
+                k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
                 KERNEL_CHECK();
                 k_weights<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag, w, S.c);
                 KERNEL_CHECK();
@@ -1685,6 +1699,8 @@ amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void*
     if (f & F_NOT_SPD) AMG_THROW(AMG_ERR_NOT_SPD, "non-finite value or diagonal entry missing or <= 0");
     if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "smooth vector w has a zero or non-finite entry");
 
+    k_dww<<<grid, TPB, 0, st>>>(n, diag, w);
+    KERNEL_CHECK();
     k_weights<<<grid, TPB, 0, st>>>(n, ptr, col, val, diag, w, c);
     KERNEL_CHECK();
     CUDA_CHECK(cudaMemsetAsync(mate, 0xff, sizeof(int) * n, st));
