@@ -654,7 +654,8 @@ __global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restr
                                                   const int* __restrict__ agg, const double* __restrict__ p,
                                                   const int* __restrict__ off, int* __restrict__ skey,
                                                   double* __restrict__ sval, int* __restrict__ cnt,
-                                                  int* __restrict__ long_list, int* __restrict__ nlong) {
+                                                  int* __restrict__ long_list, int* __restrict__ nlong,
+                                                  const double* __restrict__ rowscale) {
     __shared__ int sk[TPB];
     __shared__ double sv[TPB];
     const int lane = threadIdx.x & 31;
@@ -714,6 +715,7 @@ __global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restr
             const int kk = sk[threadIdx.x];
             double sum = sv[threadIdx.x];
             for (int e = gl + 1; e < len && sk[gbase + e] == kk; ++e) sum = __dadd_rn(sum, sv[gbase + e]);
+            if (rowscale) sum = __dmul_rn(rowscale[q], sum);
             const int u = __popc(hm & ((1u << lane) - 1u));
             skey[off[q] + u] = kk;
             sval[off[q] + u] = sum;
@@ -733,17 +735,17 @@ int rows_group(long long terms, long long rows) {
 template <bool RAP>
 void launch_rows(amg_hierarchy* h, int G, int nrows, const int* heads, const int* mate, const int* ptr,
                  const int* col, const double* val, const int* agg, const double* p, const int* off, int* skey,
-                 double* sval, int* cnt, int* long_list, int* nlong, cudaStream_t st) {
+                 double* sval, int* cnt, int* long_list, int* nlong, const double* rowscale, cudaStream_t st) {
     const int blocks = blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
     if (G == 8)
         k_rows_warp<RAP, 8><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                    long_list, nlong);
+                                                    long_list, nlong, rowscale);
     else if (G == 16)
         k_rows_warp<RAP, 16><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                     long_list, nlong);
+                                                     long_list, nlong, rowscale);
     else
         k_rows_warp<RAP, 32><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                     long_list, nlong);
+                                                     long_list, nlong, rowscale);
     KERNEL_CHECK();
 }
 
@@ -977,15 +979,6 @@ __global__ void k_gram(int n, const double* __restrict__ Y, double* __restrict__
 }
 
 // Column scaling for the pre-smoother: valm_k = val_k * minv[col_k].
-// Rows of a CSR matrix scaled in place: row i times omega / M_ii.
-__global__ void k_scale_rows(int n, const int* __restrict__ ptr, double* __restrict__ val,
-                             const double* __restrict__ minv, double omega) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double s = omega * minv[i];
-        for (int k = ptr[i]; k < ptr[i + 1]; ++k) val[k] = s * val[k];
-    }
-}
-
 // omega M^{-1} when omega != 1.
 __global__ void k_scale_vec(int n, double omega, const double* __restrict__ a, double* __restrict__ b,
                             float* __restrict__ b32) {
@@ -1010,7 +1003,8 @@ __global__ void k_scale_cols(long long m, const int* __restrict__ col, const dou
 __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                           const double* __restrict__ val, const int* __restrict__ agg, const double* __restrict__ p,
                           int* __restrict__ skey, double* __restrict__ sval, int* __restrict__ cnt,
-                          const int* __restrict__ list, const int* __restrict__ nlist) {
+                          const int* __restrict__ list, const int* __restrict__ nlist,
+                          const double* __restrict__ rowscale) {
     const int nr = list ? *nlist : n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
         const int i = list ? list[t] : t;
@@ -1037,7 +1031,7 @@ __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restr
             int e = a + 1;
             while (e < len && K[e] == key) { sum = __dadd_rn(sum, V[e]); ++e; }
             K[u] = key;
-            V[u] = sum;
+            V[u] = rowscale ? __dmul_rn(rowscale[i], sum) : sum;
             ++u;
             a = e;
         }
@@ -1161,7 +1155,7 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     scan_exclusive(S.ub, S.off, nc, S.cnt + 6, st, S.scan_tmp);
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
     launch_rows<true>(h, rows_group(2LL * A.nnz, A.n), nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
-                      S.skey, S.sval, S.ub, S.list1, S.cnt + 8, st);
+                      S.skey, S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
     k_rap_rows<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
                                                 S.skey, S.sval, S.ub, S.list1, S.cnt + 8);
     KERNEL_CHECK();
@@ -1263,9 +1257,9 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     const int n = L.A.n;
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
     launch_rows<false>(h, rows_group(L.A.nnz, n), n, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
-                       L.A.ptr, S.skey, S.sval, S.ub, S.list1, S.cnt + 8, st);
+                       L.A.ptr, S.skey, S.sval, S.ub, S.list1, S.cnt + 8, L.wminv, st);
     k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, S.skey, S.sval, S.ub,
-                                              S.list1, S.cnt + 8);
+                                              S.list1, S.cnt + 8, L.wminv);
     KERNEL_CHECK();
     DevCsr AP;
     AP.n = n;
@@ -1275,8 +1269,6 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     AP.col = S.mem.alloc<int>(AP.nnz);
     AP.val = S.mem.alloc<double>(AP.nnz);
     launch_copy(h, AP.nnz, n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val, st);
-    k_scale_rows<<<grid_for(h, n), TPB, 0, st>>>(n, AP.ptr, AP.val, L.minv, h->opt.omega);
-    KERNEL_CHECK();
     L.ap_nnz = AP.nnz;
     build_sell(h, AP, L.AP, S, fp32);
     CUDA_CHECK(cudaStreamSynchronize(st));
