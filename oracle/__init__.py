@@ -45,6 +45,7 @@ def lib():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, _ip]
             L.orc_coarse_is_cg.argtypes = [ctypes.c_void_p]
+            L.orc_set_cycle.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_setup_seg.restype = ctypes.c_void_p
             L.orc_setup_seg.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -126,7 +127,7 @@ class Hierarchy:
     """Oracle hierarchy: setup in the constructor, then V-cycle and PCG."""
 
     def __init__(self, A, w=None, sweeps=3, max_coarse=200, max_levels=32, pre=1, post=1, omega=1.0,
-                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None):
+                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None, cycle=0):
         rp, cl, vl = _csr_args(A)
         w = np.ones(A.n) if w is None else np.ascontiguousarray(w, dtype=np.float64)
         st = ctypes.c_int(0)
@@ -137,6 +138,7 @@ class Hierarchy:
                                       ctypes.byref(st))
         if not self._h:
             raise OracleError(f"orc_setup failed: {st.value}")
+        lib().orc_set_cycle(self._h, int(cycle))
         self.n = A.n
 
     def __del__(self):

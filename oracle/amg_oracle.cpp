@@ -29,6 +29,10 @@
 //   V-cycle (Eq. 2)                  -- dense error-propagation product; SPD
 //   PCG                              -- dense Cholesky solve of A
 //   flexible CG (FCG(1))             -- equals PCG for a fixed SPD preconditioner
+//   K-cycle (fcg2 coarse correction) -- equals the V-cycle with two levels; on a
+//                                       level whose coarse level has two rows it
+//                                       equals the two-grid cycle with an exact
+//                                       coarse solve (two Krylov steps span R^2)
 // Nothing here is "parity unpinned".
 #include <algorithm>
 #include <cmath>
@@ -280,6 +284,7 @@ struct Hierarchy {
     std::vector<int> cseg;
     std::vector<std::vector<double>> Lb;
     int pre = 1, post = 1;
+    int kcycle = 0;                // 1: K-cycle (two FCG iterations on every intermediate level)
     double omega = 1.0;
     int use_ld = 0;
 };
@@ -477,9 +482,37 @@ void coarse_cg(const Level& L, const double* b, double* x) {
     }
 }
 
+double dot(const double* a, const double* b, int n);
+void vcycle(const Hierarchy& H, int l, const double* b, double* x);
+
+// Coarse correction of the K-cycle (Section 3.3, the cycle used with the
+// unsmoothed prolongator): two iterations of flexible CG on A_m e = b from
+// e = 0, preconditioned by the cycle that starts on level m.
+void fcg2(const Hierarchy& H, int m, const double* b, double* e) {
+    const Csr& A = H.lev[m].A;
+    const int n = A.n;
+    std::vector<double> d1(n), q1(n), r2(n), z2(n), d2(n), q2(n);
+    vcycle(H, m, b, d1.data());                              // d1 = B_m b
+    spmv(A, d1.data(), q1.data());
+    const double rho1 = dot(d1.data(), q1.data(), n);
+    const double alpha1 = rho1 != 0.0 ? dot(d1.data(), b, n) / rho1 : 0.0;
+    for (int i = 0; i < n; ++i) {
+        e[i] = alpha1 * d1[i];
+        r2[i] = b[i] - alpha1 * q1[i];
+    }
+    vcycle(H, m, r2.data(), z2.data());                      // z2 = B_m r2
+    const double beta = rho1 != 0.0 ? dot(z2.data(), q1.data(), n) / rho1 : 0.0;
+    for (int i = 0; i < n; ++i) d2[i] = z2[i] - beta * d1[i];   // A-orthogonal to d1
+    spmv(A, d2.data(), q2.data());
+    const double rho2 = dot(d2.data(), q2.data(), n);
+    const double alpha2 = rho2 != 0.0 ? dot(d2.data(), r2.data(), n) / rho2 : 0.0;
+    for (int i = 0; i < n; ++i) e[i] = e[i] + alpha2 * d2[i];
+}
+
 // B_l b for the V-cycle of Eq. 2: pre-smoothing from a zero guess, coarse
 // correction with the restricted residual, post-smoothing; the coarsest level
-// is solved exactly.
+// is solved exactly. With the K-cycle, the coarse correction on a level that
+// is not the coarsest is fcg2 instead of one recursive cycle.
 void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const Level& L = H.lev[l];
     const int n = L.A.n;
@@ -502,7 +535,8 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const int nc = H.lev[l + 1].A.n;
     std::vector<double> bc(nc, 0.0), ec(nc);
     for (int i = 0; i < n; ++i) bc[L.agg[i]] = bc[L.agg[i]] + L.p[i] * r[i];     // P^T r, members ascending
-    vcycle(H, l + 1, bc.data(), ec.data());
+    if (H.kcycle && l + 2 < (int)H.lev.size()) fcg2(H, l + 1, bc.data(), ec.data());
+    else vcycle(H, l + 1, bc.data(), ec.data());
     for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
     for (int s = 0; s < H.post; ++s) smooth(L, H.omega, b, x);
 }
@@ -727,6 +761,9 @@ void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* 
 }
 
 int orc_coarse_is_cg(void* h) { return static_cast<Hierarchy*>(h)->coarse_cg; }
+
+// 0: V-cycle, 1: K-cycle.
+void orc_set_cycle(void* h, int kcycle) { static_cast<Hierarchy*>(h)->kcycle = kcycle; }
 
 void orc_coarse_factor(void* h, double* L) {
     const Hierarchy* H = static_cast<Hierarchy*>(h);
