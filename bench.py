@@ -43,6 +43,10 @@ def _args():
     ap.add_argument("--workload", default="poisson", choices=["poisson", "varcoef"],
                     help="poisson: 7-point Laplacian (default line); varcoef: jump coefficients exp(g), sigma 2")
     ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
+    ap.add_argument("--cycle", default="v", choices=["v", "k"],
+                    help="v: V-cycle (default line); k: K-cycle, two FCG iterations as the coarse correction")
+    ap.add_argument("--kdepth", type=int, default=32,
+                    help="K-cycle on coarse levels 1..kdepth (32: every intermediate level, the paper's cycle)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
@@ -660,7 +664,7 @@ def main():
     def step(profile=0, keep=False):
         d_x.zero_()
         h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, krylov=args.krylov,
-                          autotune=args.autotune, stream=stream.cuda_stream)
+                          autotune=args.autotune, cycle=args.kdepth if args.cycle == "k" else 0, stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
             return h, info
@@ -711,14 +715,15 @@ def main():
     # ---- accuracy of a mixed-precision or non-default run: error against an
     # FP64 solve of the same system to rel-res 1e-10, and iterations at 1e-8
     accuracy = None
-    if args.precision == "fp32" or args.workload != "poisson":
+    if args.precision == "fp32" or args.workload != "poisson" or args.cycle == "k":
         accuracy = {}
         h64 = amg.amg_setup(d_ptr, d_col, d_val, d_w, stream=stream.cuda_stream)
         xr = torch.zeros_like(d_x)
         amg.amg_solve(h64, d_b, xr, rtol=1e-10, maxit=2000)
         h64.close()
         for tol in (args.rtol, 1e-8):
-            hh = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov, stream=stream.cuda_stream)
+            hh = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov,
+                               cycle=args.kdepth if args.cycle == "k" else 0, stream=stream.cuda_stream)
             xt = torch.zeros_like(d_x)
             inf = amg.amg_solve(hh, d_b, xt, rtol=tol, maxit=2000)
             hh.close()
@@ -749,13 +754,16 @@ def main():
               for k, v in dict(ptr=A.row_ptr, col=A.col, val=A.val, w=np.ones(A.n), b=b).items()}
         xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
         e2e_steps = max(1, min(3, args.steps))
-        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov)
+        kc = args.kdepth if args.cycle == "k" else 0
+        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
+                                   cycle=kc)
         amg_h.close()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             xh[:] = 0.0
-            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov)
+            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
+                                    cycle=kc)
             amg.amg_solve_host(hh, hp["b"], xh, rtol=args.rtol, maxit=1000)
             hh.close()
         barrier()
@@ -784,8 +792,9 @@ def main():
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle",
             "data": "synthetic",
             "config": {"workload": (f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve" if args.workload == "poisson" else
-                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve"),
-                       "grid": args.grid,
+                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve") +
+                                   (f"_kcycle{args.kdepth}" if args.cycle == "k" else ""),
+                       "grid": args.grid, "cycle": args.cycle, "kdepth": args.kdepth if args.cycle == "k" else None,
                        "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
                        "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",
                        "precision": args.precision, "autotune": args.autotune,

@@ -65,6 +65,9 @@ typedef struct {
     const double* val;
 } amg_csr;
 
+/* amg_options.cycle value for the K-cycle on every intermediate level. */
+#define AMG_KCYCLE_FULL 32
+
 /* Options; amg_options_default fills the defaults noted in brackets. */
 typedef struct {
     int sweeps;        /* [3] pairwise matching steps per level; aggregates up to 2^sweeps (Section 3.2) */
@@ -81,6 +84,13 @@ typedef struct {
     int match_kernel;  /* [0] matching rounds in one cooperative launch when possible; 1: a launch pair per round */
     int krylov;        /* [0] 0 = PCG; 1 = flexible CG keeping one direction (FCG(1), the paper's outer
                           solver, Section 5), robust to a V-cycle that is not exactly linear (FP32) */
+    int cycle;         /* [0] 0: V-cycle (Eq. 2). c >= 1: K-cycle on the first c coarse levels: on levels
+                          1..c (those that are not the coarsest) the coarse correction is two flexible CG
+                          iterations preconditioned by the cycle starting on that level; deeper levels use
+                          the V-cycle. AMG_KCYCLE_FULL is the paper's K-cycle on every intermediate level
+                          (Section 3.3, the cycle it uses with this unsmoothed aggregation). The
+                          preconditioner is then not linear, so the outer solver is flexible CG whatever
+                          `krylov` says. Requires pre = post = 1; single right-hand-side solves only */
     int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */

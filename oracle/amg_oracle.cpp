@@ -284,7 +284,7 @@ struct Hierarchy {
     std::vector<int> cseg;
     std::vector<std::vector<double>> Lb;
     int pre = 1, post = 1;
-    int kcycle = 0;                // 1: K-cycle (two FCG iterations on every intermediate level)
+    int kcycle = 0;                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
     double omega = 1.0;
     int use_ld = 0;
 };
@@ -511,8 +511,8 @@ void fcg2(const Hierarchy& H, int m, const double* b, double* e) {
 
 // B_l b for the V-cycle of Eq. 2: pre-smoothing from a zero guess, coarse
 // correction with the restricted residual, post-smoothing; the coarsest level
-// is solved exactly. With the K-cycle, the coarse correction on a level that
-// is not the coarsest is fcg2 instead of one recursive cycle.
+// is solved exactly. With the K-cycle, the coarse correction on a level
+// 1..kcycle that is not the coarsest is fcg2 instead of one recursive cycle.
 void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const Level& L = H.lev[l];
     const int n = L.A.n;
@@ -535,7 +535,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const int nc = H.lev[l + 1].A.n;
     std::vector<double> bc(nc, 0.0), ec(nc);
     for (int i = 0; i < n; ++i) bc[L.agg[i]] = bc[L.agg[i]] + L.p[i] * r[i];     // P^T r, members ascending
-    if (H.kcycle && l + 2 < (int)H.lev.size()) fcg2(H, l + 1, bc.data(), ec.data());
+    if (H.kcycle > l && l + 2 < (int)H.lev.size()) fcg2(H, l + 1, bc.data(), ec.data());
     else vcycle(H, l + 1, bc.data(), ec.data());
     for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
     for (int s = 0; s < H.post; ++s) smooth(L, H.omega, b, x);
@@ -762,7 +762,7 @@ void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* 
 
 int orc_coarse_is_cg(void* h) { return static_cast<Hierarchy*>(h)->coarse_cg; }
 
-// 0: V-cycle, 1: K-cycle.
+// 0: V-cycle; c > 0: K-cycle on coarse levels 1..c (c >= levels - 2: on every intermediate level).
 void orc_set_cycle(void* h, int kcycle) { static_cast<Hierarchy*>(h)->kcycle = kcycle; }
 
 void orc_coarse_factor(void* h, double* L) {

@@ -38,6 +38,7 @@ EXPORTED = [
     "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free", "amg_setup_many",
     "amg_solve_many", "amg_system_offsets", "amg_tune_save", "amg_tune_load", "amg_tune_clear", "amg_tune_size",
 ]
+KCYCLE_FULL = 32
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_NNZ = 524288
 
@@ -52,7 +53,8 @@ class amg_options(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
                 ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("cycle", ctypes.c_int), ("autotune", ctypes.c_int), ("min_ratio", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):

@@ -149,6 +149,9 @@ struct Level {
     int sweeps_done = 0;
     int rounds[AMG_MAX_SWEEPS] = {0};
     std::vector<SweepRecord> sweeps;
+    // K-cycle work vectors of this level as the coarse level of an FCG(2)
+    // correction (d1, q1, r2, z2, d2, e), in the V-cycle's value type
+    void* kv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // launch shapes chosen by the autotuner, indexed by value type (0 FP64,
     // 1 FP32); 0 = the fixed heuristic
     int grid_pre[2] = {0, 0}, grid_post[2] = {0, 0}, grid_restrict[2] = {0, 0};
@@ -167,6 +170,14 @@ struct PcgScalars {
     double bb;        // ||b||^2
     int breakdown;
     int pad;
+};
+
+// Device scalars of the two FCG iterations of the K-cycle on one level.
+struct KcScalars {
+    double rho1;     // d1 . A d1
+    double alpha1;   // d1 . b / rho1
+    double beta;     // z2 . A d1 / rho1
+    double alpha2;   // d2 . r2 / d2 . A d2
 };
 
 // Workspace of the iterative coarsest solve (coarsest level above max_dense).
@@ -237,6 +248,7 @@ struct amg_hierarchy {
     amg::PcgScalars* sc = nullptr;      // device
     amg::PcgScalars* sc_host = nullptr; // pinned mirror
     amg::Reducer red;
+    amg::KcScalars* ks = nullptr;       // K-cycle scalars, one per level (device)
     amg::BlockWork* blk = nullptr;      // block-solve workspace, created on first use
     // batch of independent systems (block-diagonal union): system offsets
     std::vector<int> seg0;               // level 0, m + 1 entries (empty: one system)

@@ -63,8 +63,9 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     if (o.sweeps < 1 || o.sweeps > AMG_MAX_SWEEPS || o.max_levels < 1 || o.max_coarse < 1 || o.pre < 0 ||
         o.post < 0 || !(o.omega > 0.0) || (o.precision != AMG_FP64 && o.precision != AMG_FP32_VCYCLE) ||
         o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0) || o.autotune < 0 ||
-        o.autotune > 1)
+        o.autotune > 1 || o.cycle < 0 || o.cycle > AMG_KCYCLE_FULL || (o.cycle > 0 && (o.pre != 1 || o.post != 1)))
         return fail(AMG_ERR_ARG, "invalid options");
+    if (many && o.cycle != 0) return fail(AMG_ERR_ARG, "batches of systems use the V-cycle");
     amg_hierarchy* h = new amg_hierarchy;
     h->opt = o;
     h->stream = static_cast<cudaStream_t>(o.stream);

@@ -25,6 +25,7 @@ enum KernelId : int {
     K_RESIDUAL,       // r = b - A x, norms
     K_DOT,            // stand-alone dot product
     K_CONVERT,        // FP64 -> FP32 copy of the level-0 residual (FP32 V-cycle)
+    K_KFCG,           // K-cycle: the flexible CG steps of a coarse correction
     // setup phase, one scope per phase call
     S_VALIDATE,
     S_WEIGHTS,
@@ -42,7 +43,7 @@ inline const char* kernel_name(int id) {
     static const char* names[K_COUNT] = {
         "pre_residual",   "pre_residual_l0", "pre_step",     "restrict",  "coarse_solve", "post_smooth",
         "post_smooth_l0", "smooth",          "spmv_dot",     "update_xr", "update_p",     "residual",
-        "dot",            "convert_l0",      "setup_validate",  "setup_weights", "setup_match", "setup_aggregate", "setup_galerkin",
+        "dot",            "convert_l0",      "kcycle_fcg",   "setup_validate",  "setup_weights", "setup_match", "setup_aggregate", "setup_galerkin",
         "setup_compose",  "setup_smoother",  "setup_format", "setup_coarse"};
     return (id >= 0 && id < K_COUNT) ? names[id] : "";
 }

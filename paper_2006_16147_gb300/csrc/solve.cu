@@ -65,8 +65,10 @@ __device__ void finish(int mode, double a, double b, PcgScalars* sc) {
 }
 
 // Block partial sums, then the last block to arrive combines all partials in
-// a fixed order (deterministic for a fixed grid) and runs the finisher.
-__device__ __forceinline__ void reduce_and_finish(double a, double b, Reducer red, PcgScalars* sc, int mode) {
+// a fixed order (deterministic for a fixed grid) and calls fin(sum_a, sum_b)
+// on one thread.
+template <typename FIN>
+__device__ __forceinline__ void reduce_then(double a, double b, Reducer red, FIN&& fin) {
     __shared__ bool last;
     a = block_sum(a);
     b = block_sum(b);
@@ -87,9 +89,13 @@ __device__ __forceinline__ void reduce_and_finish(double a, double b, Reducer re
     sa = block_sum(sa);
     sb = block_sum(sb);
     if (threadIdx.x == 0) {
-        finish(mode, sa, sb, sc);
+        fin(sa, sb);
         *red.ticket = 0u;
     }
+}
+
+__device__ __forceinline__ void reduce_and_finish(double a, double b, Reducer red, PcgScalars* sc, int mode) {
+    reduce_then(a, b, red, [&](double sa, double sb) { finish(mode, sa, sb, sc); });
 }
 
 struct SellView {
@@ -232,6 +238,102 @@ void launch_post(bool u, int grid, cudaStream_t st, SellView SAP, const T* apw, 
     if (u) k_post<T, TB, TO, DOT, true><<<grid, TPB, 0, st>>>(SAP, apw, wm, agg, p, e, x, r, bdot, out, red, sc, mode, q2);
     else k_post<T, TB, TO, DOT, false><<<grid, TPB, 0, st>>>(SAP, apw, wm, agg, p, e, x, r, bdot, out, red, sc, mode, q2);
     KERNEL_CHECK();
+}
+
+// ------------------------------------------------------------ K-cycle ------
+// The coarse correction of a K-cycle on level m: two flexible CG iterations
+// on A_m e = b from e = 0, preconditioned by the cycle that starts on level m
+// (Section 3.3). d1 = B b; q1 = A d1; alpha1 = d1.b / d1.q1; e = alpha1 d1;
+// r2 = b - alpha1 q1; z2 = B r2; beta = z2.q1 / d1.q1; d2 = z2 - beta d1;
+// q2 = A d2 = A z2 - beta q1; alpha2 = d2.r2 / d2.q2; e += alpha2 d2. The
+// scalars stay on the device; dot products are summed in FP64.
+enum KcMode : int { KC_ALPHA1 = 0, KC_BETA = 1, KC_ALPHA2 = 2 };
+
+__device__ __forceinline__ void kc_finish(KcScalars* ks, int mode, double a, double b) {
+    if (mode == KC_ALPHA1) {
+        ks->rho1 = a;
+        ks->alpha1 = a != 0.0 ? b / a : 0.0;
+    } else if (mode == KC_BETA) {
+        ks->beta = ks->rho1 != 0.0 ? a / ks->rho1 : 0.0;
+    } else {
+        ks->alpha2 = a != 0.0 ? b / a : 0.0;
+    }
+}
+
+// q1 = A d1; d1.q1 and d1.b -> rho1, alpha1.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_kc_spmv_dot(SellView S, const T* __restrict__ val, const T* __restrict__ d1,
+                                                     T* __restrict__ q1, const T* __restrict__ b, Reducer red,
+                                                     KcScalars* ks) {
+    double dq = 0.0, db = 0.0;
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return ld(d1 + j); });
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
+            q1[i] = acc;
+            const double di = (double)d1[i];
+            dq = fma(di, (double)acc, dq);
+            db = fma(di, (double)b[i], db);
+        }
+    }
+    reduce_then(dq, db, red, [&](double a, double c) { kc_finish(ks, KC_ALPHA1, a, c); });
+}
+
+// e = alpha1 d1; r2 = b - alpha1 q1.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_kc_update1(int n, const T* __restrict__ d1, const T* __restrict__ q1,
+                                                    const T* __restrict__ b, T* __restrict__ e, T* __restrict__ r2,
+                                                    const KcScalars* ks) {
+    const T a = (T)ks->alpha1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        e[i] = a * d1[i];
+        r2[i] = fma(-a, q1[i], b[i]);
+    }
+}
+
+// z2.q1 -> beta.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_kc_dot(int n, const T* __restrict__ z2, const T* __restrict__ q1, Reducer red,
+                                                KcScalars* ks) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s = fma((double)z2[i], (double)q1[i], s);
+    reduce_then(s, 0.0, red, [&](double a, double) { kc_finish(ks, KC_BETA, a, 0.0); });
+}
+
+// d2 = z2 - beta d1; q2 = A z2 - beta q1 (= A d2, without a second product);
+// d2.q2 and d2.r2 -> alpha2.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_kc_spmv2(SellView S, const T* __restrict__ val, const T* __restrict__ z2,
+                                                  const T* __restrict__ q1, const T* __restrict__ d1,
+                                                  const T* __restrict__ r2, T* __restrict__ d2, Reducer red,
+                                                  KcScalars* ks) {
+    const T be = (T)ks->beta;
+    double dq = 0.0, dr = 0.0;
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return ld(z2 + j); });
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
+            const T q2 = fma(-be, q1[i], acc);
+            const T di = fma(-be, d1[i], z2[i]);
+            d2[i] = di;
+            dq = fma((double)di, (double)q2, dq);
+            dr = fma((double)di, (double)r2[i], dr);
+        }
+    }
+    reduce_then(dq, dr, red, [&](double a, double c) { kc_finish(ks, KC_ALPHA2, a, c); });
+}
+
+// e += alpha2 d2.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_kc_update2(int n, const T* __restrict__ d2, T* __restrict__ e,
+                                                    const KcScalars* ks) {
+    const T a = (T)ks->alpha2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) e[i] = fma(a, d2[i], e[i]);
 }
 
 // FP32 copy of the level-0 residual for the FP32 V-cycle: one conversion per
@@ -762,9 +864,183 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     }
 }
 
+// ---- K-cycle (host side) ---------------------------------------------------
+template <typename T>
+T* lvec(Level& Lv, int which) {
+    if (sizeof(T) == 4) {
+        float* v[4] = {Lv.b32, Lv.x32, Lv.r32, Lv.y32};
+        return (T*)v[which];
+    }
+    double* v[4] = {Lv.b, Lv.x, Lv.r, Lv.y};
+    return (T*)v[which];
+}
+
+template <typename T>
+struct LevelOps {
+    Level& Lv;
+    bool f32 = sizeof(T) == 4;
+    explicit LevelOps(Level& L) : Lv(L) {}
+    const T* val() const { return f32 ? (const T*)Lv.S.val32 : (const T*)Lv.S.val; }
+    const T* valm() const { return f32 ? (const T*)Lv.valm32 : (const T*)Lv.valm; }
+    const T* apw() const { return f32 ? (const T*)Lv.AP.val32 : (const T*)Lv.AP.val; }
+    const T* wm() const { return f32 ? (const T*)Lv.wminv32 : (const T*)Lv.wminv; }
+    const T* p() const { return f32 ? (const T*)Lv.p32 : (const T*)Lv.p; }
+    T* kv(int i) const { return (T*)Lv.kv[i]; }
+};
+
+template <typename T>
+void kc_fcg2(amg_hierarchy* h, int m, const T* b, T* e);
+
+// out = B_l in on a level l >= 1 of a K-cycle: pre-smoothing from zero,
+// restriction, coarse correction (two FCG iterations on the first `cycle`
+// coarse levels, the V-cycle below them, the coarsest solve at the bottom),
+// prolongation and post-smoothing; vectors in the cycle's type.
+template <typename T>
+void kc_apply(amg_hierarchy* h, int l, const T* in, T* out) {
+    cudaStream_t st = h->stream;
+    const int L = (int)h->lev.size() - 1;
+    const bool f32 = sizeof(T) == 4;
+    if (l == L) {
+        coarse_solve_launch(h, in, out, f32, !f32);
+        return;
+    }
+    Level& Lv = h->lev[l];
+    Level& Ln = h->lev[l + 1];
+    const LevelOps<T> O(Lv);
+    const SellView S = view(Lv);
+    const SellView SAP{Lv.AP.n, Lv.AP.nslices, Lv.AP.sptr, Lv.AP.col, Lv.AP.perm};
+    const int V = sizeof(T), nc = Ln.A.n;
+    const T omega = (T)h->opt.omega;
+    T* xa = lvec<T>(Lv, 1);
+    T* ra = lvec<T>(Lv, 2);
+    {
+        Scope sc_(&h->prof, st, K_PRE, by_pre(Lv, V, V));
+        launch_pre<T, T>(true, Lv.grid_pre[f32] ? Lv.grid_pre[f32] : sell_grid(h, S.nslices), st, S, O.valm(), O.wm(),
+                         omega, in, xa, ra);
+    }
+    {
+        Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(Lv.A.n, nc, V));
+        k_restrict<T><<<Lv.grid_restrict[f32] ? Lv.grid_restrict[f32] : vec_grid(h, nc), TPB, 0, st>>>(
+            nc, Lv.pt_ptr, Lv.pt_idx, O.p(), ra, lvec<T>(Ln, 0));
+        KERNEL_CHECK();
+    }
+    // coarse correction on level l+1: the coarsest solve, two FCG iterations
+    // (the first `cycle` coarse levels) or the V-cycle from level l+1
+    T* e;
+    if (l + 1 == L) {
+        e = lvec<T>(Ln, 1);
+        coarse_solve_launch(h, lvec<T>(Ln, 0), e, f32, !f32);
+    } else if (l + 1 <= h->opt.cycle) {
+        e = LevelOps<T>(Ln).kv(5);
+        kc_fcg2<T>(h, l + 1, lvec<T>(Ln, 0), e);
+    } else {
+        e = lvec<T>(Ln, 3);
+        kc_apply<T>(h, l + 1, lvec<T>(Ln, 0), e);
+    }
+    Scope sc_(&h->prof, st, K_POST, by_post2(Lv, nc, V, V, false, true));
+    launch_post<T, T, T, false>(true, Lv.grid_post[f32] ? Lv.grid_post[f32] : sell_grid(h, S.nslices), st, SAP, O.apw(),
+                                O.wm(), Lv.agg, O.p(), e, xa, ra, (const T*)nullptr, out, h->red, h->sc, FIN_NONE,
+                                nullptr);
+}
+
+template <typename T>
+void kc_fcg2(amg_hierarchy* h, int m, const T* b, T* e) {
+    cudaStream_t st = h->stream;
+    Level& Lm = h->lev[m];
+    const LevelOps<T> O(Lm);
+    const SellView S = view(Lm);
+    const int n = Lm.A.n, V = sizeof(T);
+    KcScalars* ks = h->ks + m;
+    T *d1 = O.kv(0), *q1 = O.kv(1), *r2 = O.kv(2), *z2 = O.kv(3), *d2 = O.kv(4);
+    const double by_spmv = (double)Lm.A.nnz * (V + 4) + (double)n * 3 * V;
+    kc_apply<T>(h, m, b, d1);
+    {
+        Scope sc_(&h->prof, st, K_KFCG, by_spmv);
+        k_kc_spmv_dot<T><<<red_grid(h), TPB, 0, st>>>(S, O.val(), d1, q1, b, h->red, ks);
+        KERNEL_CHECK();
+    }
+    {
+        Scope sc_(&h->prof, st, K_KFCG, 5.0 * n * V);
+        k_kc_update1<T><<<vec_grid(h, n), TPB, 0, st>>>(n, d1, q1, b, e, r2, ks);
+        KERNEL_CHECK();
+    }
+    kc_apply<T>(h, m, r2, z2);
+    {
+        Scope sc_(&h->prof, st, K_KFCG, 2.0 * n * V);
+        k_kc_dot<T><<<red_grid(h), TPB, 0, st>>>(n, z2, q1, h->red, ks);
+        KERNEL_CHECK();
+    }
+    {
+        Scope sc_(&h->prof, st, K_KFCG, (double)Lm.A.nnz * (V + 4) + (double)n * 5 * V);
+        k_kc_spmv2<T><<<red_grid(h), TPB, 0, st>>>(S, O.val(), z2, q1, d1, r2, d2, h->red, ks);
+        KERNEL_CHECK();
+    }
+    {
+        Scope sc_(&h->prof, st, K_KFCG, 3.0 * n * V);
+        k_kc_update2<T><<<vec_grid(h, n), TPB, 0, st>>>(n, d2, e, ks);
+        KERNEL_CHECK();
+    }
+}
+
+// z = B r with the K-cycle on level 0 (FP64 r and z; with rz_mode the r.z
+// (and q.z) sums of the outer CG are finished as in the V-cycle).
+template <typename T>
+void kcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
+    const int L = (int)h->lev.size() - 1;
+    if (L <= 1) {                          // no intermediate level: the K-cycle is the V-cycle
+        vcycle_typed<T>(h, r, z, rz_mode);
+        return;
+    }
+    cudaStream_t st = h->stream;
+    const bool f32 = sizeof(T) == 4;
+    const double* q2 = rz_mode == FIN_RHO_UPDATE_FCG ? h->q : nullptr;
+    Level& L0 = h->lev[0];
+    Level& L1 = h->lev[1];
+    const LevelOps<T> O(L0);
+    const SellView S = view(L0);
+    const SellView SAP{L0.AP.n, L0.AP.nslices, L0.AP.sptr, L0.AP.col, L0.AP.perm};
+    const int V = sizeof(T), n0 = L0.A.n, nc = L1.A.n;
+    const T omega = (T)h->opt.omega;
+    T* xa = lvec<T>(L0, 1);
+    T* ra = lvec<T>(L0, 2);
+    const int g = L0.grid_pre[f32] ? L0.grid_pre[f32] : sell_grid(h, S.nslices);
+    if (f32) {
+        Scope sc_(&h->prof, st, K_CONVERT, 12.0 * n0);
+        k_to_f32<<<vec_grid(h, n0), TPB, 0, st>>>(n0, r, (float*)lvec<T>(L0, 0));
+        KERNEL_CHECK();
+    }
+    {
+        Scope sc_(&h->prof, st, K_PRE_L0, by_pre(L0, V, f32 ? V : 8));
+        if (f32) launch_pre<T, T>(true, g, st, S, O.valm(), O.wm(), omega, lvec<T>(L0, 0), xa, ra);
+        else launch_pre<T, double>(true, g, st, S, O.valm(), O.wm(), omega, r, xa, ra);
+    }
+    {
+        Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(n0, nc, V));
+        k_restrict<T><<<L0.grid_restrict[f32] ? L0.grid_restrict[f32] : vec_grid(h, nc), TPB, 0, st>>>(
+            nc, L0.pt_ptr, L0.pt_idx, O.p(), ra, lvec<T>(L1, 0));
+        KERNEL_CHECK();
+    }
+    T* e = LevelOps<T>(L1).kv(5);
+    kc_fcg2<T>(h, 1, lvec<T>(L1, 0), e);
+    Scope sc_(&h->prof, st, K_POST_L0, by_post2(L0, nc, V, 8, rz_mode != FIN_NONE, true));
+    const int gp = L0.grid_post[f32] ? L0.grid_post[f32] : sell_grid(h, S.nslices);
+    if (rz_mode != FIN_NONE)
+        launch_post<T, double, double, true>(true, red_grid(h), st, SAP, O.apw(), O.wm(), L0.agg, O.p(), e, xa, ra, r, z,
+                                             h->red, h->sc, rz_mode, q2);
+    else
+        launch_post<T, double, double, false>(true, gp, st, SAP, O.apw(), O.wm(), L0.agg, O.p(), e, xa, ra, r, z,
+                                              h->red, h->sc, FIN_NONE, nullptr);
+}
+
 void vcycle_dispatch(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
-    if (h->opt.precision == AMG_FP32_VCYCLE) vcycle_typed<float>(h, r, z, rz_mode);
-    else vcycle_typed<double>(h, r, z, rz_mode);
+    const bool f32 = h->opt.precision == AMG_FP32_VCYCLE;
+    if (h->opt.cycle > 0) {
+        if (f32) kcycle_typed<float>(h, r, z, rz_mode);
+        else kcycle_typed<double>(h, r, z, rz_mode);
+    } else {
+        if (f32) vcycle_typed<float>(h, r, z, rz_mode);
+        else vcycle_typed<double>(h, r, z, rz_mode);
+    }
 }
 
 // Launch-shape candidates of a grid-stride kernel that needs at most `need`
@@ -907,6 +1183,14 @@ void prepare_solve(amg_hierarchy* h) {
         C.part = h->mem.alloc<double>(4 * (size_t)C.blocks);
         C.ctl = h->mem.alloc<int>(4);
     }
+    if (h->opt.cycle > 0) {
+        // K-cycle: FCG(2) vectors on the levels that take it, scalars per level
+        const size_t V = f32 ? 4 : 8;
+        for (size_t l = 1; l + 1 < h->lev.size() && (int)l <= h->opt.cycle; ++l)
+            for (int i = 0; i < 6; ++i) h->lev[l].kv[i] = h->mem.alloc<char>((size_t)h->lev[l].A.n * V);
+        h->ks = h->mem.alloc<KcScalars>(h->lev.size());
+        CUDA_CHECK(cudaMemsetAsync(h->ks, 0, sizeof(KcScalars) * h->lev.size(), h->stream));
+    }
     const int n0 = h->lev[0].A.n;
     h->r = h->mem.alloc<double>(n0);
     h->z = h->mem.alloc<double>(n0);
@@ -1018,7 +1302,8 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             ++inf.restarts;
             continue;
         }
-        vcycle_dispatch(h, h->r, h->z, h->opt.krylov == 1 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
+        vcycle_dispatch(h, h->r, h->z,
+                        h->opt.krylov == 1 || h->opt.cycle > 0 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
         Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
         k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
         KERNEL_CHECK();

@@ -1,5 +1,6 @@
-"""Oracle K-cycle (two FCG iterations on every intermediate level; the
-paper's cycle for the unsmoothed prolongator, Section 3.3).
+"""Oracle K-cycle (two FCG iterations as the coarse correction on every
+intermediate level, cycle=32: the paper's cycle for the unsmoothed
+prolongator, Section 3.3; cycle=c limits that to coarse levels 1..c).
 
 Pins: with two levels there is no intermediate level, so the K-cycle is the
 V-cycle bit for bit; on a level whose coarse level has two rows, two flexible
@@ -39,7 +40,7 @@ def test_two_levels_k_equals_v():
     A = W.poisson3d(8)
     b = np.random.default_rng(0).normal(size=A.n)
     Hv = oracle.Hierarchy(A)
-    Hk = oracle.Hierarchy(A, cycle=1)
+    Hk = oracle.Hierarchy(A, cycle=32)
     assert Hk.num_levels == 2
     assert np.array_equal(Hv.vcycle(b), Hk.vcycle(b))
 
@@ -48,7 +49,7 @@ def test_two_levels_k_equals_v():
                                        (lambda: W.poisson2d_aniso(4, 2, 1e-2), 1)])
 def test_kcycle_exact_on_two_row_coarse_level(mk, sweeps):
     A = mk()
-    H = oracle.Hierarchy(A, sweeps=sweeps, max_coarse=1, min_ratio=1.0, cycle=1)
+    H = oracle.Hierarchy(A, sweeps=sweeps, max_coarse=1, min_ratio=1.0, cycle=32)
     sizes = [s[0] for s in H.sizes()]
     l = sizes.index(2) - 1          # the level whose coarse level has two rows
     assert l >= 1 and sizes[l + 1] == 2 and len(sizes) > l + 2     # level l+1 is intermediate
@@ -75,11 +76,24 @@ def test_kcycle_needs_fewer_iterations(mk, mc):
     A = mk()
     b = np.random.default_rng(1).normal(size=A.n)
     its = {}
-    for cyc in (0, 1):
+    for cyc in (0, 32):
         H = oracle.Hierarchy(A, cycle=cyc, max_coarse=mc)
         assert H.num_levels >= 3
         x, info = H.pcg(b, rtol=1e-6, flexible=True)
         assert info["status"] == 0
         assert np.linalg.norm(b - A.scipy() @ x) <= 1e-6 * np.linalg.norm(b)
         its[cyc] = info["iterations"]
-    assert its[1] < its[0]
+    assert its[32] < its[0]
+
+
+def test_kcycle_depth_one_uses_vcycle_below():
+    # with the FCG correction on level 1 only, a level-1 cycle is the V-cycle
+    # from level 1 (its coarse correction on level 2 is not FCG), bit for bit
+    A = W.poisson3d(24)
+    H1 = oracle.Hierarchy(A, max_coarse=40, cycle=1)
+    Hv = oracle.Hierarchy(A, max_coarse=40)
+    assert H1.num_levels >= 4
+    r = np.random.default_rng(2).normal(size=H1.sizes()[1][0])
+    assert np.array_equal(H1.vcycle(r, level=1), Hv.vcycle(r, level=1))
+    r0 = np.random.default_rng(3).normal(size=A.n)
+    assert not np.array_equal(H1.vcycle(r0), Hv.vcycle(r0))
