@@ -46,6 +46,8 @@ def lib():
                                     ctypes.c_double, ctypes.c_int, _ip]
             L.orc_coarse_is_cg.argtypes = [ctypes.c_void_p]
             L.orc_set_cycle.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_smooth_vector.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_double,
+                                            _f64p]
             L.orc_setup_seg.restype = ctypes.c_void_p
             L.orc_setup_seg.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -117,6 +119,16 @@ def match_ld(A, w):
     if e:
         raise OracleError(f"orc_match_ld: {e}")
     return m, r.value
+
+
+def smooth_vector(A, w0, sweeps, omega=1.0):
+    """`sweeps` l1-Jacobi iterations on A w = 0 from w0 (Section 3.2)."""
+    rp, cl, vl = _csr_args(A)
+    w0 = np.ascontiguousarray(w0, dtype=np.float64)
+    w = np.empty(A.n)
+    lib().orc_smooth_vector(A.n, _p(rp, _i32p), _p(cl, _i32p), _p(vl, _f64p), _p(w0, _f64p), int(sweeps),
+                            float(omega), _p(w, _f64p))
+    return w
 
 
 class Level:

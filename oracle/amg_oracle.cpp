@@ -435,6 +435,13 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
     return 0;
 }
 
+// ------------------------------------------------------- smooth vector -----
+// An algebraically smooth vector (Section 3.2): `sweeps` iterations of the
+// l1-Jacobi smoother on A w = 0 from the sample vector w0,
+//   w <- w - (omega / M_ii) (A w)_i,
+// each row sum in column order, every operation rounded on its own.
+std::vector<double> smooth_vector(const Csr& A, const double* w0, int sweeps, double omega);
+
 // ------------------------------------------------------------- V-cycle -----
 void spmv(const Csr& A, const double* x, double* y) {
     for (int i = 0; i < A.n; ++i) {
@@ -539,6 +546,16 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     else vcycle(H, l + 1, bc.data(), ec.data());
     for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
     for (int s = 0; s < H.post; ++s) smooth(L, H.omega, b, x);
+}
+
+std::vector<double> smooth_vector(const Csr& A, const double* w0, int sweeps, double omega) {
+    const std::vector<double> minv = l1_jacobi_inverse(A);
+    std::vector<double> w(w0, w0 + A.n), aw(A.n);
+    for (int k = 0; k < sweeps; ++k) {
+        spmv(A, w.data(), aw.data());
+        for (int i = 0; i < A.n; ++i) w[i] = w[i] - (omega * minv[i]) * aw[i];
+    }
+    return w;
 }
 
 double dot(const double* a, const double* b, int n) {
@@ -761,6 +778,15 @@ void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* 
 }
 
 int orc_coarse_is_cg(void* h) { return static_cast<Hierarchy*>(h)->coarse_cg; }
+
+// Smooth vector of A (row_ptr/col/val) from w0: `sweeps` l1-Jacobi iterations on A w = 0.
+int orc_smooth_vector(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w0, int sweeps,
+                      double omega, double* w) {
+    Csr A = make_csr(n, ptr, col, val);
+    std::vector<double> r = smooth_vector(A, w0, sweeps, omega);
+    std::copy(r.begin(), r.end(), w);
+    return 0;
+}
 
 // 0: V-cycle; c > 0: K-cycle on coarse levels 1..c (c >= levels - 2: on every intermediate level).
 void orc_set_cycle(void* h, int kcycle) { static_cast<Hierarchy*>(h)->kcycle = kcycle; }

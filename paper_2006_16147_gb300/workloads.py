@@ -22,6 +22,7 @@ __all__ = [
     "Csr",
     "poisson3d",
     "poisson2d_aniso",
+    "aniso3d",
     "varcoef3d",
     "csr_matvec",
     "rhs_ones",
@@ -121,6 +122,18 @@ def poisson2d_aniso(nx: int, ny: int | None = None, eps: float = 1e-2) -> Csr:
     cz = np.zeros((2, ny, nx))
     A = _assemble_faces(cx, cy, cz, f"aniso2d_{nx}x{ny}_eps{eps:g}")
     return A
+
+
+def aniso3d(nx: int, ny: int | None = None, nz: int | None = None, k=(100.0, 100.0, 1.0)) -> Csr:
+    """7-point discretisation of -(k1 u_xx + k2 u_yy + k3 u_zz) (the supplementary
+    anisotropic Poisson problem; k = (100, 100, 1) as in its experiments,
+    (1, 1, 100) for z-aligned anisotropy)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    cx = np.full((nz, ny, nx + 1), float(k[0]))
+    cy = np.full((nz, ny + 1, nx), float(k[1]))
+    cz = np.full((nz + 1, ny, nx), float(k[2]))
+    return _assemble_faces(cx, cy, cz, f"aniso3d_{nx}x{ny}x{nz}_k{k[0]:g}-{k[1]:g}-{k[2]:g}")
 
 
 def varcoef3d(nx: int, seed: int, sigma: float = 2.0) -> Csr:
