@@ -40,8 +40,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=256)
-    ap.add_argument("--workload", default="poisson", choices=["poisson", "varcoef"],
-                    help="poisson: 7-point Laplacian (default line); varcoef: jump coefficients exp(g), sigma 2")
+    ap.add_argument("--workload", default="poisson", choices=["poisson", "varcoef", "aniso3d"],
+                    help="poisson: 7-point Laplacian (default line); varcoef: jump coefficients exp(g), sigma 2; "
+                         "aniso3d: -(100 u_xx + 100 u_yy + u_zz)")
+    ap.add_argument("--smooth-w", type=int, default=0,
+                    help="> 0: w = that many l1-Jacobi sweeps on A w = 0 from ones (amg_smooth_vector, inside the step)")
     ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
     ap.add_argument("--cycle", default="v", choices=["v", "k"],
                     help="v: V-cycle (default line); k: K-cycle, two FCG iterations as the coarse correction")
@@ -176,20 +179,32 @@ def _workload(grid, kind="poisson"):
     if kind == "varcoef":
         A = W.varcoef3d(grid, seed=2)
         b, _ = W.rhs_uniform(A, 3)
+    elif kind == "aniso3d":
+        A = W.aniso3d(grid, k=(100.0, 100.0, 1.0))
+        b, _ = W.rhs_uniform(A, 1)
     else:
         A = W.poisson3d(grid)
         b, _ = W.rhs_uniform(A, 1)
     return A, b
 
 
-def _oracle_sample(grid, rtol, kind="poisson", flexible=False):
+def _workload_name(args):
+    base = {"poisson": f"poisson3d_{args.grid}^3_7pt_fp64",
+            "varcoef": f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle",
+            "aniso3d": f"aniso3d_{args.grid}^3_k100-100-1_{args.precision}vcycle"}[args.workload]
+    return (base + "_setup+solve" + (f"_kcycle{args.kdepth}" if args.cycle == "k" else "") +
+            (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
+
+
+def _oracle_sample(grid, rtol, kind="poisson", flexible=False, cycle=0, smooth_w=0):
     """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance of the workload."""
     import oracle
     A, b = _workload(grid, kind)
     t0 = time.perf_counter()
-    H = oracle.Hierarchy(A)
+    w = oracle.smooth_vector(A, np.ones(A.n), smooth_w) if smooth_w > 0 else None
+    H = oracle.Hierarchy(A, w, cycle=cycle)
     t1 = time.perf_counter()
-    x, info = H.pcg(b, rtol=rtol, flexible=flexible)
+    x, info = H.pcg(b, rtol=rtol, flexible=flexible or cycle > 0)
     t2 = time.perf_counter()
     return dict(setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"], n=A.n)
 
@@ -204,7 +219,8 @@ def reference_arm(args):
     n_full = args.grid ** 3
     times = []
     for k in range(args.warmup + args.steps):
-        r = _oracle_sample(grid, args.rtol, args.workload, args.krylov == 1)
+        r = _oracle_sample(grid, args.rtol, args.workload, args.krylov == 1,
+                           args.kdepth if args.cycle == "k" else 0, args.smooth_w)
         if k >= args.warmup:
             times.append((r["setup_s"] + r["solve_s"]) * 1e3 * n_full / r["n"])
     v = statistics.mean(times)
@@ -213,10 +229,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": (f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve" if args.workload == "poisson" else
-                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve"),
-                       "grid": args.grid,
-                       "rtol": args.rtol},
+            "config": {"workload": _workload_name(args), "grid": args.grid, "rtol": args.rtol},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -663,7 +676,9 @@ def main():
 
     def step(profile=0, keep=False):
         d_x.zero_()
-        h = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, profile=profile, krylov=args.krylov,
+        w = (amg.amg_smooth_vector(d_ptr, d_col, d_val, d_w, args.smooth_w, stream=stream.cuda_stream)
+             if args.smooth_w > 0 else d_w)
+        h = amg.amg_setup(d_ptr, d_col, d_val, w, precision=prec, profile=profile, krylov=args.krylov,
                           autotune=args.autotune, cycle=args.kdepth if args.cycle == "k" else 0, stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
@@ -777,7 +792,8 @@ def main():
         import oracle
         oracle.build()
         g = min(args.cpu_sample_grid if args.workload == "poisson" else 48, args.grid)
-        r = _oracle_sample(g, args.rtol, args.workload, args.krylov == 1)
+        r = _oracle_sample(g, args.rtol, args.workload, args.krylov == 1, args.kdepth if args.cycle == "k" else 0,
+                           args.smooth_w)
         scale = A.n / r["n"]
         cpu = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": (f"oracle setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s ({r['iterations']} it) "
@@ -791,9 +807,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64-cg/f32-vcycle",
             "data": "synthetic",
-            "config": {"workload": (f"poisson3d_{args.grid}^3_7pt_fp64_setup+solve" if args.workload == "poisson" else
-                                    f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle_setup+solve") +
-                                   (f"_kcycle{args.kdepth}" if args.cycle == "k" else ""),
+            "config": {"workload": _workload_name(args),
                        "grid": args.grid, "cycle": args.cycle, "kdepth": args.kdepth if args.cycle == "k" else None,
                        "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
                        "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",

@@ -229,6 +229,18 @@ amg_status amg_kernel_stats_reset(amg_hierarchy* h);
 int64_t amg_launch_count(void);
 
 /*
+ * Algebraically smooth vector for amg_setup (Section 3.2: a few iterations of
+ * an A-convergent smoother on a sample vector). Writes to w (DEVICE, length
+ * n) the result of `sweeps` l1-Jacobi iterations on A w = 0 from the sample
+ * w0 (DEVICE, length n, no zero entries): w <- w - omega M^{-1} A w with
+ * M_ii = a_ii + sum_{j != i} |a_ij|. A as for amg_setup; `stream` is a
+ * cudaStream_t (NULL = legacy default); returns after the stream work has
+ * finished. w may equal w0 for an even number of sweeps. Errors as amg_setup
+ * (validation codes on A and w0), AMG_ERR_ARG for sweeps < 0 or omega <= 0.
+ */
+amg_status amg_smooth_vector(const amg_csr* A, const double* w0, double* w, int sweeps, double omega, void* stream);
+
+/*
  * Matching without allocation. The paper has no counterpart: this is a
  * service for callers that may not allocate device memory when they need a
  * matching -- code that runs while a stream is being captured into a CUDA

@@ -37,6 +37,7 @@ EXPORTED = [
     "amg_launch_count", "amg_match_noalloc", "amg_solve_batch", "amg_serve_create", "amg_serve_submit",
     "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free", "amg_setup_many",
     "amg_solve_many", "amg_system_offsets", "amg_tune_save", "amg_tune_load", "amg_tune_clear", "amg_tune_size",
+    "amg_smooth_vector",
 ]
 KCYCLE_FULL = 32
 NOALLOC_MAX_N = 65536
@@ -161,6 +162,8 @@ def lib() -> ctypes.CDLL:
         for name in ("amg_tune_save", "amg_tune_load"):
             getattr(L, name).argtypes = [ctypes.c_char_p]
             getattr(L, name).restype = ctypes.c_int
+        L.amg_smooth_vector.argtypes = [ctypes.POINTER(amg_csr), _vp, _vp, ctypes.c_int, ctypes.c_double, _vp]
+        L.amg_smooth_vector.restype = ctypes.c_int
         L.amg_tune_clear.argtypes = []
         L.amg_tune_clear.restype = None
         L.amg_tune_size.argtypes = []
@@ -363,6 +366,16 @@ def amg_kernel_stats(h: Hierarchy) -> dict:
 
 def amg_kernel_stats_reset(h: Hierarchy) -> None:
     _check(lib().amg_kernel_stats_reset(h.handle))
+
+
+def amg_smooth_vector(row_ptr, col, val, w0, sweeps: int, omega: float = 1.0, stream=None):
+    """Smooth vector for amg_setup: `sweeps` l1-Jacobi iterations on A w = 0 from w0 (device tensors)."""
+    import torch
+    A = amg_csr(int(row_ptr.shape[0] - 1), int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val))
+    w = torch.empty_like(w0)
+    st = stream if stream is not None else _current_stream()
+    _check(lib().amg_smooth_vector(ctypes.byref(A), _ptr(w0), _ptr(w), int(sweeps), float(omega), st))
+    return w
 
 
 def amg_tune_save(path: str) -> None:

@@ -336,5 +336,6 @@ bool block_check_launch(amg_hierarchy* h, const double* B, double* X, int k);
 void block_scatter_request(amg_hierarchy* h, const double* src, int k, const int* slots, double* dst);
 void block_gather_column(amg_hierarchy* h, const double* src, int slot, double* dst, int k, int j);
 amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds_out);
+void smooth_vector(const amg_csr* A, const double* w0, double* w, int sweeps, double omega, cudaStream_t st);
 
 }  // namespace amg

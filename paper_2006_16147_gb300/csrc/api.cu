@@ -396,6 +396,19 @@ void amg_serve_free(amg_server* s) {
     if (s) amg::serve_free(s);
 }
 
+amg_status amg_smooth_vector(const amg_csr* A, const double* w0, double* w, int sweeps, double omega, void* stream) {
+    if (!w) return fail(AMG_ERR_ARG, "w is null");
+    if (sweeps < 0 || !(omega > 0.0)) return fail(AMG_ERR_ARG, "sweeps must be >= 0 and omega > 0");
+    amg_status s = check_csr(A, w0);
+    if (s != AMG_OK) return s;
+    if (w0 == w && sweeps % 2 == 1)
+        return fail(AMG_ERR_ARG, "w0 and w must differ for an odd number of sweeps");
+    return guarded([&]() -> amg_status {
+        amg::smooth_vector(A, w0, w, sweeps, omega, static_cast<cudaStream_t>(stream));
+        return AMG_OK;
+    });
+}
+
 amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void* stream, int32_t* rounds) {
     if (!mate) return fail(AMG_ERR_ARG, "mate is null");
     amg_status s = check_csr(A, w);

@@ -1737,6 +1737,59 @@ __global__ void k_cat_col(long long nnz, const int* __restrict__ src, int col_of
 
 // Block-diagonal union of m systems (device arrays), set up as one hierarchy
 // that keeps every system's row offsets.
+// ---------------------------------------------- smooth vector (Section 3.2) --
+// One l1-Jacobi sweep on A w = 0: w_i - (omega / M_ii) (A w)_i, the row sum in
+// column order and every operation rounded on its own (the oracle's order).
+__global__ void k_smooth_sweep(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                               const double* __restrict__ val, const double* __restrict__ minv, double omega,
+                               const double* __restrict__ w, double* __restrict__ wout) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) s = __dadd_rn(s, __dmul_rn(val[k], w[col[k]]));
+        wout[i] = __dsub_rn(w[i], __dmul_rn(__dmul_rn(omega, minv[i]), s));
+    }
+}
+
+void smooth_vector(const amg_csr* A, const double* w0, double* w, int sweeps, double omega, cudaStream_t st) {
+    const int n = A->n;
+    int dev = 0, sms = 0;
+    CUDA_CHECK(cudaGetDevice(&dev));
+    CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DevArena tmp;
+    tmp.stream = st;
+    double* minv = tmp.alloc<double>(n);
+    double* other = tmp.alloc<double>(n);
+    int* flags = tmp.alloc<int>(1);
+    const int grid = blocks_for(n, TPB, sms * 8);
+    // the same checks as amg_setup: CSR shape, SPD diagonal, usable sample vector
+    CUDA_CHECK(cudaMemsetAsync(flags, 0, sizeof(int), st));
+    k_check_ptr<<<blocks_for(n + 1, TPB, sms * 8), TPB, 0, st>>>(n, A->nnz, A->row_ptr, flags);
+    KERNEL_CHECK();
+    int f = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&f, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "row_ptr is not a valid CSR row pointer");
+    k_check_rows<<<grid, TPB, 0, st>>>(n, A->row_ptr, A->col, A->val, w0, minv, flags);
+    KERNEL_CHECK();
+    CUDA_CHECK(cudaMemcpyAsync(&f, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "CSR columns unsorted, out of range, or pattern not symmetric");
+    if (f & F_NOT_SPD) AMG_THROW(AMG_ERR_NOT_SPD, "non-finite value or diagonal entry missing or <= 0");
+    if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "sample vector w0 has a zero or non-finite entry");
+    k_l1_jacobi<<<grid, TPB, 0, st>>>(n, A->row_ptr, A->col, A->val, minv, nullptr);
+    KERNEL_CHECK();
+    // ping-pong between w and the scratch vector so that the last sweep lands in w
+    double* cur = (sweeps % 2 == 0) ? w : other;
+    double* nxt = (sweeps % 2 == 0) ? other : w;
+    if (cur != w0) CUDA_CHECK(cudaMemcpyAsync(cur, w0, sizeof(double) * n, cudaMemcpyDefault, st));
+    for (int k = 0; k < sweeps; ++k) {
+        k_smooth_sweep<<<grid, TPB, 0, st>>>(n, A->row_ptr, A->col, A->val, minv, omega, cur, nxt);
+        KERNEL_CHECK();
+        std::swap(cur, nxt);
+    }
+    CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
 void setup_many(amg_hierarchy* h, int m, const amg_csr* As, const double* const* ws) {
     cudaStream_t st = h->stream;
     long long n = 0, nnz = 0;
