@@ -61,9 +61,10 @@ __device__ __forceinline__ Grp make_grp(int G) {
 }
 
 // acc[m] += sum_e val_e * xv(col_e, c) for the row at SELL position ip, in
-// entry order. Four entries at a time: their indices and values are loaded
-// first and the four gathered rows of X are in flight together, so a row
-// costs about two memory latencies per four entries instead of two per entry.
+// entry order. Four entries at a time (the last group predicated): their
+// indices and values are loaded first and the four gathered rows of X are in
+// flight together, so a row costs about two memory latencies per four
+// entries instead of two per entry.
 template <typename T, int CPL, typename XV>
 __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__ val, int ip, const Grp& g, int k,
                                            XV&& xv, T (&acc)[CPL]) {
@@ -92,13 +93,26 @@ __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__
             }
         }
     }
-    for (; e < w; ++e, base += 32) {
-        const int j = __ldg(S.col + base);
-        const T a = __ldg(val + base);
+    if (e < w) {                      // the last 1-3 entries as one predicated group of four
+        int j[4];
+        T a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = e + u < w;
+            j[u] = ok ? __ldg(S.col + base + 32 * u) : 0;
+            a[u] = ok ? __ldg(val + base + 32 * u) : T(0);
+        }
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
             const int c = g.gl + m * g.G;
-            if (c < k) acc[m] = fma(a, xv(j, c), acc[m]);
+            if (c < k) {
+                T xs[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xs[u] = e + u < w ? xv(j[u], c) : T(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (e + u < w) acc[m] = fma(a[u], xs[u], acc[m]);
+            }
         }
     }
 }
