@@ -51,7 +51,11 @@ def lib():
             L.orc_setup_seg.restype = ctypes.c_void_p
             L.orc_setup_seg.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, _ip]
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int, _ip]
+            L.orc_level_pbar_nnz.restype = ctypes.c_int64
+            L.orc_level_pbar_nnz.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_level_pbar.restype = ctypes.c_double
+            L.orc_level_pbar.argtypes = [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _f64p]
             for name in ("orc_free",):
                 getattr(L, name).argtypes = [ctypes.c_void_p]
             L.orc_num_levels.argtypes = [ctypes.c_void_p]
@@ -139,7 +143,7 @@ class Hierarchy:
     """Oracle hierarchy: setup in the constructor, then V-cycle and PCG."""
 
     def __init__(self, A, w=None, sweeps=3, max_coarse=200, max_levels=32, pre=1, post=1, omega=1.0,
-                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None, cycle=0):
+                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None, cycle=0, smooth_p=False):
         rp, cl, vl = _csr_args(A)
         w = np.ones(A.n) if w is None else np.ascontiguousarray(w, dtype=np.float64)
         st = ctypes.c_int(0)
@@ -147,7 +151,7 @@ class Hierarchy:
         self._h = lib().orc_setup_seg(A.n, _p(rp, _i32p), _p(cl, _i32p), _p(vl, _f64p), _p(w, _f64p), sweeps,
                                       max_coarse, max_levels, pre, post, float(omega), int(use_ld), float(min_ratio),
                                       int(max_dense), 0 if seg is None else len(sg) - 1, _p(sg, _i32p),
-                                      ctypes.byref(st))
+                                      int(smooth_p), ctypes.byref(st))
         if not self._h:
             raise OracleError(f"orc_setup failed: {st.value}")
         lib().orc_set_cycle(self._h, int(cycle))
@@ -195,6 +199,17 @@ class Hierarchy:
             lv.sweeps.append(dict(n=ns.value, nc=nc.value, nnz_c=nnzc.value, rounds=rounds.value, mate=mate,
                                   agg=agg, p=p, wc=wc))
         return lv
+
+    def pbar(self, l: int):
+        """Smoothed prolongator of level l as (Csr, omega) (hierarchies built with smooth_p)."""
+        from paper_2006_16147_gb300.workloads import Csr
+        n = self.sizes()[l][0]
+        nnz = lib().orc_level_pbar_nnz(self._h, l)
+        rp = np.empty(n + 1, dtype=np.int32)
+        cl = np.empty(nnz, dtype=np.int32)
+        vl = np.empty(nnz)
+        om = lib().orc_level_pbar(self._h, l, _p(rp, _i32p), _p(cl, _i32p), _p(vl, _f64p))
+        return Csr(rp, cl, vl), om
 
     def level_csr(self, l: int):
         from paper_2006_16147_gb300.workloads import Csr

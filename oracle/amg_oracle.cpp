@@ -272,6 +272,10 @@ struct Level {
     std::vector<double> p;
     std::vector<Pairwise> sweeps;
     std::vector<int64_t> sweep_nnz;   // nnz of the coarse matrix after each sweep
+    // smoothed prolongator (n x nc CSR, ascending columns) and its transpose
+    // (nc x n, ascending rows), present when the hierarchy smooths P
+    Csr pbar, pbar_t;
+    double omega_p = 0.0;             // the prolongator smoothing weight of this level
 };
 
 struct Hierarchy {
@@ -284,10 +288,125 @@ struct Hierarchy {
     std::vector<int> cseg;
     std::vector<std::vector<double>> Lb;
     int pre = 1, post = 1;
-    int kcycle = 0;                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
+    int kcycle = 0;
+    int smooth_p = 0;              // 1: smoothed prolongator Pbar = (I - omega D^-1 A) P (Section 3.3)                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
     double omega = 1.0;
     int use_ld = 0;
 };
+
+// ------------------------------- smoothed prolongator (Section 3.3) -------
+// Pbar = (I - omega D^-1 A) P with D = diag(A). The paper's text takes
+// omega = 1 / ||D^-1 A||_inf; its table of two-level constants for the
+// smoothed prolongator is reproduced with 4/3 of that (2/3 on the Laplacian),
+// the reading taken here: omega = 4 / (3 eta), eta = max_i sum_j |a_ij| / a_ii
+// (each row's sum in column order, one division per row).
+double smoothing_weight(const Csr& A) {
+    double eta = 0.0;
+    for (int i = 0; i < A.n; ++i) {
+        double s = 0.0, d = 0.0;
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            s = s + std::fabs(A.val[k]);
+            if (A.col[k] == i) d = A.val[k];
+        }
+        eta = std::max(eta, s / d);
+    }
+    return 4.0 / (3.0 * eta);
+}
+
+// Row i of A P (P: one nonzero p_j in column agg_j per row): the terms
+// a_ij p_j in column order, summed per coarse column from the first term,
+// columns ascending. Row i of Pbar is then p_i - t_i (A P)_iq in column
+// agg_i and -(t_i (A P)_iq) elsewhere, t_i = omega / a_ii.
+Csr smoothed_prolongator(const Csr& A, const std::vector<int32_t>& agg, const std::vector<double>& p, int nc,
+                         double omega) {
+    Csr Pb;
+    Pb.n = A.n;
+    Pb.ptr.assign(A.n + 1, 0);
+    std::vector<double> acc(nc, 0.0);
+    std::vector<char> seen(nc, 0);
+    std::vector<int> touched;
+    for (int i = 0; i < A.n; ++i) {
+        touched.clear();
+        double d = 0.0;
+        for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            const int j = A.col[k];
+            if (j == i) d = A.val[k];
+            const int q = agg[j];
+            const double t = A.val[k] * p[j];
+            if (!seen[q]) { seen[q] = 1; acc[q] = t; touched.push_back(q); }
+            else acc[q] = acc[q] + t;
+        }
+        const double ti = omega / d;
+        std::sort(touched.begin(), touched.end());
+        for (int q : touched) {
+            const double u = ti * acc[q];
+            Pb.col.push_back(q);
+            Pb.val.push_back(q == agg[i] ? p[i] - u : -u);
+            seen[q] = 0;
+        }
+        Pb.ptr[i + 1] = (int32_t)Pb.col.size();
+    }
+    return Pb;
+}
+
+// Transpose with ascending rows in every column (counting sort by column).
+Csr transpose_csr(const Csr& P, int nc) {
+    Csr T;
+    T.n = nc;
+    T.ptr.assign(nc + 1, 0);
+    for (int32_t c : P.col) T.ptr[c + 1] += 1;
+    for (int q = 0; q < nc; ++q) T.ptr[q + 1] += T.ptr[q];
+    T.col.resize(P.col.size());
+    T.val.resize(P.val.size());
+    std::vector<int32_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+    for (int i = 0; i < P.n; ++i)
+        for (int64_t k = P.ptr[i]; k < P.ptr[i + 1]; ++k) {
+            const int32_t at = pos[P.col[k]]++;
+            T.col[at] = i;
+            T.val[at] = P.val[k];
+        }
+    return T;
+}
+
+// Galerkin product Pbar^T A Pbar, coarse row by coarse row: for every fine
+// row i of column p of Pbar (ascending), every entry a_ij of row i (column
+// order) and every entry v of row j of Pbar (ascending column q), the term
+// (Pbar_ip a_ij) v is added to the running sum of column q from left to
+// right, the first term starting the sum. Columns ascending.
+Csr galerkin_general(const Csr& A, const Csr& Pb, const Csr& PbT) {
+    const int nc = PbT.n;
+    Csr C;
+    C.n = nc;
+    C.ptr.assign(nc + 1, 0);
+    std::vector<double> acc(nc, 0.0);
+    std::vector<char> seen(nc, 0);
+    std::vector<int> touched;
+    for (int p = 0; p < nc; ++p) {
+        touched.clear();
+        for (int64_t e = PbT.ptr[p]; e < PbT.ptr[p + 1]; ++e) {
+            const int i = PbT.col[e];
+            const double pip = PbT.val[e];
+            for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                const int j = A.col[k];
+                const double t = pip * A.val[k];
+                for (int64_t f = Pb.ptr[j]; f < Pb.ptr[j + 1]; ++f) {
+                    const int q = Pb.col[f];
+                    const double term = t * Pb.val[f];
+                    if (!seen[q]) { seen[q] = 1; acc[q] = term; touched.push_back(q); }
+                    else acc[q] = acc[q] + term;
+                }
+            }
+        }
+        std::sort(touched.begin(), touched.end());
+        for (int q : touched) {
+            C.col.push_back(q);
+            C.val.push_back(acc[q]);
+            seen[q] = 0;
+        }
+        C.ptr[p + 1] = (int32_t)C.col.size();
+    }
+    return C;
+}
 
 // l1-Jacobi (Eq. 5-6 with blocks of size one): M_ii = a_ii + sum_{j != i} |a_ij|.
 std::vector<double> l1_jacobi_inverse(const Csr& A) {
@@ -395,6 +514,15 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
             cur.sweeps.push_back(std::move(pw));
         }
         if (A.n == cur.A.n) break;                  // no reduction: this level is the coarsest
+        if (H.smooth_p) {
+            // smoothed prolongator of the level's aggregates; the next level
+            // matrix is Pbar^T A Pbar (the smooth vector stays the tentative one)
+            const int ncl = A.n;
+            cur.omega_p = smoothing_weight(cur.A);
+            cur.pbar = smoothed_prolongator(cur.A, agg, p, ncl, cur.omega_p);
+            cur.pbar_t = transpose_csr(cur.pbar, ncl);
+            A = galerkin_general(cur.A, cur.pbar, cur.pbar_t);
+        }
         cur.agg = std::move(agg);
         cur.p = std::move(p);
         Level next;
@@ -541,10 +669,28 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
     const int nc = H.lev[l + 1].A.n;
     std::vector<double> bc(nc, 0.0), ec(nc);
-    for (int i = 0; i < n; ++i) bc[L.agg[i]] = bc[L.agg[i]] + L.p[i] * r[i];     // P^T r, members ascending
+    if (H.smooth_p) {                                                             // Pbar^T r, rows ascending
+        for (int q = 0; q < nc; ++q) {
+            double s = 0.0;
+            for (int64_t e = L.pbar_t.ptr[q]; e < L.pbar_t.ptr[q + 1]; ++e)
+                s = e == L.pbar_t.ptr[q] ? L.pbar_t.val[e] * r[L.pbar_t.col[e]] : s + L.pbar_t.val[e] * r[L.pbar_t.col[e]];
+            bc[q] = s;
+        }
+    } else {
+        for (int i = 0; i < n; ++i) bc[L.agg[i]] = bc[L.agg[i]] + L.p[i] * r[i];     // P^T r, members ascending
+    }
     if (H.kcycle > l && l + 2 < (int)H.lev.size()) fcg2(H, l + 1, bc.data(), ec.data());
     else vcycle(H, l + 1, bc.data(), ec.data());
-    for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
+    if (H.smooth_p) {                                                             // x + Pbar e
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int64_t f = L.pbar.ptr[i]; f < L.pbar.ptr[i + 1]; ++f)
+                s = f == L.pbar.ptr[i] ? L.pbar.val[f] * ec[L.pbar.col[f]] : s + L.pbar.val[f] * ec[L.pbar.col[f]];
+            x[i] = x[i] + s;
+        }
+    } else {
+        for (int i = 0; i < n; ++i) x[i] = x[i] + L.p[i] * ec[L.agg[i]];           // x + P e
+    }
     for (int s = 0; s < H.post; ++s) smooth(L, H.omega, b, x);
 }
 
@@ -697,27 +843,27 @@ int orc_match_ld(int n, const int32_t* ptr, const int32_t* col, const double* va
 // null; *status receives 0 or a negative code.
 void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                     int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
-                    int max_dense, int nseg, const int32_t* seg, int* status);
+                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int* status);
 
 void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                 int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
                 int max_dense, int* status) {
     return orc_setup_seg(n, ptr, col, val, w, sweeps, max_coarse, max_levels, pre, post, omega, use_ld, min_ratio,
-                         max_dense, 0, nullptr, status);
+                         max_dense, 0, nullptr, 0, status);
 }
 
 // As orc_setup for the block-diagonal union of nseg systems with row offsets
 // seg[0..nseg] (the largest system decides when coarsening stops).
 void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                     int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
-                    int max_dense, int nseg, const int32_t* seg, int* status) {
+                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int* status) {
     Csr A = make_csr(n, ptr, col, val);
     int e = validate(A);
     for (int i = 0; e == 0 && i < n; ++i)
         if (!std::isfinite(w[i]) || w[i] == 0.0) e = -3;
     if (e) { *status = e; return nullptr; }
     Hierarchy* H = new Hierarchy;
-    H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld;
+    H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld; H->smooth_p = smooth_p;
     std::vector<int> sv;
     if (nseg > 0) sv.assign(seg, seg + nseg + 1);
     e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels, min_ratio, max_dense,
@@ -778,6 +924,16 @@ void orc_sweep_data(void* h, int l, int s, int32_t* mate, int32_t* agg, double* 
 }
 
 int orc_coarse_is_cg(void* h) { return static_cast<Hierarchy*>(h)->coarse_cg; }
+
+// Smoothed prolongator of level l (requires smooth_p): nnz, then the CSR arrays and omega.
+int64_t orc_level_pbar_nnz(void* h, int l) { return static_cast<Hierarchy*>(h)->lev[l].pbar.nnz(); }
+double orc_level_pbar(void* h, int l, int32_t* ptr, int32_t* col, double* val) {
+    const Level& L = static_cast<Hierarchy*>(h)->lev[l];
+    std::copy(L.pbar.ptr.begin(), L.pbar.ptr.end(), ptr);
+    std::copy(L.pbar.col.begin(), L.pbar.col.end(), col);
+    std::copy(L.pbar.val.begin(), L.pbar.val.end(), val);
+    return L.omega_p;
+}
 
 // Smooth vector of A (row_ptr/col/val) from w0: `sweeps` l1-Jacobi iterations on A w = 0.
 int orc_smooth_vector(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w0, int sweeps,
