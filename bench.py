@@ -43,6 +43,8 @@ def _args():
     ap.add_argument("--workload", default="poisson", choices=["poisson", "varcoef", "aniso3d"],
                     help="poisson: 7-point Laplacian (default line); varcoef: jump coefficients exp(g), sigma 2; "
                          "aniso3d: -(100 u_xx + 100 u_yy + u_zz)")
+    ap.add_argument("--smooth-p", type=int, default=0, choices=[0, 1],
+                    help="1: smoothed prolongator Pbar = (I - omega D^-1 A) P (the paper's VA3 setting)")
     ap.add_argument("--smooth-w", type=int, default=0,
                     help="> 0: w = that many l1-Jacobi sweeps on A w = 0 from ones (amg_smooth_vector, inside the step)")
     ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
@@ -193,16 +195,16 @@ def _workload_name(args):
             "varcoef": f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle",
             "aniso3d": f"aniso3d_{args.grid}^3_k100-100-1_{args.precision}vcycle"}[args.workload]
     return (base + "_setup+solve" + (f"_kcycle{args.kdepth}" if args.cycle == "k" else "") +
-            (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
+            ("_smoothedP" if args.smooth_p else "") + (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
 
 
-def _oracle_sample(grid, rtol, kind="poisson", flexible=False, cycle=0, smooth_w=0):
+def _oracle_sample(grid, rtol, kind="poisson", flexible=False, cycle=0, smooth_w=0, smooth_p=False):
     """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance of the workload."""
     import oracle
     A, b = _workload(grid, kind)
     t0 = time.perf_counter()
     w = oracle.smooth_vector(A, np.ones(A.n), smooth_w) if smooth_w > 0 else None
-    H = oracle.Hierarchy(A, w, cycle=cycle)
+    H = oracle.Hierarchy(A, w, cycle=cycle, smooth_p=smooth_p)
     t1 = time.perf_counter()
     x, info = H.pcg(b, rtol=rtol, flexible=flexible or cycle > 0)
     t2 = time.perf_counter()
@@ -220,7 +222,7 @@ def reference_arm(args):
     times = []
     for k in range(args.warmup + args.steps):
         r = _oracle_sample(grid, args.rtol, args.workload, args.krylov == 1,
-                           args.kdepth if args.cycle == "k" else 0, args.smooth_w)
+                           args.kdepth if args.cycle == "k" else 0, args.smooth_w, bool(args.smooth_p))
         if k >= args.warmup:
             times.append((r["setup_s"] + r["solve_s"]) * 1e3 * n_full / r["n"])
     v = statistics.mean(times)
@@ -679,7 +681,8 @@ def main():
         w = (amg.amg_smooth_vector(d_ptr, d_col, d_val, d_w, args.smooth_w, stream=stream.cuda_stream)
              if args.smooth_w > 0 else d_w)
         h = amg.amg_setup(d_ptr, d_col, d_val, w, precision=prec, profile=profile, krylov=args.krylov,
-                          autotune=args.autotune, cycle=args.kdepth if args.cycle == "k" else 0, stream=stream.cuda_stream)
+                          autotune=args.autotune, cycle=args.kdepth if args.cycle == "k" else 0,
+                          smooth_p=args.smooth_p, stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
             return h, info
@@ -730,7 +733,7 @@ def main():
     # ---- accuracy of a mixed-precision or non-default run: error against an
     # FP64 solve of the same system to rel-res 1e-10, and iterations at 1e-8
     accuracy = None
-    if args.precision == "fp32" or args.workload != "poisson" or args.cycle == "k":
+    if args.precision == "fp32" or args.workload != "poisson" or args.cycle == "k" or args.smooth_p:
         accuracy = {}
         h64 = amg.amg_setup(d_ptr, d_col, d_val, d_w, stream=stream.cuda_stream)
         xr = torch.zeros_like(d_x)
@@ -738,7 +741,8 @@ def main():
         h64.close()
         for tol in (args.rtol, 1e-8):
             hh = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov,
-                               cycle=args.kdepth if args.cycle == "k" else 0, stream=stream.cuda_stream)
+                               cycle=args.kdepth if args.cycle == "k" else 0, smooth_p=args.smooth_p,
+                               stream=stream.cuda_stream)
             xt = torch.zeros_like(d_x)
             inf = amg.amg_solve(hh, d_b, xt, rtol=tol, maxit=2000)
             hh.close()
@@ -771,14 +775,14 @@ def main():
         e2e_steps = max(1, min(3, args.steps))
         kc = args.kdepth if args.cycle == "k" else 0
         amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
-                                   cycle=kc)
+                                   cycle=kc, smooth_p=args.smooth_p)
         amg_h.close()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             xh[:] = 0.0
             hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
-                                    cycle=kc)
+                                    cycle=kc, smooth_p=args.smooth_p)
             amg.amg_solve_host(hh, hp["b"], xh, rtol=args.rtol, maxit=1000)
             hh.close()
         barrier()
@@ -793,7 +797,7 @@ def main():
         oracle.build()
         g = min(args.cpu_sample_grid if args.workload == "poisson" else 48, args.grid)
         r = _oracle_sample(g, args.rtol, args.workload, args.krylov == 1, args.kdepth if args.cycle == "k" else 0,
-                           args.smooth_w)
+                           args.smooth_w, bool(args.smooth_p))
         scale = A.n / r["n"]
         cpu = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": (f"oracle setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s ({r['iterations']} it) "

@@ -91,6 +91,10 @@ typedef struct {
                           (Section 3.3, the cycle it uses with this unsmoothed aggregation). The
                           preconditioner is then not linear, so the outer solver is flexible CG whatever
                           `krylov` says. Requires pre = post = 1; single right-hand-side solves only */
+    int smooth_p;      /* [0] 1: smoothed prolongator Pbar = (I - omega D^-1 A) P on every level, omega =
+                          4 / (3 ||D^-1 A||_inf), coarse matrices Pbar^T A Pbar (Section 3.3; the paper's VA3
+                          setting, with the weight that reproduces its smoothed-aggregation constants). V-cycle
+                          (cycle = 0), pre = post = 1, single right-hand-side solves only */
     int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */
@@ -198,6 +202,17 @@ amg_status amg_hierarchy_info(const amg_hierarchy* h, amg_hier_info* out);
  */
 amg_status amg_export_level(const amg_hierarchy* h, int level, int32_t* row_ptr, int32_t* col, double* val,
                             double* w, double* minv, int32_t* agg, double* p);
+
+/*
+ * Smoothed prolongator of level `level` (hierarchies built with smooth_p):
+ * amg_pbar_nnz gives its number of stored entries; amg_export_pbar copies the
+ * n_l x n_{l+1} CSR to HOST arrays row_ptr[n_l+1], col[nnz], val[nnz]
+ * (ascending columns) and its smoothing weight to *omega. Any pointer may be
+ * NULL to skip it. AMG_ERR_ARG for a hierarchy without it or a bad level.
+ */
+amg_status amg_pbar_nnz(const amg_hierarchy* h, int level, int64_t* nnz);
+amg_status amg_export_pbar(const amg_hierarchy* h, int level, int32_t* row_ptr, int32_t* col, double* val,
+                           double* omega);
 
 /*
  * Copies matching sweep `sweep` of level `level` to HOST arrays (requires

@@ -37,7 +37,7 @@ EXPORTED = [
     "amg_launch_count", "amg_match_noalloc", "amg_solve_batch", "amg_serve_create", "amg_serve_submit",
     "amg_serve_step", "amg_serve_poll", "amg_serve_stats_get", "amg_serve_free", "amg_setup_many",
     "amg_solve_many", "amg_system_offsets", "amg_tune_save", "amg_tune_load", "amg_tune_clear", "amg_tune_size",
-    "amg_smooth_vector",
+    "amg_smooth_vector", "amg_pbar_nnz", "amg_export_pbar",
 ]
 KCYCLE_FULL = 32
 NOALLOC_MAX_N = 65536
@@ -54,8 +54,8 @@ class amg_options(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int), ("omega", ctypes.c_double),
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
                 ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("cycle", ctypes.c_int), ("autotune", ctypes.c_int), ("min_ratio", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("cycle", ctypes.c_int), ("smooth_p", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):
@@ -162,6 +162,11 @@ def lib() -> ctypes.CDLL:
         for name in ("amg_tune_save", "amg_tune_load"):
             getattr(L, name).argtypes = [ctypes.c_char_p]
             getattr(L, name).restype = ctypes.c_int
+        L.amg_pbar_nnz.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        L.amg_pbar_nnz.restype = ctypes.c_int
+        L.amg_export_pbar.argtypes = [_vp, ctypes.c_int, _i32p, _i32p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.amg_export_pbar.restype = ctypes.c_int
         L.amg_smooth_vector.argtypes = [ctypes.POINTER(amg_csr), _vp, _vp, ctypes.c_int, ctypes.c_double, _vp]
         L.amg_smooth_vector.restype = ctypes.c_int
         L.amg_tune_clear.argtypes = []
@@ -366,6 +371,20 @@ def amg_kernel_stats(h: Hierarchy) -> dict:
 
 def amg_kernel_stats_reset(h: Hierarchy) -> None:
     _check(lib().amg_kernel_stats_reset(h.handle))
+
+
+def amg_export_pbar(h: Hierarchy, level: int) -> dict:
+    """Smoothed prolongator of a level (hierarchies built with smooth_p=1) as host arrays."""
+    nnz = ctypes.c_int64()
+    _check(lib().amg_pbar_nnz(h.handle, level, ctypes.byref(nnz)))
+    n = amg_hierarchy_info(h)["n"][level]
+    rp = np.empty(n + 1, dtype=np.int32)
+    cl = np.empty(nnz.value, dtype=np.int32)
+    vl = np.empty(nnz.value, dtype=np.float64)
+    om = ctypes.c_double()
+    _check(lib().amg_export_pbar(h.handle, level, rp.ctypes.data_as(_i32p), cl.ctypes.data_as(_i32p),
+                                 vl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(om)))
+    return dict(row_ptr=rp, col=cl, val=vl, omega=om.value)
 
 
 def amg_smooth_vector(row_ptr, col, val, w0, sweeps: int, omega: float = 1.0, stream=None):

@@ -149,6 +149,11 @@ struct Level {
     int sweeps_done = 0;
     int rounds[AMG_MAX_SWEEPS] = {0};
     std::vector<SweepRecord> sweeps;
+    // smoothed prolongator Pbar = (I - omega D^-1 A) P to the next level and
+    // its transpose (options.smooth_p): CSR (kept for export) and SELL
+    DevCsr pbar, pbar_t;
+    DevSell PB, PBT;
+    double omega_p = 0.0;
     // K-cycle work vectors of this level as the coarse level of an FCG(2)
     // correction (d1, q1, r2, z2, d2, e), in the V-cycle's value type
     void* kv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -63,9 +63,10 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
     if (o.sweeps < 1 || o.sweeps > AMG_MAX_SWEEPS || o.max_levels < 1 || o.max_coarse < 1 || o.pre < 0 ||
         o.post < 0 || !(o.omega > 0.0) || (o.precision != AMG_FP64 && o.precision != AMG_FP32_VCYCLE) ||
         o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0) || o.autotune < 0 ||
-        o.autotune > 1 || o.cycle < 0 || o.cycle > AMG_KCYCLE_FULL || (o.cycle > 0 && (o.pre != 1 || o.post != 1)))
+        o.autotune > 1 || o.cycle < 0 || o.cycle > AMG_KCYCLE_FULL || (o.cycle > 0 && (o.pre != 1 || o.post != 1)) ||
+        o.smooth_p < 0 || o.smooth_p > 1 || (o.smooth_p && (o.cycle != 0 || o.pre != 1 || o.post != 1)))
         return fail(AMG_ERR_ARG, "invalid options");
-    if (many && o.cycle != 0) return fail(AMG_ERR_ARG, "batches of systems use the V-cycle");
+    if (many && (o.cycle != 0 || o.smooth_p)) return fail(AMG_ERR_ARG, "batches of systems use the unsmoothed V-cycle");
     amg_hierarchy* h = new amg_hierarchy;
     h->opt = o;
     h->stream = static_cast<cudaStream_t>(o.stream);
@@ -394,6 +395,30 @@ amg_status amg_serve_stats_get(amg_server* s, amg_serve_stats* out) {
 
 void amg_serve_free(amg_server* s) {
     if (s) amg::serve_free(s);
+}
+
+amg_status amg_pbar_nnz(const amg_hierarchy* h, int level, int64_t* nnz) {
+    if (!h || !nnz) return fail(AMG_ERR_ARG, "null argument");
+    if (level < 0 || level + 1 >= (int)h->lev.size() || !h->lev[level].pbar.ptr)
+        return fail(AMG_ERR_ARG, "no smoothed prolongator on this level");
+    *nnz = h->lev[level].pbar.nnz;
+    return AMG_OK;
+}
+
+amg_status amg_export_pbar(const amg_hierarchy* h, int level, int32_t* row_ptr, int32_t* col, double* val,
+                           double* omega) {
+    if (!h) return fail(AMG_ERR_ARG, "null argument");
+    if (level < 0 || level + 1 >= (int)h->lev.size() || !h->lev[level].pbar.ptr)
+        return fail(AMG_ERR_ARG, "no smoothed prolongator on this level");
+    const amg::DevCsr& P = h->lev[level].pbar;
+    return guarded([&]() -> amg_status {
+        CUDA_CHECK(cudaSetDevice(h->device));
+        if (row_ptr) CUDA_CHECK(cudaMemcpy(row_ptr, P.ptr, sizeof(int) * (P.n + 1), cudaMemcpyDeviceToHost));
+        if (col) CUDA_CHECK(cudaMemcpy(col, P.col, sizeof(int) * (size_t)P.nnz, cudaMemcpyDeviceToHost));
+        if (val) CUDA_CHECK(cudaMemcpy(val, P.val, sizeof(double) * (size_t)P.nnz, cudaMemcpyDeviceToHost));
+        if (omega) *omega = h->lev[level].omega_p;
+        return AMG_OK;
+    });
 }
 
 amg_status amg_smooth_vector(const amg_csr* A, const double* w0, double* w, int sweeps, double omega, void* stream) {

@@ -953,7 +953,7 @@ BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width) {
     if (h->opt.pre != 1 || h->opt.post != 1) AMG_THROW(AMG_ERR_ARG, "block solves use 1+1 smoothing sweeps");
     if (h->lev.size() < 2) AMG_THROW(AMG_ERR_ARG, "block solves need at least two levels");
     if (!h->seg0.empty()) AMG_THROW(AMG_ERR_ARG, "block solves take a hierarchy of one system");
-    if (h->opt.cycle > 0) AMG_THROW(AMG_ERR_ARG, "block solves use the V-cycle");
+    if (h->opt.cycle > 0 || h->opt.smooth_p) AMG_THROW(AMG_ERR_ARG, "block solves use the unsmoothed V-cycle");
     if (h->blk) {
         CUDA_CHECK(cudaStreamSynchronize(h->stream));
         delete h->blk;

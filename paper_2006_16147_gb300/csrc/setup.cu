@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "amg_internal.cuh"
 #include "device_util.cuh"
@@ -1039,6 +1040,208 @@ __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restr
     }
 }
 
+// ------------------------------- smoothed prolongator (Section 3.3) -------
+// eta = max_i sum_j |a_ij| / a_ii (row sums in column order); positive, so the
+// double's bit pattern orders like an unsigned integer and atomicMax is exact.
+__global__ void k_eta_max(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ val, unsigned long long* __restrict__ maxbits) {
+    unsigned long long best = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0, d = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            s = __dadd_rn(s, fabs(val[k]));
+            if (col[k] == i) d = val[k];
+        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(__ddiv_rn(s, d));
+        best = b > best ? b : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(FULL_MASK, best, o);
+        best = t > best ? t : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(maxbits, best);
+}
+
+// Rows of A P (in place) become rows of Pbar: with t_i = omega / a_ii, the
+// entry in column agg_i is p_i - t_i (A P)_iq, every other one -(t_i (A P)_iq).
+__global__ void k_pbar_from_ap(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                               double* __restrict__ val, const int* __restrict__ aptr, const int* __restrict__ acol,
+                               const double* __restrict__ aval, const int* __restrict__ agg,
+                               const double* __restrict__ p, double omega) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int kd = find_in_row(aptr, acol, i, i);
+        const double t = __ddiv_rn(omega, aval[kd]);
+        const int ai = agg[i];
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            const double u = __dmul_rn(t, val[k]);
+            val[k] = col[k] == ai ? __dsub_rn(p[i], u) : -u;
+        }
+    }
+}
+
+// Transpose of an n x nc CSR: counts per column, then entries placed with a
+// per-column cursor (any order), then each column's entries sorted by row.
+__global__ void k_col_count(int n, const int* __restrict__ ptr, const int* __restrict__ col, int* __restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) atomicAdd(&cnt[col[k]], 1);
+}
+
+__global__ void k_col_fill(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const int* __restrict__ tptr, int* cursor,
+                           int* __restrict__ tcol, double* __restrict__ tval) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+            const int q = col[k];
+            const int at = tptr[q] + atomicAdd(&cursor[q], 1);
+            tcol[at] = i;
+            tval[at] = val[k];
+        }
+}
+
+__global__ void k_sort_row_pairs(int n, const int* __restrict__ ptr, int* __restrict__ key, double* __restrict__ val) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int b = ptr[r], e = ptr[r + 1];
+        for (int a = b + 1; a < e; ++a) {
+            const int kk = key[a];
+            const double vv = val[a];
+            int c = a - 1;
+            while (c >= b && key[c] > kk) {
+                key[c + 1] = key[c];
+                val[c + 1] = val[c];
+                --c;
+            }
+            key[c + 1] = kk;
+            val[c + 1] = vv;
+        }
+    }
+}
+
+// General Galerkin product C = Pbar^T A Pbar, one warp per coarse row p:
+// for every fine row i of column p of Pbar (ascending; PbarT row p), every
+// entry a_ij of row i (column order) and every entry v of row j of Pbar, the
+// term (Pbar_ip a_ij) v is added to the running sum of column q. Within one
+// (i, j) step the lanes hold distinct columns q, so the sums of a shared
+// hash table in shared memory are updated without races and in the step
+// order, the first term of a column starting its sum: the oracle's order.
+// FILL = false only counts the distinct columns (cnt[p]); FILL = true writes
+// the row, columns ascending (bitonic sort in shared memory), at cptr[p].
+constexpr int GH = 512;            // hash capacity per coarse row
+constexpr int GW = 4;              // warps per block
+template <bool FILL>
+__global__ void __launch_bounds__(GW * 32) k_galerkin_general(int nc, const int* __restrict__ tptr,
+                                                              const int* __restrict__ tcol,
+                                                              const double* __restrict__ tval,
+                                                              const int* __restrict__ aptr,
+                                                              const int* __restrict__ acol,
+                                                              const double* __restrict__ aval,
+                                                              const int* __restrict__ pptr,
+                                                              const int* __restrict__ pcol,
+                                                              const double* __restrict__ pval, int* __restrict__ cnt,
+                                                              const int* __restrict__ cptr, int* __restrict__ ccol,
+                                                              double* __restrict__ cval, int* __restrict__ overflow) {
+    __shared__ int hk[GW][GH];
+    __shared__ double hv[GW][GH];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int* K = hk[w];
+    double* V = hv[w];
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nc; p += nw) {
+        for (int s = lane; s < GH; s += 32) K[s] = -1;
+        __syncwarp();
+        bool full = false;
+        for (int e = tptr[p]; e < tptr[p + 1]; ++e) {
+            const int i = tcol[e];
+            const double pip = tval[e];
+            for (int k = aptr[i]; k < aptr[i + 1]; ++k) {
+                const int j = acol[k];
+                const double t = __dmul_rn(pip, aval[k]);
+                const int fb = pptr[j], fe = pptr[j + 1];
+                for (int f = fb + lane; f < fe; f += 32) {
+                    const int q = pcol[f];
+                    const double term = __dmul_rn(t, pval[f]);
+                    unsigned h = ((unsigned)q * 2654435761u) & (GH - 1);
+                    int probes = 0;
+                    for (;;) {
+                        const int cur = K[h];
+                        if (cur == q) {
+                            if (FILL) V[h] = __dadd_rn(V[h], term);
+                            break;
+                        }
+                        if (cur == -1) {
+                            const int prev = atomicCAS(&K[h], -1, q);
+                            if (prev == -1) {
+                                if (FILL) V[h] = term;
+                                break;
+                            }
+                            if (prev == q) {
+                                if (FILL) V[h] = __dadd_rn(V[h], term);
+                                break;
+                            }
+                        }
+                        h = (h + 1) & (GH - 1);
+                        if (++probes >= GH) {
+                            full = true;
+                            break;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (__any_sync(FULL_MASK, full)) {
+            if (lane == 0) atomicExch(overflow, 1);
+            continue;
+        }
+        // gather the occupied slots to the front (slot order), then sort by column
+        int m = 0;
+        for (int s0 = 0; s0 < GH; s0 += 32) {
+            const int kk = K[s0 + lane];
+            const double vv = FILL ? V[s0 + lane] : 0.0;
+            const bool occ = kk >= 0;
+            const unsigned bal = __ballot_sync(FULL_MASK, occ);
+            __syncwarp();
+            if (occ) {
+                const int at = m + __popc(bal & ((1u << lane) - 1u));
+                K[at] = kk;
+                if (FILL) V[at] = vv;
+            }
+            m += __popc(bal);
+            __syncwarp();
+        }
+        if (!FILL) {
+            if (lane == 0) cnt[p] = m;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < m) m2 <<= 1;
+        for (int s = m + lane; s < m2; s += 32) K[s] = 0x7fffffff;
+        __syncwarp();
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < m2 / 2; t += 32) {
+                    const int lo = 2 * t - (t & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const int a = K[lo], b = K[hi];
+                    if ((a > b) == up) {
+                        K[lo] = b;
+                        K[hi] = a;
+                        const double tv = V[lo];
+                        V[lo] = V[hi];
+                        V[hi] = tv;
+                    }
+                }
+                __syncwarp();
+            }
+        const int c0 = cptr[p];
+        for (int s = lane; s < m; s += 32) {
+            ccol[c0 + s] = K[s];
+            cval[c0 + s] = V[s];
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ host side ----
 struct Scratch {
     DevArena mem;
@@ -1054,6 +1257,7 @@ struct Scratch {
     int* off = nullptr;       // n + 1
     int* skey = nullptr;      // nnz
     double* sval = nullptr;   // nnz
+    long long cap_nnz = 0;    // entries c, skey and sval hold
     int* scan_tmp = nullptr;
     int* host = nullptr;      // pinned
     ~Scratch() {
@@ -1293,6 +1497,99 @@ void build_members(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     KERNEL_CHECK();
 }
 
+// Per-entry scratch for a matrix of nnz entries: the smoothed Galerkin product
+// can give a coarse matrix with more entries than the finest one.
+void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
+    if (nnz <= S.cap_nnz) return;
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    S.mem.release(S.c);
+    S.mem.release(S.skey);
+    S.mem.release(S.sval);
+    S.c = S.mem.alloc<double>(nnz);
+    S.skey = S.mem.alloc<int>(nnz);
+    S.sval = S.mem.alloc<double>(nnz);
+    S.cap_nnz = nnz;
+}
+
+// Smoothed prolongator of level L (aggregates agg/p to nc coarse rows) and
+// the coarse matrix Pbar^T A Pbar (Section 3.3), the oracle's operation
+// order throughout: omega from eta = max_i sum_j |a_ij| / a_ii, Pbar rows from
+// the rows of A P, the transpose with ascending rows, then the product.
+DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
+    cudaStream_t st = h->stream;
+    const DevCsr& A = L.A;
+    const int n = A.n;
+    unsigned long long* eta_bits = S.mem.alloc<unsigned long long>(1);
+    CUDA_CHECK(cudaMemsetAsync(eta_bits, 0, sizeof(unsigned long long), st));
+    k_eta_max<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, eta_bits);
+    KERNEL_CHECK();
+    unsigned long long eb = 0;
+    CUDA_CHECK(cudaMemcpyAsync(&eb, eta_bits, sizeof(eb), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    S.mem.release(eta_bits);
+    double eta;
+    std::memcpy(&eta, &eb, sizeof(eta));
+    const double omega = 4.0 / (3.0 * eta);
+    L.omega_p = omega;
+
+    // rows of A P (canonical), compacted, then turned into rows of Pbar
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
+    launch_rows<false>(h, rows_group(A.nnz, n), n, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr, S.skey,
+                       S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
+    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, L.agg, L.p, S.skey, S.sval, S.ub, S.list1,
+                                              S.cnt + 8, nullptr);
+    KERNEL_CHECK();
+    DevCsr& P = L.pbar;
+    P.n = n;
+    P.ptr = h->mem.alloc<int>(n + 1);
+    scan_exclusive(S.ub, P.ptr, n, P.ptr + n, st, S.scan_tmp);
+    P.nnz = read_int(P.ptr + n, S.host, st);
+    P.col = h->mem.alloc<int>(P.nnz);
+    P.val = h->mem.alloc<double>(P.nnz);
+    launch_copy(h, P.nnz, n, A.ptr, P.ptr, S.skey, S.sval, P.col, P.val, st);
+    k_pbar_from_ap<<<grid_for(h, n), TPB, 0, st>>>(n, P.ptr, P.col, P.val, A.ptr, A.col, A.val, L.agg, L.p, omega);
+    KERNEL_CHECK();
+
+    // transpose, rows ascending in every column
+    DevCsr& T = L.pbar_t;
+    T.n = nc;
+    T.nnz = P.nnz;
+    T.ptr = h->mem.alloc<int>(nc + 1);
+    T.col = h->mem.alloc<int>(P.nnz);
+    T.val = h->mem.alloc<double>(P.nnz);
+    CUDA_CHECK(cudaMemsetAsync(S.ub, 0, sizeof(int) * (nc + 1), st));
+    k_col_count<<<grid_for(h, n), TPB, 0, st>>>(n, P.ptr, P.col, S.ub);
+    KERNEL_CHECK();
+    scan_exclusive(S.ub, T.ptr, nc, T.ptr + nc, st, S.scan_tmp);
+    CUDA_CHECK(cudaMemsetAsync(S.ub, 0, sizeof(int) * (nc + 1), st));
+    k_col_fill<<<grid_for(h, n), TPB, 0, st>>>(n, P.ptr, P.col, P.val, T.ptr, S.ub, T.col, T.val);
+    KERNEL_CHECK();
+    k_sort_row_pairs<<<grid_for(h, nc), TPB, 0, st>>>(nc, T.ptr, T.col, T.val);
+    KERNEL_CHECK();
+
+    // C = Pbar^T A Pbar: count pass, offsets, fill pass
+    int* over = S.cnt + 10;
+    CUDA_CHECK(cudaMemsetAsync(over, 0, sizeof(int), st));
+    const int gblocks = blocks_for((long long)nc * 32, GW * 32, h->num_sms * 8);
+    k_galerkin_general<false><<<gblocks, GW * 32, 0, st>>>(nc, T.ptr, T.col, T.val, A.ptr, A.col, A.val, P.ptr, P.col,
+                                                          P.val, S.ub, nullptr, nullptr, nullptr, over);
+    KERNEL_CHECK();
+    if (read_int(over, S.host, st))
+        AMG_THROW(AMG_ERR_TOO_LARGE, "a row of Pbar^T A Pbar has more than %d entries", GH);
+    DevCsr C;
+    C.n = nc;
+    C.ptr = h->mem.alloc<int>(nc + 1);
+    scan_exclusive(S.ub, C.ptr, nc, C.ptr + nc, st, S.scan_tmp);
+    C.nnz = read_int(C.ptr + nc, S.host, st);
+    C.col = h->mem.alloc<int>(C.nnz);
+    C.val = h->mem.alloc<double>(C.nnz);
+    k_galerkin_general<true><<<gblocks, GW * 32, 0, st>>>(nc, T.ptr, T.col, T.val, A.ptr, A.col, A.val, P.ptr, P.col,
+                                                         P.val, nullptr, C.ptr, C.col, C.val, over);
+    KERNEL_CHECK();
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return C;
+}
+
 }  // namespace
 
 void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
@@ -1325,6 +1622,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.off = S.mem.alloc<int>(n0 + 2);
     S.skey = S.mem.alloc<int>(nnz0);
     S.sval = S.mem.alloc<double>(nnz0);
+    S.cap_nnz = nnz0;
     S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
 
     // ---- level 0: private copy of A and w, validated
@@ -1385,6 +1683,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         if (size_rule <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= AMG_MAX_LEVELS) break;
         const int nl = h->lev[l].A.n;
         DevCsr A = h->lev[l].A;
+        ensure_entry_scratch(S, A.nnz, st);
         double* w = h->lev[l].w;
         int* agg_l = h->mem.alloc<int>(nl);
         double* p_l = h->mem.alloc<double>(nl);
@@ -1482,6 +1781,16 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         cur.sweeps_done = sweeps_done;
         for (int s = 0; s < AMG_MAX_SWEEPS; ++s) cur.rounds[s] = rounds[s];
         cur.sweeps = std::move(recs);
+        if (o.smooth_p) {
+            // the next level matrix is Pbar^T A Pbar; the last pairwise matrix goes
+            DevCsr C = smooth_level(h, cur, A.n, S);
+            if (A.ptr != cur.A.ptr) {
+                h->mem.release(A.ptr);
+                h->mem.release(A.col);
+                h->mem.release(A.val);
+            }
+            A = C;
+        }
         Level next;
         next.A = A;
         next.w = w;
@@ -1517,8 +1826,13 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         else if (l == 0 || l < nlev - 1 || coarsest_cg) build_sell(h, L.A, L.S, S, fp32);
         if (l == nlev - 1) break;
         build_scaled(h, L, fp32);
-        build_members(h, L, h->lev[l + 1].A.n, S);
-        build_ap(h, L, h->lev[l + 1].A.n, S, fp32);
+        if (o.smooth_p) {
+            build_sell(h, L.pbar, L.PB, S, fp32);
+            build_sell(h, L.pbar_t, L.PBT, S, fp32);
+        } else {
+            build_members(h, L, h->lev[l + 1].A.n, S);
+            build_ap(h, L, h->lev[l + 1].A.n, S, fp32);
+        }
         if (fp32) {
             L.p32 = h->mem.alloc<float>(n);
             k_to_float<<<grid_for(h, n), TPB, 0, st>>>(n, L.p, L.p32);

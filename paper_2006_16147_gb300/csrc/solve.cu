@@ -336,6 +336,34 @@ __global__ void __launch_bounds__(TPB) k_kc_update2(int n, const T* __restrict__
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) e[i] = fma(a, d2[i], e[i]);
 }
 
+// ------------------------------------------- smoothed prolongator (SA) ----
+// Restriction b_c = Pbar^T r (rows of Pbar^T in SELL).
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_sell_spmv(SellView S, const T* __restrict__ val, const T* __restrict__ x,
+                                                   T* __restrict__ y) {
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int j) { return ld(x + j); });
+        const int ip = s * 32 + lane;
+        if (ip < S.n) y[sell_rowid(S, ip)] = acc;
+    }
+}
+
+// Prolongation x <- x + Pbar e (rows of Pbar in SELL).
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_prolong(SellView S, const T* __restrict__ val, const T* __restrict__ e,
+                                                 T* __restrict__ x) {
+    SELL_LOOP(S) {
+        const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
+                               [&](int q) { return ld(e + q); });
+        const int ip = s * 32 + lane;
+        if (ip < S.n) {
+            const int i = sell_rowid(S, ip);
+            x[i] = x[i] + acc;
+        }
+    }
+}
+
 // FP32 copy of the level-0 residual for the FP32 V-cycle: one conversion per
 // row here instead of one per gathered matrix entry in the sweep (on this GPU
 // the FP64 -> FP32 conversion runs at the FP64 rate).
@@ -765,7 +793,8 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     const int V = sizeof(T);
     const int pre = h->opt.pre < 1 ? 1 : h->opt.pre;
     const int post = h->opt.post < 1 ? 1 : h->opt.post;
-    const bool U = pre == 1;     // the pre-smoother hands u = x + omega M^-1 r to the post-smoother
+    const bool SA = h->opt.smooth_p != 0;   // smoothed prolongator: explicit Pbar^T, Pbar, then A-smoothing
+    const bool U = pre == 1 && !SA;         // the pre-smoother hands u = x + omega M^-1 r to the post-smoother
     std::vector<T*> xcur(L + 1), rcur(L + 1), out(L + 1), spare(L + 1);
 
     // downward: level 0 reads the FP64 r directly
@@ -797,6 +826,14 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         rcur[l] = ra;
         spare[l] = (xa == vec(Lv, VX)) ? vec(Lv, VT) : vec(Lv, VX);
         const int nc = h->lev[l + 1].A.n;
+        if (SA) {
+            const SellView SPT{Lv.PBT.n, Lv.PBT.nslices, Lv.PBT.sptr, Lv.PBT.col, Lv.PBT.perm};
+            Scope sc_(&h->prof, st, K_RESTRICT, (double)Lv.pbar_t.nnz * (V + 4) + (double)(Lv.A.n + nc) * V);
+            k_sell_spmv<T><<<sell_grid(h, SPT.nslices), TPB, 0, st>>>(
+                SPT, f32 ? (const T*)Lv.PBT.val32 : (const T*)Lv.PBT.val, ra, vec(h->lev[l + 1], VB));
+            KERNEL_CHECK();
+            continue;
+        }
         Scope sc_(&h->prof, st, K_RESTRICT, by_restrict(Lv.A.n, nc, V));
         k_restrict<T><<<Lv.grid_restrict[f32] ? Lv.grid_restrict[f32] : vec_grid(h, nc), TPB, 0, st>>>(
             nc, Lv.pt_ptr, Lv.pt_idx, pv(Lv), ra, vec(h->lev[l + 1], VB));
@@ -813,6 +850,36 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         const int g = Lv.grid_post[f32] ? Lv.grid_post[f32] : sell_grid(h, S.nslices);
         const T* e = out[l + 1];
         const int nc = h->lev[l + 1].A.n;
+        if (SA) {
+            // x <- x + Pbar e, then one l1-Jacobi sweep on A (the unfused post-smoother)
+            const SellView SPB{Lv.PB.n, Lv.PB.nslices, Lv.PB.sptr, Lv.PB.col, Lv.PB.perm};
+            {
+                Scope sc_(&h->prof, st, l == 0 ? K_POST_L0 : K_POST,
+                          (double)Lv.pbar.nnz * (V + 4) + 2.0 * Lv.A.n * V + (double)nc * V);
+                k_prolong<T><<<sell_grid(h, SPB.nslices), TPB, 0, st>>>(
+                    SPB, f32 ? (const T*)Lv.PB.val32 : (const T*)Lv.PB.val, e, xcur[l]);
+                KERNEL_CHECK();
+            }
+            if (l > 0) {
+                T* ya = vec(Lv, VY);
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
+                k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xcur[l], ya);
+                KERNEL_CHECK();
+                out[l] = ya;
+                continue;
+            }
+            {
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, 8));
+                k_smooth<T, double, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xcur[0], z);
+                KERNEL_CHECK();
+            }
+            if (rz_mode != FIN_NONE) {
+                Scope sc_(&h->prof, st, K_DOT, 16.0 * n0);
+                k_dot<<<red_grid(h), TPB, 0, st>>>(n0, r, z, q2, h->red, h->sc, rz_mode);
+                KERNEL_CHECK();
+            }
+            continue;
+        }
         if (l > 0) {
             T *ya = vec(Lv, VY), *yb = spare[l];
             {
@@ -1122,6 +1189,7 @@ void autotune_levels(amg_hierarchy* h) {
                                          else
                                              launch_pre<T, T>(U, g, st, S, valm, wm, omega, vb(Lv), vx(Lv), vr(Lv));
                                      });
+        if (h->opt.smooth_p) continue;     // the smoothed path has no fused post-smoother or member lists
         Lv.grid_post[f32] = tune_grid(
             h, tune_key(z0 ? "post0" : "post", V, SAP.n, Lv.ap_nnz, SAP.nslices, 1, h->num_sms), cand, [&](int g) {
                 if (z0)

@@ -1,0 +1,122 @@
+"""Smoothed prolongator (options.smooth_p = 1; the paper's VA3 setting)
+through the C ABI against the oracle built with smooth_p=True.
+
+Bars: every level's matrix, smooth vector, l1-Jacobi diagonal, tentative
+aggregates, the smoothed prolongator and its weight bit for bit (the
+coarse matrix Pbar^T A Pbar is summed in the oracle's order); the V-cycle
+within 1e-12 relative; PCG within +-1 iteration and 1e-10 in the solution.
+"""
+import numpy as np
+import pytest
+
+from paper_2006_16147_gb300 import workloads as W
+
+from gpu_util import dev, setup, solve, vcycle
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "poisson_ragged": (lambda: W.poisson3d(33, 17, 9), None, 40),
+    "poisson24": (lambda: W.poisson3d(24), None, 60),
+    "aniso3d": (lambda: W.aniso3d(20, 16, 12), None, 40),
+    "aniso2d": (lambda: W.poisson2d_aniso(96, 80, 1e-2), None, 40),
+    "varcoef": (lambda: W.varcoef3d(20, seed=2), None, 40),
+    "spd_random_w": (lambda: W.random_spd(600, 0.012, 7), 7, 40),
+}
+
+
+def _w(A, seed):
+    if seed is None:
+        return np.ones(A.n)
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.3, 2.0, A.n) * rng.choice([-1.0, 1.0], A.n)
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoothed_setup_bit_exact(orc, name):
+    from paper_2006_16147_gb300 import amg
+    mk, seed, mc = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=mc, smooth_p=True)
+    h = setup(A, w, max_coarse=mc, smooth_p=1)
+    info = amg.amg_hierarchy_info(h)
+    assert info["n"] == [s[0] for s in H.sizes()]
+    assert info["nnz"] == [s[1] for s in H.sizes()]
+    for l in range(H.num_levels):
+        ol = H.level(l)
+        gl = amg.amg_export_level(h, l)
+        for k in ("row_ptr", "col", "val", "w", "minv"):
+            assert np.array_equal(getattr(ol, k), gl[k]), (l, k)
+        if l < H.num_levels - 1:
+            assert np.array_equal(ol.agg, gl["agg"]) and np.array_equal(ol.p, gl["p"]), l
+            Pb, om = H.pbar(l)
+            gp = amg.amg_export_pbar(h, l)
+            assert gp["omega"] == om
+            for a, b in ((Pb.row_ptr, gp["row_ptr"]), (Pb.col, gp["col"]), (Pb.val, gp["val"])):
+                assert np.array_equal(a, b), l
+    assert np.array_equal(H.coarse_factor(), amg.amg_coarse_factor(h))
+    h.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoothed_vcycle_and_pcg_parity(orc, name):
+    mk, seed, mc = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=mc, smooth_p=True)
+    h = setup(A, w, max_coarse=mc, smooth_p=1)
+    r = np.random.default_rng(3).normal(size=A.n)
+    zo = H.vcycle(r)
+    zg = vcycle(h, r)
+    assert np.linalg.norm(zg - zo) <= 1e-12 * np.linalg.norm(zo)
+    b, _ = W.rhs_uniform(A, 1)
+    xo, io = H.pcg(b, rtol=1e-6, maxit=500)
+    xg, ig = solve(h, b, rtol=1e-6, maxit=500)
+    assert io["status"] == 0 and ig["status"] == 0
+    assert abs(ig["iterations"] - io["iterations"]) <= 1
+    assert np.linalg.norm(b - A.scipy() @ xg) <= 1e-6 * np.linalg.norm(b)
+    if ig["iterations"] == io["iterations"]:
+        assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    h.close()
+
+
+def test_smoothed_fp32_and_fewer_iterations():
+    A = W.poisson3d(48)
+    b, _ = W.rhs_uniform(A, 1)
+    its = {}
+    for sp, prec, kr in ((0, 0, 0), (1, 0, 0), (1, 1, 1)):
+        h = setup(A, smooth_p=sp, precision=prec, krylov=kr)
+        x, info = solve(h, b, rtol=1e-8, maxit=500)
+        assert info["status"] == 0
+        assert np.linalg.norm(b - A.scipy() @ x) <= 1e-8 * np.linalg.norm(b)
+        its[(sp, prec)] = info["iterations"]
+        h.close()
+    assert its[(1, 0)] < its[(0, 0)]
+    assert abs(its[(1, 1)] - its[(1, 0)]) <= 2
+
+
+def test_smoothed_option_checks():
+    import torch
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(12)
+    with pytest.raises(amg.AmgError):
+        setup(A, smooth_p=1, cycle=1)
+    with pytest.raises(amg.AmgError):
+        setup(A, smooth_p=2)
+    h = setup(A, smooth_p=1)
+    X = torch.zeros(A.n, 2, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(amg.AmgError):
+        amg.amg_solve_batch(h, dev(W.rhs_normal(A.n, seed=1, k=2)), X)
+    h.close()
+    h = setup(A)
+    with pytest.raises(amg.AmgError):
+        amg.amg_export_pbar(h, 0)
+    h.close()
