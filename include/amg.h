@@ -94,7 +94,10 @@ typedef struct {
     int smooth_p;      /* [0] 1: smoothed prolongator Pbar = (I - omega D^-1 A) P on every level, omega =
                           4 / (3 ||D^-1 A||_inf), coarse matrices Pbar^T A Pbar (Section 3.3; the paper's VA3
                           setting, with the weight that reproduces its smoothed-aggregation constants). V-cycle
-                          (cycle = 0), pre = post = 1, single right-hand-side solves only */
+                          (cycle = 0), pre = post = 1, single right-hand-side solves only. A row of A Pbar or
+                          of Pbar^T A Pbar may hold up to 8192 entries (else AMG_ERR_TOO_LARGE); the
+                          environment variable AMG_SPGEMM_CAP_SHIFT = k (0..3) divides that limit and the
+                          product's internal capacity tiers by 2^k, so small tests reach every tier */
     int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */

@@ -368,44 +368,45 @@ Csr transpose_csr(const Csr& P, int nc) {
     return T;
 }
 
-// Galerkin product Pbar^T A Pbar, coarse row by coarse row: for every fine
-// row i of column p of Pbar (ascending), every entry a_ij of row i (column
-// order) and every entry v of row j of Pbar (ascending column q), the term
-// (Pbar_ip a_ij) v is added to the running sum of column q from left to
-// right, the first term starting the sum. Columns ascending.
-Csr galerkin_general(const Csr& A, const Csr& Pb, const Csr& PbT) {
-    const int nc = PbT.n;
-    Csr C;
-    C.n = nc;
-    C.ptr.assign(nc + 1, 0);
-    std::vector<double> acc(nc, 0.0);
-    std::vector<char> seen(nc, 0);
+// Sparse product X = Y Z (Z with ncols columns), row by row: for every entry
+// y of row p of Y (column order) and every entry z of row j of Z (ascending
+// column q), the term y z is added to the running sum of column q from left
+// to right, the first term starting the sum. Columns ascending.
+Csr spgemm(const Csr& Y, const Csr& Z, int ncols) {
+    Csr X;
+    X.n = Y.n;
+    X.ptr.assign(Y.n + 1, 0);
+    std::vector<double> acc(ncols, 0.0);
+    std::vector<char> seen(ncols, 0);
     std::vector<int> touched;
-    for (int p = 0; p < nc; ++p) {
+    for (int p = 0; p < Y.n; ++p) {
         touched.clear();
-        for (int64_t e = PbT.ptr[p]; e < PbT.ptr[p + 1]; ++e) {
-            const int i = PbT.col[e];
-            const double pip = PbT.val[e];
-            for (int64_t k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
-                const int j = A.col[k];
-                const double t = pip * A.val[k];
-                for (int64_t f = Pb.ptr[j]; f < Pb.ptr[j + 1]; ++f) {
-                    const int q = Pb.col[f];
-                    const double term = t * Pb.val[f];
-                    if (!seen[q]) { seen[q] = 1; acc[q] = term; touched.push_back(q); }
-                    else acc[q] = acc[q] + term;
-                }
+        for (int64_t e = Y.ptr[p]; e < Y.ptr[p + 1]; ++e) {
+            const int j = Y.col[e];
+            const double y = Y.val[e];
+            for (int64_t f = Z.ptr[j]; f < Z.ptr[j + 1]; ++f) {
+                const int q = Z.col[f];
+                const double term = y * Z.val[f];
+                if (!seen[q]) { seen[q] = 1; acc[q] = term; touched.push_back(q); }
+                else acc[q] = acc[q] + term;
             }
         }
         std::sort(touched.begin(), touched.end());
         for (int q : touched) {
-            C.col.push_back(q);
-            C.val.push_back(acc[q]);
+            X.col.push_back(q);
+            X.val.push_back(acc[q]);
             seen[q] = 0;
         }
-        C.ptr[p + 1] = (int32_t)C.col.size();
+        X.ptr[p + 1] = (int32_t)X.col.size();
     }
-    return C;
+    return X;
+}
+
+// Galerkin product Pbar^T A Pbar as two sparse products: W = A Pbar, then
+// Pbar^T W (the transpose's rows hold the fine rows ascending).
+Csr galerkin_general(const Csr& A, const Csr& Pb, const Csr& PbT) {
+    const Csr W = spgemm(A, Pb, PbT.n);
+    return spgemm(PbT, W, PbT.n);
 }
 
 // l1-Jacobi (Eq. 5-6 with blocks of size one): M_ii = a_ii + sum_{j != i} |a_ij|.

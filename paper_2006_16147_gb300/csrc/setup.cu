@@ -8,6 +8,7 @@
 // sums use explicitly rounded operations (__dmul_rn, __dadd_rn, ...), never a
 // fused multiply-add, in a fixed order that is part of the definition.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -365,6 +366,78 @@ __global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __re
     }
 }
 
+// Rows longer than the group kernel's G but at most CAP entries, one
+// block per listed row: (edge, weight order, neighbour) keys bitonic-sorted in
+// shared memory, edges first by the strict order (larger weight, then smaller
+// (lo, hi), which for a fixed row is the smaller neighbour), non-edges last.
+// Longer rows are appended to `longer` for a launch of larger CAP or for
+// k_sort_edges.
+constexpr int EDGE_CAPS[2] = {4096, 16384};
+constexpr int LONG_TPB = 256;
+__global__ void __launch_bounds__(LONG_TPB) k_sort_edges_long(const int* __restrict__ list,
+                                                              const int* __restrict__ nlist, int CAP,
+                                                              const int* __restrict__ ptr,
+                                                              const int* __restrict__ col,
+                                                              const double* __restrict__ c, int* __restrict__ nbr,
+                                                              int* __restrict__ pos, int* __restrict__ cand, int* mate,
+                                                              int* __restrict__ longer, int* __restrict__ nlonger) {
+    extern __shared__ long long esm[];
+    long long* WK = esm;
+    int* U = reinterpret_cast<int*>(esm + CAP);
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    const int tid = threadIdx.x;
+    const int nr = *nlist;
+    for (int t = blockIdx.x; t < nr; t += gridDim.x) {
+        const int v = list[t];
+        const int b = ptr[v], len = ptr[v + 1] - b;
+        if (len > CAP) {
+            if (tid == 0) longer[atomicAdd(nlonger, 1)] = v;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < len) m2 <<= 1;
+        for (int s = tid; s < m2; s += LONG_TPB) {
+            const double cw = s < len ? c[b + s] : NEG_INF;
+            const bool edge = cw != NEG_INF;
+            WK[s] = edge ? weight_order(cw) : (long long)0x8000000000000000ULL;
+            U[s] = edge ? col[b + s] : 0x7fffffff;
+        }
+        __syncthreads();
+        // x before y: edges first, then larger weight order, then smaller neighbour
+        auto before = [](long long wx, int ux, long long wy, int uy) {
+            const bool ex = ux != 0x7fffffff, ey = uy != 0x7fffffff;
+            if (ex != ey) return ex;
+            if (wx != wy) return wx > wy;
+            return ux < uy;
+        };
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int u = tid; u < m2 / 2; u += LONG_TPB) {
+                    const int lo = 2 * u - (u & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const long long wl = WK[lo], wh = WK[hi];
+                    const int ul = U[lo], uh = U[hi];
+                    if (up ? before(wh, uh, wl, ul) : before(wl, ul, wh, uh)) {
+                        WK[lo] = wh;
+                        WK[hi] = wl;
+                        U[lo] = uh;
+                        U[hi] = ul;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int s = tid; s < len; s += LONG_TPB) nbr[b + s] = U[s] != 0x7fffffff ? U[s] : -1;
+        if (tid == 0) {
+            pos[v] = b;
+            const bool any = len > 0 && U[0] != 0x7fffffff;
+            cand[v] = any ? U[0] : -1;
+            if (!any) mate[v] = -2;
+        }
+        __syncthreads();
+    }
+}
+
 // Best free neighbour of v from its sorted list starting at k = pos[v]
 // (e = end of v's row); advances pos[v]. Four list entries and their mate
 // words are loaded together, so skipping matched neighbours costs two memory
@@ -619,6 +692,108 @@ __global__ void k_rap_rows(int nc, const int* __restrict__ heads, const int* __r
             a = e;
         }
         cnt[q] = u;
+    }
+}
+
+// The rows the group kernel below leaves out, up to CAP terms, one block per
+// listed row: the terms (member order, then column order) are keyed by
+// (coarse column, position), bitonic-sorted in shared memory (a stable sort
+// by column), and the first thread of every run of equal columns sums the run
+// left to right from its first term: the canonical order of k_rap_rows and
+// k_ap_rows, bit for bit. Longer rows are appended to `longer` for a launch
+// of larger CAP or for those kernels.
+constexpr int ROW_CAPS[2] = {4096, 8192};
+template <bool RAP>
+__global__ void __launch_bounds__(LONG_TPB) k_rows_long(const int* __restrict__ list, const int* __restrict__ nlist,
+                                                        int CAP,
+                                                        const int* __restrict__ heads, const int* __restrict__ mate,
+                                                        const int* __restrict__ ptr, const int* __restrict__ col,
+                                                        const double* __restrict__ val, const int* __restrict__ agg,
+                                                        const double* __restrict__ p, const int* __restrict__ off,
+                                                        int* __restrict__ skey, double* __restrict__ sval,
+                                                        int* __restrict__ cnt, int* __restrict__ longer,
+                                                        int* __restrict__ nlonger, const double* __restrict__ rowscale) {
+    extern __shared__ unsigned long long rsm[];
+    unsigned long long* KS = rsm;
+    double* VS = reinterpret_cast<double*>(rsm + CAP);
+    __shared__ int wsum[LONG_TPB / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nr = *nlist;
+    for (int t = blockIdx.x; t < nr; t += gridDim.x) {
+        const int q = list[t];
+        int h = q, m = -1;
+        if (RAP) {
+            h = heads[q];
+            m = mate[h];
+        }
+        const int b0 = ptr[h], l0 = ptr[h + 1] - b0;
+        int b1 = 0, l1 = 0;
+        if (RAP && m > h) {
+            b1 = ptr[m];
+            l1 = ptr[m + 1] - b1;
+        }
+        const int len = l0 + l1;
+        if (len > CAP) {
+            if (tid == 0) longer[atomicAdd(nlonger, 1)] = q;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < len) m2 <<= 1;
+        for (int s = tid; s < m2; s += LONG_TPB) {
+            if (s < len) {
+                const bool first = s < l0;
+                const int k = first ? b0 + s : b1 + s - l0;
+                const int j = col[k];
+                KS[s] = ((unsigned long long)(unsigned)agg[j] << 32) | (unsigned)s;
+                VS[s] = RAP ? __dmul_rn(__dmul_rn(p[first ? h : m], val[k]), p[j]) : __dmul_rn(val[k], p[j]);
+            } else {
+                KS[s] = ~0ull;
+            }
+        }
+        __syncthreads();
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int u = tid; u < m2 / 2; u += LONG_TPB) {
+                    const int lo = 2 * u - (u & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long a = KS[lo], bb = KS[hi];
+                    if ((a > bb) == up) {
+                        KS[lo] = bb;
+                        KS[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        int base = 0;
+        for (int c0 = 0; c0 < len; c0 += LONG_TPB) {
+            const int r = c0 + tid;
+            const bool head = r < len && (r == 0 || (KS[r] >> 32) != (KS[r - 1] >> 32));
+            const unsigned bal = __ballot_sync(FULL_MASK, head);
+            if (lane == 0) wsum[wid] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < LONG_TPB / 32; ++w2) {
+                const int cw = wsum[w2];
+                before += w2 < wid ? cw : 0;
+                total += cw;
+            }
+            if (head) {
+                const unsigned key = (unsigned)(KS[r] >> 32);
+                double sum = VS[(unsigned)KS[r]];
+                for (int e = r + 1; e < len && (unsigned)(KS[e] >> 32) == key; ++e)
+                    sum = __dadd_rn(sum, VS[(unsigned)KS[e]]);
+                if (rowscale) sum = __dmul_rn(rowscale[q], sum);
+                const int u = base + before + __popc(bal & ((1u << lane) - 1u));
+                skey[off[q] + u] = (int)key;
+                sval[off[q] + u] = sum;
+            }
+            base += total;
+            __syncthreads();
+        }
+        if (tid == 0) cnt[q] = base;
+        __syncthreads();
     }
 }
 
@@ -1098,128 +1273,231 @@ __global__ void k_col_fill(int n, const int* __restrict__ ptr, const int* __rest
         }
 }
 
-__global__ void k_sort_row_pairs(int n, const int* __restrict__ ptr, int* __restrict__ key, double* __restrict__ val) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const int b = ptr[r], e = ptr[r + 1];
-        for (int a = b + 1; a < e; ++a) {
-            const int kk = key[a];
-            const double vv = val[a];
-            int c = a - 1;
-            while (c >= b && key[c] > kk) {
-                key[c + 1] = key[c];
-                val[c + 1] = val[c];
-                --c;
+// Sort the (key, value) pairs of every row by key (keys distinct within a
+// row): one warp per row (BLOCK = false, rows of at most CAP pairs) or one
+// block per listed row (BLOCK = true), bitonic sort in shared memory. A row
+// longer than CAP is appended to `longs` for the block launch, or flags
+// `overflow` when there is no such list.
+template <bool BLOCK>
+__global__ void k_sort_pairs(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
+                             const int* __restrict__ ptr, int* __restrict__ key, double* __restrict__ val,
+                             int* __restrict__ longs, int* __restrict__ nlongs, int* __restrict__ overflow) {
+    extern __shared__ double ssm[];
+    const int U = BLOCK ? blockDim.x : 32;                 // threads per row
+    const int lane = BLOCK ? threadIdx.x : (threadIdx.x & 31);
+    const int w = BLOCK ? 0 : (threadIdx.x >> 5);
+    const int units = BLOCK ? 1 : (blockDim.x >> 5);
+    double* V = ssm + (size_t)w * CAP;
+    int* K = reinterpret_cast<int*>(ssm + (size_t)units * CAP) + (size_t)w * CAP;
+    const int nunits = BLOCK ? gridDim.x : (gridDim.x * blockDim.x) >> 5;
+    const int nr = list ? *nlist : nrows;
+    auto sync = [] {
+        if (BLOCK) __syncthreads();
+        else __syncwarp();
+    };
+    for (int t = BLOCK ? blockIdx.x : ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nr; t += nunits) {
+        const int r = list ? list[t] : t;
+        const int b = ptr[r], m = ptr[r + 1] - b;
+        if (m <= 1) continue;
+        if (m > CAP) {
+            if (lane == 0) {
+                if (longs) longs[atomicAdd(nlongs, 1)] = r;
+                else atomicExch(overflow, 1);
             }
-            key[c + 1] = kk;
-            val[c + 1] = vv;
-        }
-    }
-}
-
-// General Galerkin product C = Pbar^T A Pbar, one warp per coarse row p:
-// for every fine row i of column p of Pbar (ascending; PbarT row p), every
-// entry a_ij of row i (column order) and every entry v of row j of Pbar, the
-// term (Pbar_ip a_ij) v is added to the running sum of column q. Within one
-// (i, j) step the lanes hold distinct columns q, so the sums of a shared
-// hash table in shared memory are updated without races and in the step
-// order, the first term of a column starting its sum: the oracle's order.
-// FILL = false only counts the distinct columns (cnt[p]); FILL = true writes
-// the row, columns ascending (bitonic sort in shared memory), at cptr[p].
-constexpr int GH = 512;            // hash capacity per coarse row
-constexpr int GW = 4;              // warps per block
-template <bool FILL>
-__global__ void __launch_bounds__(GW * 32) k_galerkin_general(int nc, const int* __restrict__ tptr,
-                                                              const int* __restrict__ tcol,
-                                                              const double* __restrict__ tval,
-                                                              const int* __restrict__ aptr,
-                                                              const int* __restrict__ acol,
-                                                              const double* __restrict__ aval,
-                                                              const int* __restrict__ pptr,
-                                                              const int* __restrict__ pcol,
-                                                              const double* __restrict__ pval, int* __restrict__ cnt,
-                                                              const int* __restrict__ cptr, int* __restrict__ ccol,
-                                                              double* __restrict__ cval, int* __restrict__ overflow) {
-    __shared__ int hk[GW][GH];
-    __shared__ double hv[GW][GH];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    int* K = hk[w];
-    double* V = hv[w];
-    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < nc; p += nw) {
-        for (int s = lane; s < GH; s += 32) K[s] = -1;
-        __syncwarp();
-        bool full = false;
-        for (int e = tptr[p]; e < tptr[p + 1]; ++e) {
-            const int i = tcol[e];
-            const double pip = tval[e];
-            for (int k = aptr[i]; k < aptr[i + 1]; ++k) {
-                const int j = acol[k];
-                const double t = __dmul_rn(pip, aval[k]);
-                const int fb = pptr[j], fe = pptr[j + 1];
-                for (int f = fb + lane; f < fe; f += 32) {
-                    const int q = pcol[f];
-                    const double term = __dmul_rn(t, pval[f]);
-                    unsigned h = ((unsigned)q * 2654435761u) & (GH - 1);
-                    int probes = 0;
-                    for (;;) {
-                        const int cur = K[h];
-                        if (cur == q) {
-                            if (FILL) V[h] = __dadd_rn(V[h], term);
-                            break;
-                        }
-                        if (cur == -1) {
-                            const int prev = atomicCAS(&K[h], -1, q);
-                            if (prev == -1) {
-                                if (FILL) V[h] = term;
-                                break;
-                            }
-                            if (prev == q) {
-                                if (FILL) V[h] = __dadd_rn(V[h], term);
-                                break;
-                            }
-                        }
-                        h = (h + 1) & (GH - 1);
-                        if (++probes >= GH) {
-                            full = true;
-                            break;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        if (__any_sync(FULL_MASK, full)) {
-            if (lane == 0) atomicExch(overflow, 1);
-            continue;
-        }
-        // gather the occupied slots to the front (slot order), then sort by column
-        int m = 0;
-        for (int s0 = 0; s0 < GH; s0 += 32) {
-            const int kk = K[s0 + lane];
-            const double vv = FILL ? V[s0 + lane] : 0.0;
-            const bool occ = kk >= 0;
-            const unsigned bal = __ballot_sync(FULL_MASK, occ);
-            __syncwarp();
-            if (occ) {
-                const int at = m + __popc(bal & ((1u << lane) - 1u));
-                K[at] = kk;
-                if (FILL) V[at] = vv;
-            }
-            m += __popc(bal);
-            __syncwarp();
-        }
-        if (!FILL) {
-            if (lane == 0) cnt[p] = m;
             continue;
         }
         int m2 = 1;
         while (m2 < m) m2 <<= 1;
-        for (int s = m + lane; s < m2; s += 32) K[s] = 0x7fffffff;
-        __syncwarp();
+        for (int s = lane; s < m2; s += U) {
+            K[s] = s < m ? key[b + s] : 0x7fffffff;
+            V[s] = s < m ? val[b + s] : 0.0;
+        }
+        sync();
         for (int size = 2; size <= m2; size <<= 1)
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = lane; t < m2 / 2; t += 32) {
-                    const int lo = 2 * t - (t & (stride - 1));
+                for (int u = lane; u < m2 / 2; u += U) {
+                    const int lo = 2 * u - (u & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const int a = K[lo], c = K[hi];
+                    if ((a > c) == up) {
+                        K[lo] = c;
+                        K[hi] = a;
+                        const double tv = V[lo];
+                        V[lo] = V[hi];
+                        V[hi] = tv;
+                    }
+                }
+                sync();
+            }
+        for (int s = lane; s < m; s += U) {
+            key[b + s] = K[s];
+            val[b + s] = V[s];
+        }
+        sync();
+    }
+}
+
+// Sparse product X = Y Z, one unit per row p of X (a warp, or with BLOCK the
+// whole block): for every entry y of row p of Y (column order) and every
+// entry z of row j of Z, the term y z is added to the running sum of column
+// q. Within one (p, j) step the threads hold distinct columns q, so the sums
+// of a hash table in shared memory are updated without races and in the step
+// order (steps are separated by a warp or block barrier), the first term of a
+// column starting its sum: the oracle's order. FILL = false only counts the
+// distinct columns (cnt[p]); FILL = true writes the row, columns ascending
+// (bitonic sort in shared memory), at xptr[p] and skips the rows whose count
+// is above its capacity. The table has CAP slots per unit in dynamic shared
+// memory and takes at most CAP / 2 columns, which keeps linear probing short;
+// with `list` only the rows list[0 .. *nlist) are done. A row with more
+// columns stops at once; in the count pass it is appended to `longs` for a
+// launch of larger capacity (its count set to INT_MAX until then), or flags
+// `overflow` when there is no such list.
+constexpr int SPG_TIERS = 4;
+constexpr int SPG_CAP[SPG_TIERS] = {512, 2048, 8192, 16384};   // hash slots per row; at most half are used
+constexpr int SPG_UNITS[SPG_TIERS] = {4, 1, 1, 1};             // rows per block (warps, or one block)
+constexpr int SPG_THREADS[SPG_TIERS] = {128, 128, 256, 512};   // threads per block
+template <bool FILL, bool BLOCK>
+__global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
+                              const int* __restrict__ yptr, const int* __restrict__ ycol,
+                              const double* __restrict__ yval, const int* __restrict__ zptr,
+                              const int* __restrict__ zcol, const double* __restrict__ zval, int* __restrict__ cnt,
+                              const int* __restrict__ xptr, int* __restrict__ xcol, double* __restrict__ xval,
+                              int* __restrict__ longs, int* __restrict__ nlongs, int* __restrict__ overflow) {
+    extern __shared__ double gsm[];
+    __shared__ int wsum[32];
+    const int U = BLOCK ? blockDim.x : 32;                  // threads per row
+    const int tid = BLOCK ? threadIdx.x : (threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int unit = BLOCK ? 0 : wid;
+    const int upb = BLOCK ? 1 : (blockDim.x >> 5);
+    double* V = gsm + (size_t)unit * CAP;
+    int* K = reinterpret_cast<int*>(gsm + (size_t)upb * CAP) + (size_t)unit * CAP;
+    const int nunits = BLOCK ? gridDim.x : (gridDim.x * blockDim.x) >> 5;
+    const int nr = list ? *nlist : nrows;
+    const int hshift = 32 - (31 - __clz(CAP));             // Fibonacci hashing: the top log2(CAP) bits
+    auto sync = [] {
+        if (BLOCK) __syncthreads();
+        else __syncwarp();
+    };
+    // number of threads of the unit with `pred` (also a barrier)
+    auto count = [](bool pred) {
+        if (BLOCK) return __syncthreads_count(pred);
+        return __popc(__ballot_sync(FULL_MASK, pred));
+    };
+    // exclusive rank of `pred` among the unit's threads and their total
+    auto rank = [&](bool pred, int& total) {
+        const unsigned bal = __ballot_sync(FULL_MASK, pred);
+        const int in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (!BLOCK) {
+            total = __popc(bal);
+            return in_warp;
+        }
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0;
+        total = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+            const int c = wsum[w2];
+            before += w2 < wid ? c : 0;
+            total += c;
+        }
+        __syncthreads();
+        return before + in_warp;
+    };
+    for (int t = BLOCK ? blockIdx.x : ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nr; t += nunits) {
+        const int p = list ? list[t] : t;
+        if (FILL && cnt[p] > (CAP >> 1)) continue;        // done by a launch of larger capacity
+        for (int s = tid; s < CAP; s += U) K[s] = -1;
+        sync();
+        bool full = false;
+        int used = 0;                                     // distinct columns so far (uniform in the unit)
+        const int eb = yptr[p], ee = yptr[p + 1];
+        int jn = eb < ee ? ycol[eb] : 0;
+        double yn = eb < ee ? yval[eb] : 0.0;
+        int fbn = eb < ee ? zptr[jn] : 0, fen = eb < ee ? zptr[jn + 1] : 0;
+        for (int e = eb; e < ee && !full; ++e) {
+            const double y = yn;
+            const int fb = fbn, fe = fen;
+            if (e + 1 < ee) {                              // the next step's row, loaded ahead
+                jn = ycol[e + 1];
+                yn = yval[e + 1];
+                fbn = zptr[jn];
+                fen = zptr[jn + 1];
+            }
+            for (int f0 = fb; f0 < fe && !full; f0 += U) {
+                const int f = f0 + tid;
+                bool added = false;
+                if (f < fe) {
+                    const int q = zcol[f];
+                    const double term = __dmul_rn(y, zval[f]);
+                    unsigned hs = ((unsigned)q * 2654435769u) >> hshift;
+                    for (;;) {                            // ends: the table is never more than half full
+                        const int cur = K[hs];
+                        if (cur == q) {
+                            if (FILL) V[hs] = __dadd_rn(V[hs], term);
+                            break;
+                        }
+                        if (cur == -1) {
+                            const int prev = atomicCAS(&K[hs], -1, q);
+                            if (prev == -1) {
+                                if (FILL) V[hs] = term;
+                                added = true;
+                                break;
+                            }
+                            if (prev == q) {
+                                if (FILL) V[hs] = __dadd_rn(V[hs], term);
+                                break;
+                            }
+                        }
+                        hs = (hs + 1) & (unsigned)(CAP - 1);
+                    }
+                }
+                used += count(added);
+                full = used > (CAP >> 1);
+            }
+            sync();
+        }
+        if (full) {
+            if (tid == 0) {
+                if (longs && !FILL) {
+                    longs[atomicAdd(nlongs, 1)] = p;
+                    cnt[p] = 0x7fffffff;
+                } else {
+                    atomicExch(overflow, 1);
+                }
+            }
+            sync();
+            continue;
+        }
+        // gather the occupied slots to the front (slot order), then sort by column
+        int m = 0;
+        for (int s0 = 0; s0 < CAP; s0 += U) {
+            const int kk = K[s0 + tid];
+            const double vv = FILL ? V[s0 + tid] : 0.0;
+            const bool occ = kk >= 0;
+            int total;
+            const int r = rank(occ, total);
+            sync();
+            if (occ) {
+                K[m + r] = kk;
+                if (FILL) V[m + r] = vv;
+            }
+            m += total;
+            sync();
+        }
+        if (!FILL) {
+            if (tid == 0) cnt[p] = m;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < m) m2 <<= 1;
+        for (int s = m + tid; s < m2; s += U) K[s] = 0x7fffffff;
+        sync();
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int u = tid; u < m2 / 2; u += U) {
+                    const int lo = 2 * u - (u & (stride - 1));
                     const int hi = lo + stride;
                     const bool up = (lo & size) == 0;
                     const int a = K[lo], b = K[hi];
@@ -1231,14 +1509,14 @@ __global__ void __launch_bounds__(GW * 32) k_galerkin_general(int nc, const int*
                         V[hi] = tv;
                     }
                 }
-                __syncwarp();
+                sync();
             }
-        const int c0 = cptr[p];
-        for (int s = lane; s < m; s += 32) {
-            ccol[c0 + s] = K[s];
-            cval[c0 + s] = V[s];
+        const int c0 = xptr[p];
+        for (int s = tid; s < m; s += U) {
+            xcol[c0 + s] = K[s];
+            xval[c0 + s] = V[s];
         }
-        __syncwarp();
+        sync();
     }
 }
 
@@ -1249,7 +1527,9 @@ struct Scratch {
     double* c = nullptr;
     int *mate = nullptr, *cand = nullptr, *list0 = nullptr, *list1 = nullptr, *mlist = nullptr;
     int* cnt = nullptr;       // [0,1] list counters, [2,3] match counters, [4] rounds, [5] flags, [6..7] totals,
-                              // [8] rows left to the thread-per-row product kernels
+                              // [8] rows left by the group row-product kernels, [9] by the group edge sort,
+                              // [10..13] sparse-product and pair-sort overflow and list counters,
+                              // [13, 14] also rows left by the long-row kernels
     int* flag = nullptr;      // n
     int* qid = nullptr;       // n
     int* heads = nullptr;     // n
@@ -1271,6 +1551,34 @@ int read_int(const int* dev, int* host, cudaStream_t st) {
     CUDA_CHECK(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
     return *host;
+}
+
+// The rows of a row product that the group kernel listed in (list, *nlist):
+// a block each up to ROW_CAPS[0] terms (rows left listed in S.qid, counted in
+// S.cnt[13]), then up to ROW_CAPS[1] (rows left in S.list0, S.cnt[14]), then
+// the thread-per-row kernel for any longer ones.
+template <bool RAP>
+void launch_rows_long(amg_hierarchy* h, Scratch& S, int nrows, const int* list, const int* nlist, const int* heads,
+                      const int* mate, const int* ptr, const int* col, const double* val, const int* agg,
+                      const double* p, const int* off, int* cnt, const double* rowscale, cudaStream_t st) {
+    constexpr int tb = (int)(sizeof(unsigned long long) + sizeof(double));
+    CUDA_CHECK(cudaFuncSetAttribute(k_rows_long<RAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROW_CAPS[1] * tb));
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 2 * sizeof(int), st));
+    k_rows_long<RAP><<<h->num_sms * 3, LONG_TPB, ROW_CAPS[0] * tb, st>>>(
+        list, nlist, ROW_CAPS[0], heads, mate, ptr, col, val, agg, p, off, S.skey, S.sval, cnt, S.qid, S.cnt + 13,
+        rowscale);
+    KERNEL_CHECK();
+    k_rows_long<RAP><<<h->num_sms, LONG_TPB, ROW_CAPS[1] * tb, st>>>(S.qid, S.cnt + 13, ROW_CAPS[1], heads, mate, ptr,
+                                                                     col, val, agg, p, off, S.skey, S.sval, cnt,
+                                                                     S.list0, S.cnt + 14, rowscale);
+    KERNEL_CHECK();
+    if (RAP)
+        k_rap_rows<<<grid_for(h, nrows), TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, S.skey, S.sval,
+                                                      cnt, S.list0, S.cnt + 14);
+    else
+        k_ap_rows<<<grid_for(h, nrows), TPB, 0, st>>>(nrows, ptr, col, val, agg, p, S.skey, S.sval, cnt, S.list0,
+                                                     S.cnt + 14, rowscale);
+    KERNEL_CHECK();
 }
 
 // Locally-dominant matching by frontier rounds. Returns the number of rounds.
@@ -1298,8 +1606,20 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
             k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
                                                             S.cnt + 9);
         KERNEL_CHECK();
-        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate, S.list1,
-                                                     S.cnt + 9);
+        {
+            // long rows: a block each in two capacities, then a thread each
+            constexpr int eb = (int)(sizeof(long long) + sizeof(int));
+            CUDA_CHECK(cudaFuncSetAttribute(k_sort_edges_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            EDGE_CAPS[1] * eb));
+            k_sort_edges_long<<<h->num_sms * 4, LONG_TPB, EDGE_CAPS[0] * eb, st>>>(
+                S.list1, S.cnt + 9, EDGE_CAPS[0], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.qid, S.cnt + 13);
+            KERNEL_CHECK();
+            k_sort_edges_long<<<h->num_sms, LONG_TPB, EDGE_CAPS[1] * eb, st>>>(
+                S.qid, S.cnt + 13, EDGE_CAPS[1], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.heads, S.cnt + 14);
+            KERNEL_CHECK();
+        }
+        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate, S.heads,
+                                                     S.cnt + 14);
         KERNEL_CHECK();
         int nn = n;
         const int* ptr = A.ptr;
@@ -1360,9 +1680,8 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
     launch_rows<true>(h, rows_group(2LL * A.nnz, A.n), nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
                       S.skey, S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
-    k_rap_rows<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
-                                                S.skey, S.sval, S.ub, S.list1, S.cnt + 8);
-    KERNEL_CHECK();
+    launch_rows_long<true>(h, S, nc, S.list1, S.cnt + 8, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
+                           S.ub, nullptr, st);
     DevCsr C;
     C.n = nc;
     C.ptr = owner.alloc<int>(nc + 1);
@@ -1462,9 +1781,8 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
     launch_rows<false>(h, rows_group(L.A.nnz, n), n, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
                        L.A.ptr, S.skey, S.sval, S.ub, S.list1, S.cnt + 8, L.wminv, st);
-    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, S.skey, S.sval, S.ub,
-                                              S.list1, S.cnt + 8, L.wminv);
-    KERNEL_CHECK();
+    launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
+                            L.A.ptr, S.ub, L.wminv, st);
     DevCsr AP;
     AP.n = n;
     AP.ptr = S.mem.alloc<int>(n + 1);
@@ -1511,6 +1829,72 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.cap_nnz = nnz;
 }
 
+// X = Y Z with k_spgemm_hash: count passes of growing
+// capacity (each taking the rows that did not fit the one before), offsets,
+// then fill passes over the same row lists. The result lives in the scratch
+// arena when `scratch`, else in the hierarchy's.
+DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& S, bool scratch) {
+    cudaStream_t st = h->stream;
+    const int n = Y.n;
+    int* over = S.cnt + 10;
+    int* nl = S.cnt + 11;                               // rows listed for tiers 1, 2 and 3
+    int* lists[SPG_TIERS] = {nullptr, S.list0, S.list1, S.qid};
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 4 * sizeof(int), st));
+    // AMG_SPGEMM_CAP_SHIFT = k (0..3) divides every capacity by 2^k, so that
+    // small test matrices reach every tier
+    int cshift = 0;
+    if (const char* e = std::getenv("AMG_SPGEMM_CAP_SHIFT")) cshift = std::max(0, std::min(3, std::atoi(e)));
+    auto cap = [&](int t) { return SPG_CAP[t] >> cshift; };
+    auto smem = [&](int t) { return (size_t)SPG_UNITS[t] * cap(t) * (sizeof(double) + sizeof(int)); };
+    const int smax = (int)smem(SPG_TIERS - 1);
+    CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_hash<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_hash<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    int rows[SPG_TIERS] = {n, 0, 0, 0};
+    auto blocks = [&](int t) {
+        const int cap = h->num_sms * (t == 0 ? 8 : (t == 1 ? 6 : 2));
+        return std::max(1, std::min((rows[t] + SPG_UNITS[t] - 1) / SPG_UNITS[t], cap));
+    };
+    auto launch = [&](bool fill, int t, const int* xptr, int* xcol, double* xval) {
+        const bool last = t == SPG_TIERS - 1;
+        int* longs = (fill || last) ? nullptr : lists[t + 1];
+        int* nlongs = (fill || last) ? nullptr : nl + t;
+        const int* lst = lists[t];
+        const int* nls = t ? nl + t - 1 : nullptr;
+        const dim3 g(blocks(t)), b(SPG_THREADS[t]);
+        const size_t sm = smem(t);
+        if (t == 0 && !fill)
+            k_spgemm_hash<false, false><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
+                                                         Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
+        else if (t == 0)
+            k_spgemm_hash<true, false><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
+                                                        Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
+        else if (!fill)
+            k_spgemm_hash<false, true><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
+                                                        Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
+        else
+            k_spgemm_hash<true, true><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
+                                                       Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
+        KERNEL_CHECK();
+    };
+    for (int t = 0; t < SPG_TIERS; ++t) {
+        if (t > 0) rows[t] = read_int(nl + t - 1, S.host, st);
+        if (rows[t] == 0) break;
+        launch(false, t, nullptr, nullptr, nullptr);
+    }
+    if (read_int(over, S.host, st))
+        AMG_THROW(AMG_ERR_TOO_LARGE, "a row of a sparse product has more than %d entries",
+                  cap(SPG_TIERS - 1) / 2);
+    DevCsr X;
+    X.n = n;
+    X.ptr = scratch ? S.mem.alloc<int>(n + 1) : h->mem.alloc<int>(n + 1);
+    scan_exclusive(S.ub, X.ptr, n, X.ptr + n, st, S.scan_tmp);
+    X.nnz = read_int(X.ptr + n, S.host, st);
+    X.col = scratch ? S.mem.alloc<int>(X.nnz) : h->mem.alloc<int>(X.nnz);
+    X.val = scratch ? S.mem.alloc<double>(X.nnz) : h->mem.alloc<double>(X.nnz);
+    for (int t = 0; t < SPG_TIERS && rows[t] > 0; ++t) launch(true, t, X.ptr, X.col, X.val);
+    return X;
+}
+
 // Smoothed prolongator of level L (aggregates agg/p to nc coarse rows) and
 // the coarse matrix Pbar^T A Pbar (Section 3.3), the oracle's operation
 // order throughout: omega from eta = max_i sum_j |a_ij| / a_ii, Pbar rows from
@@ -1536,9 +1920,8 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
     launch_rows<false>(h, rows_group(A.nnz, n), n, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr, S.skey,
                        S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
-    k_ap_rows<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, L.agg, L.p, S.skey, S.sval, S.ub, S.list1,
-                                              S.cnt + 8, nullptr);
-    KERNEL_CHECK();
+    launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr,
+                            S.ub, nullptr, st);
     DevCsr& P = L.pbar;
     P.n = n;
     P.ptr = h->mem.alloc<int>(n + 1);
@@ -1564,28 +1947,35 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     CUDA_CHECK(cudaMemsetAsync(S.ub, 0, sizeof(int) * (nc + 1), st));
     k_col_fill<<<grid_for(h, n), TPB, 0, st>>>(n, P.ptr, P.col, P.val, T.ptr, S.ub, T.col, T.val);
     KERNEL_CHECK();
-    k_sort_row_pairs<<<grid_for(h, nc), TPB, 0, st>>>(nc, T.ptr, T.col, T.val);
-    KERNEL_CHECK();
+    {
+        // rows of up to 2048 pairs: a warp each; longer rows: a block each
+        constexpr int WCAP = 2048, WPB = 4, BCAP = 16384;
+        const size_t sm_w = (size_t)WPB * WCAP * (sizeof(double) + sizeof(int));
+        const size_t sm_b = (size_t)BCAP * (sizeof(double) + sizeof(int));
+        CUDA_CHECK(cudaFuncSetAttribute(k_sort_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_w));
+        CUDA_CHECK(cudaFuncSetAttribute(k_sort_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
+        int* over = S.cnt + 10;
+        int* nl = S.cnt + 11;
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 2 * sizeof(int), st));
+        k_sort_pairs<false><<<blocks_for((long long)nc * 32, WPB * 32, h->num_sms * 8), WPB * 32, sm_w, st>>>(
+            nc, nullptr, nullptr, WCAP, T.ptr, T.col, T.val, S.list0, nl, over);
+        KERNEL_CHECK();
+        const int nlong = read_int(nl, S.host, st);
+        if (nlong > 0) {
+            k_sort_pairs<true><<<std::min(nlong, h->num_sms), 1024, sm_b, st>>>(nc, S.list0, nl, BCAP, T.ptr, T.col,
+                                                                               T.val, nullptr, nullptr, over);
+            KERNEL_CHECK();
+        }
+        if (read_int(over, S.host, st))
+            AMG_THROW(AMG_ERR_TOO_LARGE, "a column of Pbar has more than %d entries", BCAP);
+    }
 
-    // C = Pbar^T A Pbar: count pass, offsets, fill pass
-    int* over = S.cnt + 10;
-    CUDA_CHECK(cudaMemsetAsync(over, 0, sizeof(int), st));
-    const int gblocks = blocks_for((long long)nc * 32, GW * 32, h->num_sms * 8);
-    k_galerkin_general<false><<<gblocks, GW * 32, 0, st>>>(nc, T.ptr, T.col, T.val, A.ptr, A.col, A.val, P.ptr, P.col,
-                                                          P.val, S.ub, nullptr, nullptr, nullptr, over);
-    KERNEL_CHECK();
-    if (read_int(over, S.host, st))
-        AMG_THROW(AMG_ERR_TOO_LARGE, "a row of Pbar^T A Pbar has more than %d entries", GH);
-    DevCsr C;
-    C.n = nc;
-    C.ptr = h->mem.alloc<int>(nc + 1);
-    scan_exclusive(S.ub, C.ptr, nc, C.ptr + nc, st, S.scan_tmp);
-    C.nnz = read_int(C.ptr + nc, S.host, st);
-    C.col = h->mem.alloc<int>(C.nnz);
-    C.val = h->mem.alloc<double>(C.nnz);
-    k_galerkin_general<true><<<gblocks, GW * 32, 0, st>>>(nc, T.ptr, T.col, T.val, A.ptr, A.col, A.val, P.ptr, P.col,
-                                                         P.val, nullptr, C.ptr, C.col, C.val, over);
-    KERNEL_CHECK();
+    // C = Pbar^T (A Pbar): two sparse products in the oracle's order
+    DevCsr W = spgemm_hash(h, A, P, S, true);
+    DevCsr C = spgemm_hash(h, T, W, S, false);
+    S.mem.release(W.val);
+    S.mem.release(W.col);
+    S.mem.release(W.ptr);
     CUDA_CHECK(cudaStreamSynchronize(st));
     return C;
 }
@@ -1783,7 +2173,11 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         cur.sweeps = std::move(recs);
         if (o.smooth_p) {
             // the next level matrix is Pbar^T A Pbar; the last pairwise matrix goes
-            DevCsr C = smooth_level(h, cur, A.n, S);
+            DevCsr C;
+            {
+                Scope sc_(&h->prof, st, S_SMOOTH_P, 0.0);
+                C = smooth_level(h, cur, A.n, S);
+            }
             if (A.ptr != cur.A.ptr) {
                 h->mem.release(A.ptr);
                 h->mem.release(A.col);

@@ -31,6 +31,8 @@ __all__ = [
     "batch_edges",
     "block_diagonal",
     "random_spd",
+    "random_spd_sparse",
+    "with_hubs",
 ]
 
 
@@ -220,3 +222,46 @@ def random_spd(n: int, density: float, seed: int) -> Csr:
     np.add.at(row_ptr, rows + 1, 1)
     row_ptr = np.cumsum(row_ptr)
     return Csr(row_ptr.astype(np.int32), cols.astype(np.int32), d[rows, cols], f"random_spd_{n}_{seed}")
+
+
+def random_spd_sparse(n: int, k: int, seed: int) -> Csr:
+    """Random sparse SPD matrix without a dense mask: each row draws k random
+    partners, the pattern is symmetrised, off-diagonal values are uniform in
+    [-1, 1] (symmetric), the diagonal is the absolute row sum plus a margin in
+    [0.1, 1]."""
+    import scipy.sparse as sp
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows = np.repeat(np.arange(n), k)
+    cols = rng.integers(0, n, size=n * k)
+    keep = rows != cols
+    rows, cols = rows[keep], cols[keep]
+    vals = rng.uniform(-1.0, 1.0, size=rows.shape[0])
+    U = sp.coo_matrix((vals, (np.minimum(rows, cols), np.maximum(rows, cols))), shape=(n, n)).tocsr()
+    U.sum_duplicates()
+    S = (U + U.T).tocsr()
+    d = np.asarray(abs(S).sum(axis=1)).ravel() + rng.uniform(0.1, 1.0, size=n)
+    M = (S + sp.diags(d)).tocsr()
+    M.sort_indices()
+    return Csr(M.indptr, M.indices, M.data, f"random_spd_sparse_{n}_{k}_{seed}")
+
+
+def with_hubs(A: Csr, sizes, seed: int) -> Csr:
+    """A with hub unknowns appended: hub h couples to sizes[h] distinct random
+    unknowns of A with values -U(0.1, 1) (symmetric). Every diagonal grows by
+    the absolute values added to its row, so a diagonally dominant A stays
+    SPD; a hub's diagonal is its absolute row sum times 1.5."""
+    import scipy.sparse as sp
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n, m = A.n, len(sizes)
+    rows, cols, vals = [], [], []
+    for h, k in enumerate(sizes):
+        nb = np.sort(rng.choice(n, size=int(k), replace=False))
+        rows.append(nb)
+        cols.append(np.full(nb.shape[0], h))
+        vals.append(-rng.uniform(0.1, 1.0, size=nb.shape[0]))
+    B = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, m)).tocsr()
+    extra = np.asarray(abs(B).sum(axis=1)).ravel()
+    hub_d = 1.5 * np.asarray(abs(B).sum(axis=0)).ravel()
+    M = sp.bmat([[A.scipy() + sp.diags(extra), B], [B.T, sp.diags(hub_d)]]).tocsr()
+    M.sort_indices()
+    return Csr(M.indptr, M.indices, M.data, f"{A.name}_hubs{m}_{seed}")

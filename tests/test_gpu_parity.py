@@ -33,6 +33,9 @@ CASES = {
     "varcoef": (lambda: W.varcoef3d(24, seed=2), None),
     "spd_random_w": (lambda: W.random_spd(700, 0.01, 7), 7),
     "spd_dense_rows": (lambda: W.random_spd(300, 0.08, 8), 8),
+    # hub rows of 41 to 17001 entries: every long-row kernel tier of the edge
+    # sort and the row products, and the thread-per-row kernels past them
+    "hubs": (lambda: W.with_hubs(W.poisson2d_aniso(150, 150, 1e-2), [40, 300, 3000, 5000, 9000, 17000], 4), None),
 }
 
 

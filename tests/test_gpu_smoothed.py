@@ -22,6 +22,8 @@ CASES = {
     "aniso2d": (lambda: W.poisson2d_aniso(96, 80, 1e-2), None, 40),
     "varcoef": (lambda: W.varcoef3d(20, seed=2), None, 40),
     "spd_random_w": (lambda: W.random_spd(600, 0.012, 7), 7, 40),
+    # coarse rows on both sides of 512 entries (up to 1134): both Galerkin passes
+    "spd_wide_coarse": (lambda: W.random_spd_sparse(8192, 4, 5), None, 2000),
 }
 
 
@@ -120,3 +122,25 @@ def test_smoothed_option_checks():
     with pytest.raises(amg.AmgError):
         amg.amg_export_pbar(h, 0)
     h.close()
+
+
+def test_smoothed_setup_every_capacity_tier(orc, monkeypatch):
+    # capacities divided by 4 (tiers of 64, 256, 1024, 2048 columns): the
+    # wide coarse rows (up to 1134 columns) pass through every tier
+    from paper_2006_16147_gb300 import amg
+    monkeypatch.setenv("AMG_SPGEMM_CAP_SHIFT", "2")
+    mk, seed, mc = CASES["spd_wide_coarse"]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=mc, smooth_p=True)
+    h = setup(A, w, max_coarse=mc, smooth_p=1)
+    for l in range(H.num_levels):
+        ol = H.level(l)
+        gl = amg.amg_export_level(h, l)
+        for k in ("row_ptr", "col", "val"):
+            assert np.array_equal(getattr(ol, k), gl[k]), (l, k)
+    h.close()
+    monkeypatch.setenv("AMG_SPGEMM_CAP_SHIFT", "3")           # limit 1024 columns: the wide rows overflow
+    with pytest.raises(amg.AmgError) as ei:
+        setup(A, w, max_coarse=mc, smooth_p=1)
+    assert ei.value.status == amg.AMG_ERR_TOO_LARGE

@@ -46,3 +46,24 @@ def test_rhs_seeded():
     assert W.rhs_normal(10, 3, 4).shape == (10, 4)
     e = W.batch_edges(256, 5)
     assert min(e) >= 16 and max(e) <= 64 and len(e) == 256
+
+
+def test_random_spd_sparse_spd_and_seeded():
+    A = W.random_spd_sparse(500, 4, 3)
+    B = W.random_spd_sparse(500, 4, 3)
+    assert np.array_equal(A.val, B.val) and np.array_equal(A.col, B.col)
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    assert np.all(np.diff(A.col[A.row_ptr[0]:A.row_ptr[1]]) > 0)
+    off = np.abs(D).sum(axis=1) - np.abs(np.diag(D))
+    assert np.all(np.diag(D) > off)                   # strictly diagonally dominant => SPD
+    assert np.linalg.eigvalsh(D).min() > 0
+
+
+def test_with_hubs_spd_and_row_lengths():
+    A = W.with_hubs(W.poisson2d_aniso(12, 10), [5, 40], 3)
+    assert A.n == 122
+    assert np.diff(A.row_ptr)[-2:].tolist() == [6, 41]
+    D = A.to_dense()
+    assert np.array_equal(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
