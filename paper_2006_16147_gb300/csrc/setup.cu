@@ -488,6 +488,60 @@ __device__ __forceinline__ void block_append(int k, const int* items, int* list,
 
 __device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 
+// Round r >= 1 of the persistent matching over work items first, first +
+// stride, ...: LD_NG consecutive items per vertex matched in round r - 1,
+// item gl taking its neighbours gl, gl + LD_NG, ...; no block-wide
+// synchronisation inside the round, so the work items of a thread overlap.
+// Pairs are collected per thread (beyond BA_MAX straight into the list) and
+// appended once per block. Every thread of the block must call it.
+constexpr int LD_NG = 8;
+constexpr int LD_SOLO_ITEMS = 1024;   // rounds with at most this many items run in one block
+__device__ __forceinline__ void ld_round(long long r, long long first, long long stride, const int* __restrict__ ptr,
+                                         const int* __restrict__ col, const int* __restrict__ nbr, int* pos,
+                                         int* cand, int* mate, int* const* lists, int* cnt, int n, bool leader) {
+    const int* M = lists[(r - 1) & 1];
+    const int m_cnt = min(__ldcg(cnt + (int)((r - 1) % 3)), n);
+    int* nl = lists[r & 1];
+    int* nc = cnt + (int)(r % 3);
+    // slot (r+1) % 3 was last read at the start of round r-1; it collects round r+1's pairs
+    if (leader) cnt[(int)((r + 1) % 3)] = 0;
+    int items[BA_MAX];
+    int k = 0;
+    const long long total = (long long)m_cnt * LD_NG;
+    for (long long u = first; u < total; u += stride) {
+        const int t = (int)(u / LD_NG), gl = (int)(u % LD_NG);
+        const int m = __ldcg(M + t);
+        const int ke = __ldg(ptr + m + 1);
+        for (int q = __ldg(ptr + m) + gl; q < ke; q += LD_NG) {
+            const int x = __ldg(col + q);
+            // x's state and its list position together (one latency)
+            const int mx = __ldcg(mate + x), cx = __ldcg(cand + x);
+            const int kx = __ldcg(pos + x), ex = __ldg(ptr + x + 1);
+            if (x == m || mx != -1 || cx != m) continue;
+            const int b = best_free_sorted(x, kx, ex, nbr, pos, mate);
+            cand[x] = b;
+            if (b < 0) {
+                mate[x] = -2;
+                continue;
+            }
+            fence_sc_gpu();
+            if (__ldcg(cand + b) != x) continue;
+            const int lo = min(x, b), hi = max(x, b);
+            if (atomicCAS(&mate[lo], -1, hi) != -1) continue;
+            mate[hi] = lo;
+            if (k + 2 <= BA_MAX) {
+                items[k++] = lo;
+                items[k++] = hi;
+            } else {
+                const int at = atomicAdd(nc, 2);
+                if (at < n) nl[at] = lo;
+                if (at + 1 < n) nl[at + 1] = hi;
+            }
+        }
+    }
+    block_append(k, items, nl, nc, n);
+}
+
 // One round per grid barrier. Round 0 matches the mutual pairs of the initial
 // candidates. Round r >= 1 takes the vertices matched in round r-1; each of
 // their free neighbours whose candidate was one of them picks its next best
@@ -501,15 +555,17 @@ __device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::
 // The set of pairs matched in each round equals one round of the
 // locally-dominant algorithm.
 //
-// cnt: [0..2] match-list counters (ring of three rounds), [6] barrier
-// arrivals, [7] error, [8] rounds that matched at least one pair.
+// cnt: [0..2] match-list counters (ring of three rounds), [7] error, [8]
+// rounds that matched at least one pair, [15] round number handed over after
+// a one-block phase, [32] barrier arrivals (a cache line of its own, away
+// from the counters the rounds update).
 __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __restrict__ ptr,
                                                         const int* __restrict__ col, const int* __restrict__ nbr,
                                                         int* pos, int* cand, int* mate, int* list0, int* list1,
                                                         int* mlist, int* cnt, long long max_rounds) {
     (void)mlist;
     int* lists[2] = {list0, list1};
-    unsigned* bar = reinterpret_cast<unsigned*>(cnt + 6);
+    unsigned* bar = reinterpret_cast<unsigned*>(cnt + 32);
     int* err = cnt + 7;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned epoch = 0;
@@ -532,61 +588,40 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
     grid_sync(bar, ++epoch, err);
     if (__ldcg(err)) return;
     if (leader && __ldcg(cnt + 0) > 0) cnt[8] += 1;
-    constexpr int NG = 8;
-    for (long long r = 1;; ++r) {
-        const int* M = lists[(r - 1) & 1];
+    long long r = 1;
+    for (;;) {
         const int m_cnt = min(__ldcg(cnt + (int)((r - 1) % 3)), n);
         if (m_cnt == 0) return;
         if (r > max_rounds) {
             if (leader) atomicExch(err, 2);
             return;
         }
-        int* nl = lists[r & 1];
-        int* nc = cnt + (int)(r % 3);
-        // slot (r+1) % 3 was last read at the start of round r-1; it collects round r+1's pairs
-        if (leader) cnt[(int)((r + 1) % 3)] = 0;
-        // NG consecutive lanes per matched vertex, lane gl taking neighbours
-        // gl, gl + NG, ...; no block-wide synchronisation inside the round,
-        // so the work items of a thread overlap. Pairs are collected per
-        // thread (beyond BA_MAX straight into the list) and appended once.
-        int k = 0;
-        const long long total = (long long)m_cnt * NG;
-        for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < total;
-             u += (long long)gridDim.x * blockDim.x) {
-            const int t = (int)(u / NG), gl = (int)(u % NG);
-            const int m = __ldcg(M + t);
-            const int ke = __ldg(ptr + m + 1);
-            for (int q = __ldg(ptr + m) + gl; q < ke; q += NG) {
-                const int x = __ldg(col + q);
-                // x's state and its list position together (one latency)
-                const int mx = __ldcg(mate + x), cx = __ldcg(cand + x);
-                const int kx = __ldcg(pos + x), ex = __ldg(ptr + x + 1);
-                if (x == m || mx != -1 || cx != m) continue;
-                const int b = best_free_sorted(x, kx, ex, nbr, pos, mate);
-                cand[x] = b;
-                if (b < 0) {
-                    mate[x] = -2;
-                    continue;
+        if ((long long)m_cnt * LD_NG <= LD_SOLO_ITEMS) {
+            // a small frontier: block 0 runs the rounds alone, separated by
+            // block barriers, until the frontier grows or ends; the other
+            // blocks wait at the grid barrier and then take up its round number
+            if (blockIdx.x == 0) {
+                for (;;) {
+                    ld_round(r, threadIdx.x, blockDim.x, ptr, col, nbr, pos, cand, mate, lists, cnt, n, leader);
+                    __syncthreads();
+                    const int mc = min(__ldcg(cnt + (int)(r % 3)), n);
+                    if (leader && mc > 0) cnt[8] += 1;
+                    ++r;
+                    if (mc == 0 || (long long)mc * LD_NG > LD_SOLO_ITEMS || r > max_rounds) break;
                 }
-                fence_sc_gpu();
-                if (__ldcg(cand + b) != x) continue;
-                const int lo = min(x, b), hi = max(x, b);
-                if (atomicCAS(&mate[lo], -1, hi) != -1) continue;
-                mate[hi] = lo;
-                if (k + 2 <= BA_MAX) {
-                    items[k++] = lo;
-                    items[k++] = hi;
-                } else {
-                    const int at = atomicAdd(nc, 2);
-                    if (at < n) nl[at] = lo;
-                    if (at + 1 < n) nl[at + 1] = hi;
-                }
+                if (threadIdx.x == 0) cnt[15] = (int)r;
             }
+            grid_sync(bar, ++epoch, err);
+            if (__ldcg(err)) return;
+            r = __ldcg(cnt + 15);
+            continue;
         }
-        block_append(k, items, nl, nc, n);
+        ld_round(r, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, ptr, col, nbr, pos, cand, mate,
+                 lists, cnt, n, leader);
         grid_sync(bar, ++epoch, err);
         if (__ldcg(err)) return;
-        if (leader && __ldcg(nc) > 0) cnt[8] += 1;
+        if (leader && __ldcg(cnt + (int)(r % 3)) > 0) cnt[8] += 1;
+        ++r;
     }
 }
 
@@ -1592,7 +1627,7 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
         int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
         double* sc = S.sval;
         int* pos = S.flag;
-        CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 16, st));
+        CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 64, st));
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 9, 0, sizeof(int), st));
         const int G = rows_group(A.nnz, n);
         const int gblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
@@ -2004,7 +2039,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.list0 = S.mem.alloc<int>(n0);
     S.list1 = S.mem.alloc<int>(n0);
     S.mlist = S.mem.alloc<int>(n0);
-    S.cnt = S.mem.alloc<int>(16);
+    S.cnt = S.mem.alloc<int>(64);
     S.flag = S.mem.alloc<int>(n0 + 1);
     S.qid = S.mem.alloc<int>(n0 + 1);
     S.heads = S.mem.alloc<int>(n0 + 1);
