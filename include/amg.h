@@ -88,11 +88,11 @@ typedef struct {
                           1..c (those that are not the coarsest) the coarse correction is two flexible CG
                           iterations preconditioned by the cycle starting on that level; deeper levels use
                           the V-cycle. AMG_KCYCLE_FULL is the paper's K-cycle on every intermediate level
-                          (Section 3.3, the cycle it uses with this unsmoothed aggregation). The
+                          (Section 3.2, the cycle it uses with this unsmoothed aggregation). The
                           preconditioner is then not linear, so the outer solver is flexible CG whatever
                           `krylov` says. Requires pre = post = 1; single right-hand-side solves only */
     int smooth_p;      /* [0] 1: smoothed prolongator Pbar = (I - omega D^-1 A) P on every level, omega =
-                          4 / (3 ||D^-1 A||_inf), coarse matrices Pbar^T A Pbar (Section 3.3; the paper's VA3
+                          4 / (3 ||D^-1 A||_inf), coarse matrices Pbar^T A Pbar (Section 3.2; the paper's VA3
                           setting, with the weight that reproduces its smoothed-aggregation constants). V-cycle
                           (cycle = 0), pre = post = 1, single right-hand-side solves only. A row of A Pbar or
                           of Pbar^T A Pbar may hold up to 8192 entries (else AMG_ERR_TOO_LARGE); the

@@ -289,12 +289,12 @@ struct Hierarchy {
     std::vector<std::vector<double>> Lb;
     int pre = 1, post = 1;
     int kcycle = 0;
-    int smooth_p = 0;              // 1: smoothed prolongator Pbar = (I - omega D^-1 A) P (Section 3.3)                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
+    int smooth_p = 0;              // 1: smoothed prolongator Pbar = (I - omega D^-1 A) P (Section 3.2)                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
     double omega = 1.0;
     int use_ld = 0;
 };
 
-// ------------------------------- smoothed prolongator (Section 3.3) -------
+// ------------------------------- smoothed prolongator (Section 3.2) -------
 // Pbar = (I - omega D^-1 A) P with D = diag(A). The paper's text takes
 // omega = 1 / ||D^-1 A||_inf; its table of two-level constants for the
 // smoothed prolongator is reproduced with 4/3 of that (2/3 on the Laplacian),
@@ -621,7 +621,7 @@ void coarse_cg(const Level& L, const double* b, double* x) {
 double dot(const double* a, const double* b, int n);
 void vcycle(const Hierarchy& H, int l, const double* b, double* x);
 
-// Coarse correction of the K-cycle (Section 3.3, the cycle used with the
+// Coarse correction of the K-cycle (Section 3.2, the cycle used with the
 // unsmoothed prolongator): two iterations of flexible CG on A_m e = b from
 // e = 0, preconditioned by the cycle that starts on level m.
 void fcg2(const Hierarchy& H, int m, const double* b, double* e) {

@@ -1250,7 +1250,7 @@ __global__ void k_ap_rows(int n, const int* __restrict__ ptr, const int* __restr
     }
 }
 
-// ------------------------------- smoothed prolongator (Section 3.3) -------
+// ------------------------------- smoothed prolongator (Section 3.2) -------
 // eta = max_i sum_j |a_ij| / a_ii (row sums in column order); positive, so the
 // double's bit pattern orders like an unsigned integer and atomicMax is exact.
 __global__ void k_eta_max(int n, const int* __restrict__ ptr, const int* __restrict__ col,
@@ -1931,7 +1931,7 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
 }
 
 // Smoothed prolongator of level L (aggregates agg/p to nc coarse rows) and
-// the coarse matrix Pbar^T A Pbar (Section 3.3), the oracle's operation
+// the coarse matrix Pbar^T A Pbar (Section 3.2), the oracle's operation
 // order throughout: omega from eta = max_i sum_j |a_ij| / a_ii, Pbar rows from
 // the rows of A P, the transpose with ascending rows, then the product.
 DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {

@@ -243,7 +243,7 @@ void launch_post(bool u, int grid, cudaStream_t st, SellView SAP, const T* apw, 
 // ------------------------------------------------------------ K-cycle ------
 // The coarse correction of a K-cycle on level m: two flexible CG iterations
 // on A_m e = b from e = 0, preconditioned by the cycle that starts on level m
-// (Section 3.3). d1 = B b; q1 = A d1; alpha1 = d1.b / d1.q1; e = alpha1 d1;
+// (Section 3.2). d1 = B b; q1 = A d1; alpha1 = d1.b / d1.q1; e = alpha1 d1;
 // r2 = b - alpha1 q1; z2 = B r2; beta = z2.q1 / d1.q1; d2 = z2 - beta d1;
 // q2 = A d2 = A z2 - beta q1; alpha2 = d2.r2 / d2.q2; e += alpha2 d2. The
 // scalars stay on the device; dot products are summed in FP64.

@@ -1,6 +1,6 @@
 """Oracle K-cycle (two FCG iterations as the coarse correction on every
 intermediate level, cycle=32: the paper's cycle for the unsmoothed
-prolongator, Section 3.3; cycle=c limits that to coarse levels 1..c).
+prolongator, Section 3.2; cycle=c limits that to coarse levels 1..c).
 
 Pins: with two levels there is no intermediate level, so the K-cycle is the
 V-cycle bit for bit; on a level whose coarse level has two rows, two flexible

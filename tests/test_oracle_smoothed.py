@@ -1,5 +1,5 @@
 """Oracle smoothed prolongator Pbar = (I - omega D^-1 A) P and the general
-Galerkin product Pbar^T A Pbar (Section 3.3; the paper's VA3 setting).
+Galerkin product Pbar^T A Pbar (Section 3.2; the paper's VA3 setting).
 
 Pins: the two-level constant K of the paper's smoothed-aggregation table
 (HGS, 16^3) from the oracle's Pbar; omega = 2/3 on the Laplacian; the coarse
