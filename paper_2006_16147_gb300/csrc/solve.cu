@@ -349,6 +349,60 @@ __global__ void __launch_bounds__(TPB) k_sell_spmv(SellView S, const T* __restri
     }
 }
 
+// Wide rows (the dense coarse levels of smoothed hierarchies), FP64, CSR,
+// one warp per row: lanes take the row's entries k = lane, lane + 32, ...,
+// the partial sums meet in a shuffle reduction, lane 0 applies the row's
+// step. s_i = sum_j v_ij x_j with v_ij = a_ij, or (a_ij m_j) x_j for W_PRE
+// (the same rounded products as the column-scaled values of the SELL path).
+//   W_SPMV    y_i = s_i                              (restriction Pbar^T r)
+//   W_ADD     y_i = y_i + s_i                        (prolongation x + Pbar e)
+//   W_PRE     y_i = b_i - omega s_i, xo_i = wm_i b_i (pre-smoothing from zero)
+//   W_SMOOTH  y_i = x_i + omega m_i (b_i - s_i)      (smoothing sweep)
+enum WideOp : int { W_SPMV = 0, W_ADD = 1, W_PRE = 2, W_SMOOTH = 3 };
+constexpr int WIDE_MIN_A = 64;   // mean entries per row from which a level matrix takes this path
+constexpr int WIDE_MIN_P = 64;   // the same for Pbar and its transpose
+template <int OP>
+__global__ void __launch_bounds__(TPB) k_wide(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                              const double* __restrict__ val, const double* __restrict__ x,
+                                              const double* __restrict__ minv, const double* __restrict__ wm,
+                                              double omega, const double* __restrict__ b, double* __restrict__ y,
+                                              double* __restrict__ xo) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const int kb = ptr[i], ke = ptr[i + 1];
+        double acc0 = 0.0, acc1 = 0.0;
+        int k = kb + lane;
+        for (; k + 32 < ke; k += 64) {
+            const int j0 = col[k], j1 = col[k + 32];
+            const double v0 = OP == W_PRE ? val[k] * minv[j0] : val[k];
+            const double v1 = OP == W_PRE ? val[k + 32] * minv[j1] : val[k + 32];
+            acc0 = fma(v0, ld(x + j0), acc0);
+            acc1 = fma(v1, ld(x + j1), acc1);
+        }
+        if (k < ke) {
+            const int j0 = col[k];
+            const double v0 = OP == W_PRE ? val[k] * minv[j0] : val[k];
+            acc0 = fma(v0, ld(x + j0), acc0);
+        }
+        double acc = acc0 + acc1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        if (lane == 0) {
+            if (OP == W_SPMV) y[i] = acc;
+            if (OP == W_ADD) y[i] = y[i] + acc;
+            if (OP == W_PRE) {
+                const double bi = b[i];
+                y[i] = fma(-omega, acc, bi);
+                xo[i] = wm[i] * bi;
+            }
+            if (OP == W_SMOOTH) y[i] = fma(omega * minv[i], b[i] - acc, x[i]);
+        }
+    }
+}
+
+bool wide(const DevCsr& M, int min_mean) { return M.n > 0 && (long long)M.nnz >= (long long)min_mean * M.n; }
+
 // Prolongation x <- x + Pbar e (rows of Pbar in SELL).
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_prolong(SellView S, const T* __restrict__ val, const T* __restrict__ e,
@@ -698,6 +752,7 @@ int vec_grid(const amg_hierarchy* h, long long n) { return blocks_for(n, TPB, h-
 
 // Fixed grid of every reducing kernel (deterministic partial order).
 int red_grid(const amg_hierarchy* h) { return h->red.blocks; }
+int wide_grid(const amg_hierarchy* h, long long rows) { return blocks_for(rows * 32, TPB, h->num_sms * 16); }
 
 void coarse_solve_launch(amg_hierarchy* h, const void* b, void* x, bool fp32_in, bool fp64_out) {
     const int n = h->nc;
@@ -809,7 +864,15 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             k_to_f32<<<vec_grid(h, Lv.A.n), TPB, 0, st>>>(Lv.A.n, r, (float*)vec(Lv, VB));
             KERNEL_CHECK();
         }
-        {
+        const bool wideA = SA && !f32 && wide(Lv.A, WIDE_MIN_A);       // dense coarse level of a smoothed hierarchy
+        if (wideA) {
+            Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 ? 8 : V));
+            const double* bl = l == 0 ? r : (const double*)vec(Lv, VB);
+            k_wide<W_PRE><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, bl, Lv.minv,
+                                                                Lv.wminv, (double)omega, bl, (double*)ra,
+                                                                (double*)xa);
+            KERNEL_CHECK();
+        } else {
             Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 && !f32 ? 8 : V));
             if (l == 0 && !f32) launch_pre<T, double>(U, g, st, S, valm(Lv), wm(Lv), omega, r, xa, ra);
             else launch_pre<T, T>(U, g, st, S, valm(Lv), wm(Lv), omega, vec(Lv, VB), xa, ra);
@@ -829,8 +892,13 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         if (SA) {
             const SellView SPT{Lv.PBT.n, Lv.PBT.nslices, Lv.PBT.sptr, Lv.PBT.col, Lv.PBT.perm};
             Scope sc_(&h->prof, st, K_RESTRICT, (double)Lv.pbar_t.nnz * (V + 4) + (double)(Lv.A.n + nc) * V);
-            k_sell_spmv<T><<<sell_grid(h, SPT.nslices), TPB, 0, st>>>(
-                SPT, f32 ? (const T*)Lv.PBT.val32 : (const T*)Lv.PBT.val, ra, vec(h->lev[l + 1], VB));
+            if (!f32 && wide(Lv.pbar_t, WIDE_MIN_P))
+                k_wide<W_SPMV><<<wide_grid(h, nc), TPB, 0, st>>>(nc, Lv.pbar_t.ptr, Lv.pbar_t.col, Lv.pbar_t.val,
+                                                                 (const double*)ra, nullptr, nullptr, 0.0, nullptr,
+                                                                 (double*)vec(h->lev[l + 1], VB), nullptr);
+            else
+                k_sell_spmv<T><<<sell_grid(h, SPT.nslices), TPB, 0, st>>>(
+                    SPT, f32 ? (const T*)Lv.PBT.val32 : (const T*)Lv.PBT.val, ra, vec(h->lev[l + 1], VB));
             KERNEL_CHECK();
             continue;
         }
@@ -856,14 +924,25 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             {
                 Scope sc_(&h->prof, st, l == 0 ? K_POST_L0 : K_POST,
                           (double)Lv.pbar.nnz * (V + 4) + 2.0 * Lv.A.n * V + (double)nc * V);
-                k_prolong<T><<<sell_grid(h, SPB.nslices), TPB, 0, st>>>(
-                    SPB, f32 ? (const T*)Lv.PB.val32 : (const T*)Lv.PB.val, e, xcur[l]);
+                if (!f32 && wide(Lv.pbar, WIDE_MIN_P))
+                    k_wide<W_ADD><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(Lv.A.n, Lv.pbar.ptr, Lv.pbar.col,
+                                                                       Lv.pbar.val, (const double*)e, nullptr,
+                                                                       nullptr, 0.0, nullptr, (double*)xcur[l],
+                                                                       nullptr);
+                else
+                    k_prolong<T><<<sell_grid(h, SPB.nslices), TPB, 0, st>>>(
+                        SPB, f32 ? (const T*)Lv.PB.val32 : (const T*)Lv.PB.val, e, xcur[l]);
                 KERNEL_CHECK();
             }
             if (l > 0) {
                 T* ya = vec(Lv, VY);
                 Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
-                k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xcur[l], ya);
+                if (!f32 && wide(Lv.A, WIDE_MIN_A))
+                    k_wide<W_SMOOTH><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
+                        Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xcur[l], Lv.minv, nullptr,
+                        (double)omega, (const double*)vec(Lv, VB), (double*)ya, nullptr);
+                else
+                    k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xcur[l], ya);
                 KERNEL_CHECK();
                 out[l] = ya;
                 continue;
