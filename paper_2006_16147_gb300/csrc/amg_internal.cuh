@@ -224,6 +224,10 @@ struct BlockWork {
     double* cw[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // coarsest CG x, r, z, p, q (n_c x K)
     double* cpart = nullptr;            // coarsest CG block partials
     int* cctl = nullptr;                // [0] barrier arrivals, [1] error
+    cudaGraphExec_t gstep[2] = {nullptr, nullptr};   // captured steps without / with active columns
+    long long gkernels[2] = {0, 0};     // kernels in each graph (added to the launch count per replay)
+    int gk = -1;                        // column count and output the graphs were captured for
+    const double* gX = nullptr;
     ~BlockWork();
 };
 

@@ -23,6 +23,8 @@
 namespace amg {
 
 BlockWork::~BlockWork() {
+    for (auto& g : gstep)
+        if (g) cudaGraphExecDestroy(g);
     if (mode_host) cudaFreeHost(mode_host);
     if (iters_host) cudaFreeHost(iters_host);
     if (rr_host) cudaFreeHost(rr_host);
@@ -1034,10 +1036,11 @@ void block_init_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     KERNEL_CHECK();
 }
 
-// One step of columns [0, k) (see the file comment), then an asynchronous
-// copy of the column states to the host mirrors. Launches only.
-void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k) {
-    (void)B;
+namespace {
+
+// The kernels of one step of columns [0, k): with `any_active` the CG half
+// (q = A p, x and r updates), then the V-cycle and p = z + beta p.
+void block_step_kernels(amg_hierarchy* h, double* X, int k, bool any_active) {
     BlockWork& W = *h->blk;
     cudaStream_t st = h->stream;
     const int ld = W.K;
@@ -1047,8 +1050,6 @@ void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     Level& L0 = h->lev[0];
     const int n = L0.A.n;
     const double nnz = (double)L0.A.nnz;
-    bool any_active = false;
-    for (int c = 0; c < k; ++c) any_active |= W.mode_host[c] == COL_ACTIVE;
     if (any_active) {
         {
             Scope sc_(&h->prof, st, K_SPMV_DOT, 12.0 * nnz + 16.0 * n * k);
@@ -1070,6 +1071,73 @@ void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k) {
         DISPATCH_CPL(cpl, bk_update_p<CPL><<<grid_rows(h, n, G), TPB, 0, st>>>(n, W.Z, W.P, k, ld, G, W.sc))
         KERNEL_CHECK();
     }
+}
+
+bool any_active_column(const BlockWork& W, int k) {
+    for (int c = 0; c < k; ++c)
+        if (W.mode_host[c] == COL_ACTIVE) return true;
+    return false;
+}
+
+// The same step as one CUDA graph launch: the step's kernels are captured
+// once per (active columns or not) on a private stream (the caller's may be
+// the legacy default stream, which cannot capture) and replayed on the
+// hierarchy's stream. Used while profiling is off and the coarsest level is
+// dense (the coarsest CG is a cooperative launch).
+void block_step_graph(amg_hierarchy* h, double* X, int k) {
+    BlockWork& W = *h->blk;
+    if (W.gk != k || W.gX != X) {
+        for (auto& g : W.gstep)
+            if (g) {
+                CUDA_CHECK(cudaGraphExecDestroy(g));
+                g = nullptr;
+            }
+        W.gk = k;
+        W.gX = X;
+    }
+    const bool act = any_active_column(W, k);
+    cudaGraphExec_t& ge = W.gstep[act ? 1 : 0];
+    if (!ge) {
+        cudaStream_t st = h->stream;
+        cudaStream_t cs = nullptr;
+        CUDA_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        h->stream = cs;
+        cudaGraph_t graph = nullptr;
+        try {
+            CUDA_CHECK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const long long before = launch_counter().load();
+            try {
+                block_step_kernels(h, X, k, act);
+                W.gkernels[act ? 1 : 0] = launch_counter().load() - before;
+            } catch (...) {
+                cudaStreamEndCapture(cs, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            CUDA_CHECK(cudaStreamEndCapture(cs, &graph));
+            CUDA_CHECK(cudaGraphInstantiate(&ge, graph, 0));
+            CUDA_CHECK(cudaGraphDestroy(graph));
+        } catch (...) {
+            h->stream = st;
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        h->stream = st;
+        CUDA_CHECK(cudaStreamDestroy(cs));
+    }
+    CUDA_CHECK(cudaGraphLaunch(ge, h->stream));
+    launch_counter().fetch_add(W.gkernels[act ? 1 : 0], std::memory_order_relaxed);
+    copy_state_async(h, W);
+}
+
+}  // namespace
+
+// One step of columns [0, k) (see the file comment), then an asynchronous
+// copy of the column states to the host mirrors. Launches only.
+void block_step_launch(amg_hierarchy* h, const double* B, double* X, int k) {
+    (void)B;
+    BlockWork& W = *h->blk;
+    block_step_kernels(h, X, k, any_active_column(W, k));
     copy_state_async(h, W);
 }
 
@@ -1125,6 +1193,7 @@ amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, doub
     copy_state_async(h, W);
     CUDA_CHECK(cudaStreamSynchronize(h->stream));
     int steps = 0;
+    const bool graphs = !h->prof.on && !h->coarse_cg;
     for (;;) {
         bool live = false;
         int maxi = 0;
@@ -1133,7 +1202,8 @@ amg_status solve_batch(amg_hierarchy* h, int k, const double* B, double* X, doub
             maxi = std::max(maxi, W.iters_host[c]);
         }
         if (!live || maxi >= maxit || ++steps > 4 * maxit + 16) break;
-        block_step_launch(h, B, X, k);
+        if (graphs) block_step_graph(h, X, k);
+        else block_step_launch(h, B, X, k);
         CUDA_CHECK(cudaStreamSynchronize(h->stream));
         if (block_check_launch(h, B, X, k)) CUDA_CHECK(cudaStreamSynchronize(h->stream));
     }

@@ -178,6 +178,7 @@ struct ManyWork {
     double* rr_host = nullptr;
     double* bb_host = nullptr;
     cudaGraphExec_t step = nullptr;
+    long long step_kernels = 0;         // kernels in the step graph (added to the launch count per replay)
     const double* b = nullptr;
     double* x = nullptr;
     ~ManyWork() {
@@ -261,6 +262,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
     };
     try {
         CUDA_CHECK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const long long before = launch_counter().load();
         try {
             m_spmv<<<sgrid, TPB, 0, cs>>>(S, L0.S.val, p, nullptr, q);
             KERNEL_CHECK();
@@ -275,6 +277,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
             KERNEL_CHECK();
             m_update_p<<<vgrid, TPB, 0, cs>>>(n, h->seg_row0, z, p, M.sc);
             KERNEL_CHECK();
+            M.step_kernels = launch_counter().load() - before;
         } catch (...) {
             cudaStreamEndCapture(cs, &graph);
             if (graph) cudaGraphDestroy(graph);
@@ -302,6 +305,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
         }
         if (!live || maxi >= maxit || ++steps > 4 * maxit + 16) break;
         CUDA_CHECK(cudaGraphLaunch(M.step, st));
+        launch_counter().fetch_add(M.step_kernels, std::memory_order_relaxed);
         copy_state(h, M, m);
         bool check = false;
         for (int s = 0; s < m; ++s) check |= M.mode_host[s] == COL_CHECK;

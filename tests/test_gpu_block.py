@@ -97,3 +97,23 @@ def test_zero_columns_and_initial_guess(orc):
     for c in (0, 1, 3, 4):
         assert infos[c]["true_relres"] <= 1e-6
     h.close()
+
+
+def test_graph_steps_equal_direct_launches(orc):
+    # unprofiled solves replay one captured graph per CG step; profiled solves
+    # launch the same kernels one by one: the results must agree bit for bit,
+    # also on a second solve with other columns (graphs re-captured for k, X)
+    from paper_2006_16147_gb300 import amg
+    A = W.poisson3d(24, 20, 18)
+    for k, seed in ((8, 11), (3, 12)):
+        B = W.rhs_normal(A.n, seed, k)
+        hg = setup(A)
+        hp = setup(A, profile=1)
+        Xg, ig = _batch(hg, B)
+        Xp, ip = _batch(hp, B)
+        Xg2, _ = _batch(hg, B)                      # a new output buffer: graphs captured again
+        assert np.array_equal(Xg, Xp) and np.array_equal(Xg, Xg2)
+        assert [i["iterations"] for i in ig] == [i["iterations"] for i in ip]
+        assert amg.amg_kernel_stats(hp) and not amg.amg_kernel_stats(hg)
+        hg.close()
+        hp.close()
