@@ -331,24 +331,29 @@ __global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __re
                 len = -1;
             }
         }
-        double cw = NEG_INF;
-        int u = -1, lo = 0x7fffffff, hi = 0x7fffffff, edge = 0;
+        // key of this lane's entry: (weight order, neighbour); within one row
+        // the strict order's (lo, hi) tiebreak is the neighbour's index order.
+        // Non-edges carry neighbour INT_MAX.
+        long long wk = (long long)0x8000000000000000ULL;
+        int u = -1, uk = 0x7fffffff;
+        bool edge = false;
         if (gl < len) {
-            cw = c[b + gl];
+            const double cw = c[b + gl];
             u = col[b + gl];
             edge = cw != NEG_INF;
-            lo = min(u, v);
-            hi = max(u, v);
+            if (edge) {
+                wk = weight_order(cw);
+                uk = u;
+            }
         }
         int better = 0, nedge = 0, nonedge_before = 0;
 #pragma unroll
         for (int t = 0; t < G; ++t) {
-            const double ct = __shfl_sync(FULL_MASK, cw, t, G);
-            const int lot = __shfl_sync(FULL_MASK, lo, t, G);
-            const int hit = __shfl_sync(FULL_MASK, hi, t, G);
-            const int et = __shfl_sync(FULL_MASK, edge, t, G);
+            const long long wt = __shfl_sync(FULL_MASK, wk, t, G);
+            const int ut = __shfl_sync(FULL_MASK, uk, t, G);
+            const bool et = ut != 0x7fffffff;
             nedge += et;
-            better += et && key_better(ct, lot, hit, cw, lo, hi);
+            better += et && (wt > wk || (wt == wk && ut < uk));
             nonedge_before += (t < gl && t < len && !et);
         }
         if (gl < len) {
