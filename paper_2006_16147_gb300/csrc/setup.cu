@@ -1384,26 +1384,34 @@ __global__ void k_sort_pairs(int nrows, const int* __restrict__ list, const int*
 // q. Within one (p, j) step the threads hold distinct columns q, so the sums
 // of a hash table in shared memory are updated without races and in the step
 // order (steps are separated by a warp or block barrier), the first term of a
-// column starting its sum: the oracle's order. FILL = false only counts the
-// distinct columns (cnt[p]); FILL = true writes the row, columns ascending
-// (bitonic sort in shared memory), at xptr[p] and skips the rows whose count
-// is above its capacity. The table has CAP slots per unit in dynamic shared
-// memory and takes at most CAP / 2 columns, which keeps linear probing short;
-// with `list` only the rows list[0 .. *nlist) are done. A row with more
-// columns stops at once; in the count pass it is appended to `longs` for a
-// launch of larger capacity (its count set to INT_MAX until then), or flags
-// `overflow` when there is no such list.
+// column starting its sum: the oracle's order. The table has CAP slots per
+// unit in dynamic shared memory and takes at most CAP / 2 columns, which
+// keeps linear probing short; with `list` only the rows list[0 .. *nlist)
+// are done. Modes:
+//   SPG_COUNT  count the distinct columns (cnt[p]);
+//   SPG_FILL   write the row, columns ascending (bitonic sort in shared
+//              memory), at xoff[p] of (xcol, xval); rows whose count is above
+//              the capacity are left to a launch of larger capacity;
+//   SPG_ONE    one pass: write the sorted row into a scratch slot (at
+//              xoff[p] * stride, or t * stride for the t-th listed row) and
+//              its count to cnt[p].
+// In SPG_COUNT and SPG_ONE a row with more columns stops at once and is
+// appended to `longs` for a launch of larger capacity (its count set to
+// INT_MAX until then), or flags `overflow` when there is no such list.
+enum SpgMode : int { SPG_COUNT = 0, SPG_FILL = 1, SPG_ONE = 2 };
 constexpr int SPG_TIERS = 4;
 constexpr int SPG_CAP[SPG_TIERS] = {512, 2048, 8192, 16384};   // hash slots per row; at most half are used
 constexpr int SPG_UNITS[SPG_TIERS] = {4, 1, 1, 1};             // rows per block (warps, or one block)
 constexpr int SPG_THREADS[SPG_TIERS] = {128, 128, 256, 512};   // threads per block
-template <bool FILL, bool BLOCK>
+template <int MODE, bool BLOCK>
 __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
                               const int* __restrict__ yptr, const int* __restrict__ ycol,
                               const double* __restrict__ yval, const int* __restrict__ zptr,
                               const int* __restrict__ zcol, const double* __restrict__ zval, int* __restrict__ cnt,
-                              const int* __restrict__ xptr, int* __restrict__ xcol, double* __restrict__ xval,
-                              int* __restrict__ longs, int* __restrict__ nlongs, int* __restrict__ overflow) {
+                              const int* __restrict__ xoff, long long stride, int* __restrict__ xcol,
+                              double* __restrict__ xval, int* __restrict__ longs, int* __restrict__ nlongs,
+                              int* __restrict__ overflow) {
+    constexpr bool FILL = MODE != SPG_COUNT;               // the values are summed
     extern __shared__ double gsm[];
     __shared__ int wsum[32];
     const int U = BLOCK ? blockDim.x : 32;                  // threads per row
@@ -1447,7 +1455,7 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
     };
     for (int t = BLOCK ? blockIdx.x : ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < nr; t += nunits) {
         const int p = list ? list[t] : t;
-        if (FILL && cnt[p] > (CAP >> 1)) continue;        // done by a launch of larger capacity
+        if (MODE == SPG_FILL && cnt[p] > (CAP >> 1)) continue;   // done by a launch of larger capacity
         for (int s = tid; s < CAP; s += U) K[s] = -1;
         sync();
         bool full = false;
@@ -1500,7 +1508,7 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
         }
         if (full) {
             if (tid == 0) {
-                if (longs && !FILL) {
+                if (longs && MODE != SPG_FILL) {
                     longs[atomicAdd(nlongs, 1)] = p;
                     cnt[p] = 0x7fffffff;
                 } else {
@@ -1526,7 +1534,7 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
             m += total;
             sync();
         }
-        if (!FILL) {
+        if (MODE == SPG_COUNT) {
             if (tid == 0) cnt[p] = m;
             continue;
         }
@@ -1551,12 +1559,55 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
                 }
                 sync();
             }
-        const int c0 = xptr[p];
+        const long long c0 = MODE == SPG_FILL ? (long long)xoff[p]
+                                              : (list ? (long long)t * stride : (long long)xoff[p] * stride);
         for (int s = tid; s < m; s += U) {
             xcol[c0 + s] = K[s];
             xval[c0 + s] = V[s];
         }
+        if (MODE == SPG_ONE && tid == 0) cnt[p] = m;
         sync();
+    }
+}
+
+// Scratch units (8 entries) a one-pass row needs: min(terms of the row,
+// cap) rounded up, terms = sum of the lengths of the Z rows it reads.
+__global__ void k_spgemm_units(int n, const int* __restrict__ yptr, const int* __restrict__ ycol,
+                               const int* __restrict__ zptr, int cap, int* __restrict__ units) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        int sum = 0;
+        for (int e = yptr[p]; e < yptr[p + 1]; ++e) {
+            const int j = ycol[e];
+            sum += zptr[j + 1] - zptr[j];
+            if (sum >= cap) {
+                sum = cap;
+                break;
+            }
+        }
+        units[p] = (sum + 7) >> 3;
+    }
+}
+
+// Rows of a one-pass product from their scratch slots (as in SPG_ONE) to the
+// CSR arrays, a warp per row; rows with more than `limit` columns went on to
+// a launch of larger capacity and are copied from its slots.
+__global__ void k_spgemm_copy(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int limit,
+                              const int* __restrict__ cnt, const int* __restrict__ xoff, long long stride,
+                              const int* __restrict__ scol, const double* __restrict__ sval,
+                              const int* __restrict__ xptr, int* __restrict__ xcol, double* __restrict__ xval) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nr = list ? *nlist : nrows;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nr; t += nw) {
+        const int p = list ? list[t] : t;
+        const int m = cnt[p];
+        if (m > limit) continue;
+        const long long src = list ? (long long)t * stride : (long long)xoff[p] * stride;
+        const int dst = xptr[p];
+        for (int s = lane; s < m; s += 32) {
+            xcol[dst + s] = scol[src + s];
+            xval[dst + s] = sval[src + s];
+        }
     }
 }
 
@@ -1869,10 +1920,11 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.cap_nnz = nnz;
 }
 
-// X = Y Z with k_spgemm_hash: count passes of growing
-// capacity (each taking the rows that did not fit the one before), offsets,
-// then fill passes over the same row lists. The result lives in the scratch
-// arena when `scratch`, else in the hierarchy's.
+// X = Y Z with k_spgemm_hash: passes of growing capacity, each taking the
+// rows that did not fit the one before. A pass writes its rows, sorted, into
+// scratch slots (then the offsets and a copy into place), or, when the slots
+// would be too large, counts them and fills them after the offsets. The
+// result lives in the scratch arena when `scratch`, else in the hierarchy's.
 DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& S, bool scratch) {
     cudaStream_t st = h->stream;
     const int n = Y.n;
@@ -1887,39 +1939,65 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
     auto cap = [&](int t) { return SPG_CAP[t] >> cshift; };
     auto smem = [&](int t) { return (size_t)SPG_UNITS[t] * cap(t) * (sizeof(double) + sizeof(int)); };
     const int smax = (int)smem(SPG_TIERS - 1);
-    CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_hash<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_hash<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    for (const void* f : {(const void*)k_spgemm_hash<SPG_COUNT, true>, (const void*)k_spgemm_hash<SPG_FILL, true>,
+                          (const void*)k_spgemm_hash<SPG_ONE, true>})
+        CUDA_CHECK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     int rows[SPG_TIERS] = {n, 0, 0, 0};
+    bool one[SPG_TIERS] = {false, false, false, false};   // tier done in one pass (scratch slots)
+    int* scol[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
+    double* sval[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
     auto blocks = [&](int t) {
-        const int cap = h->num_sms * (t == 0 ? 8 : (t == 1 ? 6 : 2));
-        return std::max(1, std::min((rows[t] + SPG_UNITS[t] - 1) / SPG_UNITS[t], cap));
+        const int cp = h->num_sms * (t == 0 ? 8 : (t == 1 ? 6 : 2));
+        return std::max(1, std::min((rows[t] + SPG_UNITS[t] - 1) / SPG_UNITS[t], cp));
     };
-    auto launch = [&](bool fill, int t, const int* xptr, int* xcol, double* xval) {
+    auto launch = [&](int mode, int t, const int* xoff, long long stride, int* xcol, double* xval) {
         const bool last = t == SPG_TIERS - 1;
-        int* longs = (fill || last) ? nullptr : lists[t + 1];
-        int* nlongs = (fill || last) ? nullptr : nl + t;
+        int* longs = (mode == SPG_FILL || last) ? nullptr : lists[t + 1];
+        int* nlongs = (mode == SPG_FILL || last) ? nullptr : nl + t;
         const int* lst = lists[t];
         const int* nls = t ? nl + t - 1 : nullptr;
         const dim3 g(blocks(t)), b(SPG_THREADS[t]);
         const size_t sm = smem(t);
-        if (t == 0 && !fill)
-            k_spgemm_hash<false, false><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
-                                                         Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
-        else if (t == 0)
-            k_spgemm_hash<true, false><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
-                                                        Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
-        else if (!fill)
-            k_spgemm_hash<false, true><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
-                                                        Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
-        else
-            k_spgemm_hash<true, true><<<g, b, sm, st>>>(n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col,
-                                                       Z.val, S.ub, xptr, xcol, xval, longs, nlongs, over);
+#define SPG_ARGS n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, xoff, stride, xcol, xval, longs, nlongs, over
+        if (t == 0) {
+            if (mode == SPG_COUNT) k_spgemm_hash<SPG_COUNT, false><<<g, b, sm, st>>>(SPG_ARGS);
+            else if (mode == SPG_FILL) k_spgemm_hash<SPG_FILL, false><<<g, b, sm, st>>>(SPG_ARGS);
+            else k_spgemm_hash<SPG_ONE, false><<<g, b, sm, st>>>(SPG_ARGS);
+        } else {
+            if (mode == SPG_COUNT) k_spgemm_hash<SPG_COUNT, true><<<g, b, sm, st>>>(SPG_ARGS);
+            else if (mode == SPG_FILL) k_spgemm_hash<SPG_FILL, true><<<g, b, sm, st>>>(SPG_ARGS);
+            else k_spgemm_hash<SPG_ONE, true><<<g, b, sm, st>>>(SPG_ARGS);
+        }
+#undef SPG_ARGS
         KERNEL_CHECK();
     };
-    for (int t = 0; t < SPG_TIERS; ++t) {
-        if (t > 0) rows[t] = read_int(nl + t - 1, S.host, st);
+    // first tier: one pass into scratch slots of min(terms, capacity) entries
+    // when their total fits int32 units, else count now and fill later
+    one[0] = (long long)n * ((cap(0) / 2 + 7) / 8) <= 0x7fffffffLL;
+    if (one[0]) {
+        k_spgemm_units<<<grid_for(h, n), TPB, 0, st>>>(n, Y.ptr, Y.col, Z.ptr, cap(0) / 2, S.flag);
+        KERNEL_CHECK();
+        scan_exclusive(S.flag, S.off, n, S.off + n, st, S.scan_tmp);
+        const long long units = read_int(S.off + n, S.host, st);
+        scol[0] = S.mem.alloc<int>(units * 8 + 1);
+        sval[0] = S.mem.alloc<double>(units * 8 + 1);
+        launch(SPG_ONE, 0, S.off, 8, scol[0], sval[0]);
+    } else {
+        launch(SPG_COUNT, 0, nullptr, 0, nullptr, nullptr);
+    }
+    // larger tiers on the listed rows: one pass when the slots stay below 2^28 entries
+    for (int t = 1; t < SPG_TIERS; ++t) {
+        rows[t] = read_int(nl + t - 1, S.host, st);
         if (rows[t] == 0) break;
-        launch(false, t, nullptr, nullptr, nullptr);
+        const long long slots = (long long)rows[t] * (cap(t) / 2);
+        one[t] = slots <= (1LL << 28);
+        if (one[t]) {
+            scol[t] = S.mem.alloc<int>(slots);
+            sval[t] = S.mem.alloc<double>(slots);
+            launch(SPG_ONE, t, nullptr, cap(t) / 2, scol[t], sval[t]);
+        } else {
+            launch(SPG_COUNT, t, nullptr, 0, nullptr, nullptr);
+        }
     }
     if (read_int(over, S.host, st))
         AMG_THROW(AMG_ERR_TOO_LARGE, "a row of a sparse product has more than %d entries",
@@ -1931,7 +2009,22 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
     X.nnz = read_int(X.ptr + n, S.host, st);
     X.col = scratch ? S.mem.alloc<int>(X.nnz) : h->mem.alloc<int>(X.nnz);
     X.val = scratch ? S.mem.alloc<double>(X.nnz) : h->mem.alloc<double>(X.nnz);
-    for (int t = 0; t < SPG_TIERS && rows[t] > 0; ++t) launch(true, t, X.ptr, X.col, X.val);
+    for (int t = 0; t < SPG_TIERS && rows[t] > 0; ++t) {
+        if (!one[t]) {
+            launch(SPG_FILL, t, X.ptr, 0, X.col, X.val);
+            continue;
+        }
+        const int* lst = lists[t];
+        const int* nls = t ? nl + t - 1 : nullptr;
+        k_spgemm_copy<<<blocks_for((long long)rows[t] * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
+            n, lst, nls, cap(t) / 2, S.ub, S.off, t ? cap(t) / 2 : 8, scol[t], sval[t], X.ptr, X.col, X.val);
+        KERNEL_CHECK();
+    }
+    for (int t = 0; t < SPG_TIERS; ++t)
+        if (scol[t]) {
+            S.mem.release(scol[t]);
+            S.mem.release(sval[t]);
+        }
     return X;
 }
 
