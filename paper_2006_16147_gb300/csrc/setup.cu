@@ -1403,6 +1403,11 @@ constexpr int SPG_TIERS = 4;
 constexpr int SPG_CAP[SPG_TIERS] = {512, 2048, 8192, 16384};   // hash slots per row; at most half are used
 constexpr int SPG_UNITS[SPG_TIERS] = {4, 1, 1, 1};             // rows per block (warps, or one block)
 constexpr int SPG_THREADS[SPG_TIERS] = {128, 128, 256, 512};   // threads per block
+// a unit's threads per step (32, or the block) never exceed half the capacity,
+// also with the capacities divided by 8 for tests
+static_assert(32 <= (SPG_CAP[0] >> 3) / 2 && SPG_THREADS[1] <= (SPG_CAP[1] >> 3) / 2 &&
+                  SPG_THREADS[2] <= (SPG_CAP[2] >> 3) / 2 && SPG_THREADS[3] <= (SPG_CAP[3] >> 3) / 2,
+              "probe loop needs a free slot");
 template <int MODE, bool BLOCK>
 __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
                               const int* __restrict__ yptr, const int* __restrict__ ycol,
@@ -1480,7 +1485,9 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
                     const int q = zcol[f];
                     const double term = __dmul_rn(y, zval[f]);
                     unsigned hs = ((unsigned)q * 2654435769u) >> hshift;
-                    for (;;) {                            // ends: the table is never more than half full
+                    // ends: a step starts with at most CAP / 2 columns and adds at
+                    // most U <= CAP / 2, so the key or a free slot is always found
+                    for (;;) {
                         const int cur = K[hs];
                         if (cur == q) {
                             if (FILL) V[hs] = __dadd_rn(V[hs], term);
