@@ -494,14 +494,14 @@ __device__ __forceinline__ void block_append(int k, const int* items, int* list,
 __device__ __forceinline__ void fence_sc_gpu() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 
 // Round r >= 1 of the persistent matching over work items first, first +
-// stride, ...: LD_NG consecutive items per vertex matched in round r - 1,
-// item gl taking its neighbours gl, gl + LD_NG, ...; no block-wide
+// stride, ...: 2^ngl consecutive items per vertex matched in round r - 1,
+// item gl taking its neighbours gl, gl + 2^ngl, ...; no block-wide
 // synchronisation inside the round, so the work items of a thread overlap.
 // Pairs are collected per thread (beyond BA_MAX straight into the list) and
 // appended once per block. Every thread of the block must call it.
-constexpr int LD_NG = 8;
 constexpr int LD_SOLO_ITEMS = 1024;   // rounds with at most this many items run in one block
-__device__ __forceinline__ void ld_round(long long r, long long first, long long stride, const int* __restrict__ ptr,
+__device__ __forceinline__ void ld_round(long long r, long long first, long long stride, int ngl,
+                                         const int* __restrict__ ptr,
                                          const int* __restrict__ col, const int* __restrict__ nbr, int* pos,
                                          int* cand, int* mate, int* const* lists, int* cnt, int n, bool leader) {
     const int* M = lists[(r - 1) & 1];
@@ -512,12 +512,13 @@ __device__ __forceinline__ void ld_round(long long r, long long first, long long
     if (leader) cnt[(int)((r + 1) % 3)] = 0;
     int items[BA_MAX];
     int k = 0;
-    const long long total = (long long)m_cnt * LD_NG;
+    const int ng = 1 << ngl;
+    const long long total = (long long)m_cnt << ngl;
     for (long long u = first; u < total; u += stride) {
-        const int t = (int)(u / LD_NG), gl = (int)(u % LD_NG);
+        const int t = (int)(u >> ngl), gl = (int)(u & (ng - 1));
         const int m = __ldcg(M + t);
         const int ke = __ldg(ptr + m + 1);
-        for (int q = __ldg(ptr + m) + gl; q < ke; q += LD_NG) {
+        for (int q = __ldg(ptr + m) + gl; q < ke; q += ng) {
             const int x = __ldg(col + q);
             // x's state and its list position together (one latency)
             const int mx = __ldcg(mate + x), cx = __ldcg(cand + x);
@@ -567,8 +568,7 @@ __device__ __forceinline__ void ld_round(long long r, long long first, long long
 __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __restrict__ ptr,
                                                         const int* __restrict__ col, const int* __restrict__ nbr,
                                                         int* pos, int* cand, int* mate, int* list0, int* list1,
-                                                        int* mlist, int* cnt, long long max_rounds) {
-    (void)mlist;
+                                                        int ngl, int* cnt, long long max_rounds) {
     int* lists[2] = {list0, list1};
     unsigned* bar = reinterpret_cast<unsigned*>(cnt + 32);
     int* err = cnt + 7;
@@ -601,18 +601,18 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
             if (leader) atomicExch(err, 2);
             return;
         }
-        if ((long long)m_cnt * LD_NG <= LD_SOLO_ITEMS) {
+        if (((long long)m_cnt << ngl) <= LD_SOLO_ITEMS) {
             // a small frontier: block 0 runs the rounds alone, separated by
             // block barriers, until the frontier grows or ends; the other
             // blocks wait at the grid barrier and then take up its round number
             if (blockIdx.x == 0) {
                 for (;;) {
-                    ld_round(r, threadIdx.x, blockDim.x, ptr, col, nbr, pos, cand, mate, lists, cnt, n, leader);
+                    ld_round(r, threadIdx.x, blockDim.x, ngl, ptr, col, nbr, pos, cand, mate, lists, cnt, n, leader);
                     __syncthreads();
                     const int mc = min(__ldcg(cnt + (int)(r % 3)), n);
                     if (leader && mc > 0) cnt[8] += 1;
                     ++r;
-                    if (mc == 0 || (long long)mc * LD_NG > LD_SOLO_ITEMS || r > max_rounds) break;
+                    if (mc == 0 || ((long long)mc << ngl) > LD_SOLO_ITEMS || r > max_rounds) break;
                 }
                 if (threadIdx.x == 0) cnt[15] = (int)r;
             }
@@ -621,8 +621,8 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
             r = __ldcg(cnt + 15);
             continue;
         }
-        ld_round(r, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, ptr, col, nbr, pos, cand, mate,
-                 lists, cnt, n, leader);
+        ld_round(r, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, ngl, ptr, col, nbr, pos, cand,
+                 mate, lists, cnt, n, leader);
         grid_sync(bar, ++epoch, err);
         if (__ldcg(err)) return;
         if (leader && __ldcg(cnt + (int)(r % 3)) > 0) cnt[8] += 1;
@@ -1723,7 +1723,10 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
         const int* ptr = A.ptr;
         const int* col = A.col;
         long long max_rounds = (long long)n + 4;
-        void* args[] = {&nn, &ptr, &col, &nbr, &pos, &S.cand, &S.mate, &S.list0, &S.list1, &S.mlist, &S.cnt,
+        // lanes per frontier vertex: 8, 16 or 32 by the mean row length
+        const double mean = n > 0 ? (double)A.nnz / n : 0.0;
+        int ngl = mean >= 48.0 ? 5 : (mean >= 16.0 ? 4 : 3);
+        void* args[] = {&nn, &ptr, &col, &nbr, &pos, &S.cand, &S.mate, &S.list0, &S.list1, &ngl, &S.cnt,
                         &max_rounds};
         CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)k_ld_persistent, dim3(h->coop_blocks), dim3(1024), args, 0,
                                                st));
