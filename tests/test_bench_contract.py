@@ -1,6 +1,8 @@
-"""bench.py's reference arm (the oracle timed on the host cores) on CPU: one
-JSON line with the contract's keys, printed by rank 0 only when launched as
-two ranks with torch.distributed.run (the other rank exits 0 without work)."""
+"""bench.py's host-side parts on CPU: the reference arm (the oracle timed on
+the host cores) prints one JSON line with the contract's keys, from rank 0
+only when launched as two ranks with torch.distributed.run (the other rank
+exits 0 without work); the clock sampler parses nvidia-smi's samples (a
+stand-in script here)."""
 import json
 import os
 import socket
@@ -34,3 +36,24 @@ def test_reference_arm_two_ranks_prints_one_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_sampler_parses_smi_samples(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi on PATH prints three samples, one of them with a
+    # power-cap reason active; the sampler reports their median and maximum
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1965, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2070, 2070, 940.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    sys.path.insert(0, ROOT)
+    import bench
+    import time
+    with bench.ClockSampler(0) as clk:
+        time.sleep(1.0)
+    s = clk.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not os.path.exists(clk.path)
