@@ -663,10 +663,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
+    torch.cuda.set_device(local)          # before the process group: NCCL binds this rank's GPU
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
     from paper_2006_16147_gb300 import amg
