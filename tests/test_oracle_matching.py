@@ -151,3 +151,46 @@ def _subgraph(A, edges):
     rp = np.zeros(n + 1, dtype=np.int64)
     np.add.at(rp, rows + 1, 1)
     return np.cumsum(rp), cols, d[rows, cols]
+
+
+def _ld_rounds_equal_weights(nx, ny, nz):
+    # Independent replay of the locally-dominant rounds for equal weights on
+    # the 7-point grid: every free vertex points to its smallest-index free
+    # neighbour (the (lo, hi) tiebreak), mutual pairs match, until no free
+    # vertex has a free neighbour.
+    n = nx * ny * nz
+    idx = np.arange(n)
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    nbrs = [(-nx * ny, k > 0), (-nx, j > 0), (-1, i > 0), (1, i < nx - 1), (nx, j < ny - 1), (nx * ny, k < nz - 1)]
+    mate = np.full(n, -1)
+    rounds = 0
+    while True:
+        free = mate < 0
+        cand = np.full(n, -1)
+        for off, ok in nbrs:
+            sel = ok & free & (cand < 0)
+            nb = idx[sel] + off
+            take = free[nb]
+            cand[idx[sel][take]] = nb[take]
+        c = np.where(cand >= 0, cand, idx)
+        mutual = free & (cand >= 0) & (c[c] == idx) & (idx < c)
+        if not mutual.any():
+            return mate, rounds
+        a, b = idx[mutual], c[mutual]
+        mate[a], mate[b] = b, a
+        rounds += 1
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (16, 16, 16), (10, 7, 5), (9, 4, 3)])
+def test_ld_rounds_match_an_independent_replay(orc, shape):
+    # pins the oracle's round count (the launch-pair GPU mode is compared
+    # against it) and its matching; on N^3 the rounds form a diagonal
+    # wavefront of 2.5 N - 2 rounds
+    A = W.poisson3d(*shape)
+    ld, rounds = orc.match_ld(A, np.ones(A.n))
+    mate, r = _ld_rounds_equal_weights(*shape)
+    assert rounds == r
+    assert np.array_equal(ld >= 0, mate >= 0)
+    assert np.array_equal(ld[mate >= 0], mate[mate >= 0])
+    if shape[0] == shape[1] == shape[2]:
+        assert rounds == 5 * shape[0] // 2 - 2
