@@ -207,3 +207,22 @@ def test_coarsest_cg_reaches_its_tolerance(orc):
     assert np.linalg.norm(b - A.scipy() @ x) <= 1e-4 * np.linalg.norm(b)
     # and it is a CG iterate, not the exact solution
     assert np.linalg.norm(b - A.scipy() @ x) > 1e-10 * np.linalg.norm(b)
+
+
+def test_three_sweeps_on_even_grid_give_2x2x2_cubes():
+    # Equal weights and the index tiebreak pair along x, then along y on the
+    # pairs' graph, then along z: every level-0 aggregate is a 2 x 2 x 2 cube
+    import oracle
+    oracle.build()
+    nx, ny, nz = 8, 6, 4
+    A = W.poisson3d(nx, ny, nz)
+    H = oracle.Hierarchy(A, max_coarse=1, max_levels=2)
+    agg = H.level(0).agg
+    idx = np.arange(A.n)
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    cube = (i // 2) + (nx // 2) * ((j // 2) + (ny // 2) * (k // 2))
+    assert H.sizes()[1][0] == A.n // 8
+    # the same partition (numbering aside): each cube is one aggregate and vice versa
+    pairs = set(zip(cube.tolist(), agg.tolist()))
+    assert len(pairs) == A.n // 8 == len(set(agg.tolist()))
+    assert np.allclose(H.level(0).p, 1.0 / np.sqrt(8.0), rtol=1e-15, atol=0)
