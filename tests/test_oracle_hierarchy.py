@@ -226,3 +226,27 @@ def test_three_sweeps_on_even_grid_give_2x2x2_cubes():
     pairs = set(zip(cube.tolist(), agg.tolist()))
     assert len(pairs) == A.n // 8 == len(set(agg.tolist()))
     assert np.allclose(H.level(0).p, 1.0 / np.sqrt(8.0), rtol=1e-15, atol=0)
+
+
+def test_coarse_laplacian_is_half_the_coarse_grid_laplacian():
+    # with 2 x 2 x 2 cubes and p = 1/sqrt(8), P^T A P has diagonal
+    # (8 * 6 - 2 * 12) / 8 = 3 and -4/8 towards each face neighbour: half
+    # the 7-point operator of the coarse grid, boundary rows included
+    import oracle
+    oracle.build()
+    nx, ny, nz = 8, 6, 4
+    A = W.poisson3d(nx, ny, nz)
+    H = oracle.Hierarchy(A, max_coarse=1, max_levels=2)
+    C = H.level_csr(1)
+    ref = W.poisson3d(nx // 2, ny // 2, nz // 2)
+    agg = H.level(0).agg
+    # coarse numbering: aggregate of the cube with the smallest member first
+    idx = np.arange(A.n)
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    cube = (i // 2) + (nx // 2) * ((j // 2) + (ny // 2) * (k // 2))
+    perm = np.empty(ref.n, dtype=np.int64)
+    perm[agg] = cube
+    Cd = C.to_dense()
+    Rd = 0.5 * ref.to_dense()[np.ix_(perm, perm)]
+    assert np.array_equal(Cd != 0, Rd != 0)
+    assert np.abs(Cd - Rd).max() <= 4e-16 * 3.0
