@@ -59,7 +59,10 @@ def _args():
                     help="1: autotuned launch shapes (timed once per shape, during warm-up)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-grid", type=int, default=128)
+    ap.add_argument("--cpu-sample-grid", type=int, default=0,
+                    help="grid of the CPU oracle baseline (0: the benchmarked grid itself, not scaled)")
+    ap.add_argument("--profile-steps", type=int, default=5,
+                    help="profiled steps after the timed region: per-kernel CUDA-event times and the roofline")
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: 5 cached hierarchies, Poisson arrivals, p50/p99 latency and solves/s")
     ap.add_argument("--serve-requests", type=int, default=60)
@@ -75,7 +78,7 @@ def _args():
 
 
 # DRAM traffic per row of the level-0 FP64 V-cycle kernels, from one ncu
-# capture on 3D Poisson 160^3 (profiles/ncu_traffic_pre_post_poisson160_fp64.md),
+# capture on 3D Poisson 160^3 (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid for the 7-point Poisson workload in FP64 and only while the kernel
 # source it was taken on is unchanged (checked by hash).
 _TRAFFIC = {
@@ -199,41 +202,88 @@ def _workload_name(args):
             ("_smoothedP" if args.smooth_p else "") + (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
 
 
-def _oracle_sample(grid, rtol, kind="poisson", flexible=False, cycle=0, smooth_w=0, smooth_p=False):
-    """Oracle (plain FP64, 1 thread) setup + PCG on a grid^3 instance of the workload."""
+def _host_info():
+    """Host cores, CPU model and compiler of the machine the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        cxx = subprocess.run(["g++", "--version"], capture_output=True, text=True, timeout=10).stdout.splitlines()[0]
+    except Exception:
+        cxx = ""
+    return {"host_cores": os.cpu_count(), "cpu_model": model, "compiler": cxx + " -O2 -ffp-contract=off"}
+
+
+def _oracle_run(A, b, rtol, flexible=False, cycle=0, smooth_w=0, smooth_p=False):
+    """Oracle (plain FP64, 1 thread) setup + PCG on (A, b); setup and solve timed separately."""
     import oracle
-    A, b = _workload(grid, kind)
     t0 = time.perf_counter()
     w = oracle.smooth_vector(A, np.ones(A.n), smooth_w) if smooth_w > 0 else None
     H = oracle.Hierarchy(A, w, cycle=cycle, smooth_p=smooth_p)
     t1 = time.perf_counter()
     x, info = H.pcg(b, rtol=rtol, flexible=flexible or cycle > 0)
     t2 = time.perf_counter()
-    return dict(setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"], n=A.n)
+    del H
+    return dict(setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"], n=A.n,
+                true_relres=info["true_relres"])
+
+
+def _oracle_kw(args):
+    return dict(flexible=args.krylov == 1, cycle=args.kdepth if args.cycle == "k" else 0,
+                smooth_w=args.smooth_w, smooth_p=bool(args.smooth_p))
+
+
+REF_BUDGET_S = 150.0   # timed full-size oracle steps stop once the next one would pass this
 
 
 def reference_arm(args):
+    """The CPU oracle timed on the full workload (no scaling), rank 0 only.
+
+    Warm-up steps run the oracle on the 32^3 instance of the same workload
+    (untimed; they load and exercise the code). Timed steps each run the
+    oracle's setup + PCG on the full-size instance; they stop after --steps or
+    once the next step would pass REF_BUDGET_S (at least one), and the line
+    reports the number actually run.
+    """
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    grid = min(args.grid, 64 if args.workload == "poisson" else 48)
-    n_full = args.grid ** 3
-    times = []
-    for k in range(args.warmup + args.steps):
-        r = _oracle_sample(grid, args.rtol, args.workload, args.krylov == 1,
-                           args.kdepth if args.cycle == "k" else 0, args.smooth_w, bool(args.smooth_p))
-        if k >= args.warmup:
-            times.append((r["setup_s"] + r["solve_s"]) * 1e3 * n_full / r["n"])
-    v = statistics.mean(times)
-    sample = (f"oracle setup + PCG to {args.rtol:g} on the {grid}^3 instance of the same workload "
-              f"({r['iterations']} iterations), scaled by unknowns x{n_full / r['n']:.0f}")
+    kw = _oracle_kw(args)
+    As, bs = _workload(min(32, args.grid), args.workload)
+    for _ in range(args.warmup):
+        _oracle_run(As, bs, args.rtol, **kw)
+    A, b = _workload(args.grid, args.workload)
+    runs = []
+    t_start = time.perf_counter()
+    while len(runs) < args.steps:
+        runs.append(_oracle_run(A, b, args.rtol, **kw))
+        step_s = runs[-1]["setup_s"] + runs[-1]["solve_s"]
+        if time.perf_counter() - t_start + step_s > REF_BUDGET_S:
+            break
+    wall_ms = (time.perf_counter() - t_start) * 1e3
+    v = statistics.mean((r["setup_s"] + r["solve_s"]) * 1e3 for r in runs)
+    host = _host_info()
+    sample = (f"oracle setup {statistics.mean(r['setup_s'] for r in runs):.2f} s + PCG "
+              f"{statistics.mean(r['solve_s'] for r in runs):.2f} s ({runs[-1]['iterations']} it) on the full "
+              f"{args.grid}^3 instance, {len(runs)} timed step(s) of {args.steps} requested (time budget "
+              f"{REF_BUDGET_S:.0f} s), not scaled; warm-up steps on the 32^3 instance")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": len(runs), "warmup": args.warmup, "steps_requested": args.steps, "ms_per_step": v,
+            "timed_wall_ms": wall_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
             "config": {"workload": _workload_name(args), "grid": args.grid, "rtol": args.rtol},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "setup_ms": statistics.mean(r["setup_s"] for r in runs) * 1e3,
+            "solve_ms": statistics.mean(r["solve_s"] for r in runs) * 1e3,
+            "iterations": runs[-1]["iterations"], "true_relres": runs[-1]["true_relres"],
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample, **host},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -702,24 +752,18 @@ def main():
     for _ in range(args.warmup):
         step()
 
-    # ---- timed region: K steps, CUDA events on the library's stream
+    # ---- timed region: K unprofiled steps, CUDA events on the library's stream
     infos = []
     hinfos = []
     barrier()
     launches0 = amg.amg_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kstats = {}
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for k in range(args.steps):
-            h, info = step(profile=1, keep=True)
+            h, info = step(profile=0, keep=True)
             infos.append(info)
             hinfos.append(amg.amg_hierarchy_info(h))
-            for name, (sc, kms, by) in amg.amg_kernel_stats(h).items():
-                s = kstats.setdefault(name, [0, 0.0, 0.0])
-                s[0] += sc
-                s[1] += kms
-                s[2] += by
             h.close()
         ev1.record(stream)
         barrier()
@@ -730,6 +774,25 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     clocks = clk.summary()
+
+    # ---- per-kernel times: a few more steps with the library's CUDA-event
+    # scopes around every kernel (on the launching stream), right after the
+    # timed region; they give the kernel table and the roofline
+    kstats = {}
+    psteps = max(1, min(args.profile_steps, args.steps))
+    pev0, pev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pev0.record(stream)
+    for k in range(psteps):
+        h, _ = step(profile=1, keep=True)
+        for name, (sc, kms, by) in amg.amg_kernel_stats(h).items():
+            st_ = kstats.setdefault(name, [0, 0.0, 0.0])
+            st_[0] += sc
+            st_[1] += kms
+            st_[2] += by
+        h.close()
+    pev1.record(stream)
+    torch.cuda.synchronize()
+    profiled_ms = pev0.elapsed_time(pev1) / psteps
 
     # residual check of the last solution (independent of the library)
     xs = d_x.cpu().numpy()
@@ -766,8 +829,9 @@ def main():
     roofline = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "traffic_source": ("ncu DRAM bytes on 160^3 scaled by rows" if traffic else None),
-                "bytes_per_launch": by_tot / nl, "ms_per_launch": per_launch_ms, "launches": nl // args.steps}
-    kernel_table = {k: {"launches_per_step": v[0] // args.steps, "ms_per_step": round(v[1] / args.steps, 4),
+                "bytes_per_launch": by_tot / nl, "ms_per_launch": per_launch_ms, "launches": nl // psteps,
+                "timing": f"CUDA events around every launch over {psteps} profiled steps after the timed region"}
+    kernel_table = {k: {"launches_per_step": v[0] // psteps, "ms_per_step": round(v[1] / psteps, 4),
                         "GBps": round(v[2] / max(v[1], 1e-12) / 1e6, 1) if v[2] else None}
                     for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
 
@@ -795,18 +859,23 @@ def main():
         h2d = A.row_ptr.nbytes + A.col.nbytes + A.val.nbytes + 8 * A.n * 3
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * A.n)}
 
-    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    # ---- CPU oracle baseline (rank 0, N = 1 only): the oracle as it stands on
+    # the same workload, once, setup and PCG timed separately
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         import oracle
         oracle.build()
-        g = min(args.cpu_sample_grid if args.workload == "poisson" else 48, args.grid)
-        r = _oracle_sample(g, args.rtol, args.workload, args.krylov == 1, args.kdepth if args.cycle == "k" else 0,
-                           args.smooth_w, bool(args.smooth_p))
+        g = args.cpu_sample_grid if args.cpu_sample_grid > 0 else args.grid
+        As, bs = (A, b) if g == args.grid else _workload(g, args.workload)
+        r = _oracle_run(As, bs, args.rtol, **_oracle_kw(args))
         scale = A.n / r["n"]
         cpu = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+               "setup_ms": r["setup_s"] * 1e3 * scale, "solve_ms": r["solve_s"] * 1e3 * scale,
+               "iterations": r["iterations"],
                "sample": (f"oracle setup {r['setup_s']:.2f} s + PCG {r['solve_s']:.2f} s ({r['iterations']} it) "
-                          f"on the {g}^3 instance of the same workload, scaled x{scale:.0f} by unknowns")}
+                          + (f"on the full {g}^3 instance, one run, not scaled" if scale == 1 else
+                             f"on the {g}^3 instance, scaled x{scale:.0f} by unknowns")),
+               **_host_info()}
 
     if rank == 0:
         it = [i["iterations"] for i in infos]
@@ -827,7 +896,11 @@ def main():
             "solve_ms": round(statistics.mean(i["solve_ms"] for i in infos), 3),
             "levels": hi["n"], "opc": round(hi["opc"], 4), "solves_per_s": round(world * 1e3 / ms, 3),
             "match_rounds": int(sum(sum(r) for r in hi["rounds"])),
-            "roofline": roofline, "kernels": kernel_table, "gpu_launches": int(launches), "accuracy": accuracy,
+            "roofline": roofline, "kernels": kernel_table, "profiled_ms_per_step": round(profiled_ms, 3),
+            "kernel_stats": f"CUDA events around every launch over {psteps} profiled steps after the timed "
+                            "region; the timed steps run unprofiled",
+            "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // args.steps),
+            "accuracy": accuracy,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

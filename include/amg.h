@@ -81,7 +81,10 @@ typedef struct {
                           setting of Section 5); use krylov = 1 then, as that solve is not a fixed operator */
     int keep_sweeps;   /* [0] keep every sweep's matching and aggregates for amg_export_sweep */
     int profile;       /* [0] time every kernel / setup phase with CUDA events (amg_kernel_stats) */
-    int match_kernel;  /* [0] matching rounds in one cooperative launch when possible; 1: a launch pair per round */
+    int match_kernel;  /* [0] how the locally-dominant matching of each sweep is computed (the same matching
+                          every way): 0 = proposals without rounds (Suitor method; hierarchy rounds report
+                          0); 1 = locally-dominant rounds, a launch pair per round; 2 = the same rounds in one
+                          cooperative launch when the device allows it (else as 1) */
     int krylov;        /* [0] 0 = PCG; 1 = flexible CG keeping one direction (FCG(1), the paper's outer
                           solver, Section 5), robust to a V-cycle that is not exactly linear (FP32) */
     int cycle;         /* [0] 0: V-cycle (Eq. 2). c >= 1: K-cycle on the first c coarse levels: on levels
@@ -260,18 +263,20 @@ amg_status amg_smooth_vector(const amg_csr* A, const double* w0, double* w, int 
 
 /*
  * Matching without allocation. The paper has no counterpart: this is a
- * service for callers that may not allocate device memory when they need a
- * matching -- code that runs while a stream is being captured into a CUDA
- * graph, applications that hand out all device memory from their own pool or
- * budget, and hosts that forbid allocation after start-up.
+ * service for callers that may not allocate device memory at the point where
+ * they need a matching -- applications that reserve all device memory at
+ * start-up and hand it out from their own pool or budget (a cudaMalloc there
+ * would fail or push another tenant out of memory), and latency-bound hosts
+ * that forbid allocation after start-up (cudaMalloc and cudaFree can
+ * synchronise the device and take an unbounded time).
  *
- * Computes the Eq. 3 weights of (A, w) and the locally-dominant matching with
- * the index tiebreak, exactly as the first sweep of amg_setup does, and
- * writes mate[i] (partner index, or -1 for an unmatched row) to the caller's
- * DEVICE array of length n. A and w are device arrays as for amg_setup;
- * `stream` is a cudaStream_t (NULL = legacy default stream); *rounds (host,
- * may be NULL) receives the number of matching rounds. The call returns after
- * the stream work has finished.
+ * Computes the same edge weights and the same locally-dominant matching with
+ * the index tiebreak as the first sweep of amg_setup, and writes mate[i]
+ * (partner index, or -1 for an unmatched row) to the caller's DEVICE array
+ * of length n. A and w are device arrays as for amg_setup; `stream` is a
+ * cudaStream_t (NULL = legacy default stream); *rounds (host, may be NULL)
+ * receives the number of matching rounds. The call reads counters back to
+ * the host and returns after the stream work has finished.
  *
  * The only working memory is a fixed array inside the library image
  * (about 5.5 MB of device memory on every GPU that loads the library, held
@@ -279,9 +284,10 @@ amg_status amg_smooth_vector(const amg_csr* A, const double* w0, double* w, int 
  * nnz <= AMG_NOALLOC_MAX_NNZ; larger inputs return AMG_ERR_TOO_LARGE before
  * any device work. The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress), so make that first call before any stream
- * capture begins. All calls share the one array: calls that overlap on the
- * GPU (other threads, other streams) race and must be serialised by the
- * caller. No cudaMalloc, cudaFree or other allocating routine is called.
+ * capture begins. All calls share the one array and every call clears the
+ * counters it needs: calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller. No cudaMalloc, cudaFree
+ * or other allocating routine is called.
  * Errors as amg_setup (validation codes), AMG_ERR_TIMEOUT, AMG_ERR_CUDA.
  */
 #define AMG_NOALLOC_MAX_N 65536

@@ -422,10 +422,11 @@ def amg_launch_count() -> int:
 def amg_match_noalloc(row_ptr, col, val, w, mate, stream=None) -> int:
     """Matching of (A, w) into the device tensor `mate` without any device allocation.
 
-    For callers that may not allocate when they need it (during stream capture,
-    under an external memory pool or budget). Uses the library's fixed scratch
-    array, so n <= NOALLOC_MAX_N and nnz <= NOALLOC_MAX_NNZ; calls must not
-    overlap on the GPU. Returns the number of matching rounds.
+    For callers that may not allocate when they need it (all device memory
+    reserved at start-up for their own pool or budget, or no allocation allowed
+    after start-up). Uses the library's fixed scratch array, so
+    n <= NOALLOC_MAX_N and nnz <= NOALLOC_MAX_NNZ; calls must not overlap on
+    the GPU. Returns the number of matching rounds.
     """
     n = int(row_ptr.shape[0] - 1)
     A = amg_csr(n, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val))

@@ -274,7 +274,7 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned epoch, int* 
 __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                              const double* __restrict__ c, double* __restrict__ sc, int* __restrict__ nbr,
                              int* __restrict__ pos, int* __restrict__ cand, int* mate, const int* __restrict__ list,
-                             const int* __restrict__ nlist) {
+                             const int* __restrict__ nlist, int* __restrict__ spos) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int nr = list ? *nlist : n;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nr; t += gridDim.x * blockDim.x) {
@@ -297,6 +297,8 @@ __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __re
             ++m;
         }
         for (int k = m; k < e; ++k) nbr[k] = -1;
+        if (spos)
+            for (int k = b; k < m; ++k) spos[find_in_row(ptr, col, v, nbr[k])] = k;
         pos[v] = b;
         cand[v] = m > b ? nbr[b] : -1;
         if (m == b) mate[v] = -2;
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __re
                                                          const int* __restrict__ col, const double* __restrict__ c,
                                                          int* __restrict__ nbr, int* __restrict__ pos,
                                                          int* __restrict__ cand, int* mate, int* __restrict__ long_list,
-                                                         int* __restrict__ nlong) {
+                                                         int* __restrict__ nlong, int* __restrict__ spos) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __re
         if (gl < len) {
             const int rank = edge ? better : nedge + nonedge_before;
             nbr[b + rank] = edge ? u : -1;
+            if (spos) spos[b + gl] = b + rank;
             if (edge && rank == 0) cand[v] = u;
         }
         if (gl == 0 && len >= 0 && v < n) {
@@ -385,7 +388,8 @@ __global__ void __launch_bounds__(LONG_TPB) k_sort_edges_long(const int* __restr
                                                               const int* __restrict__ col,
                                                               const double* __restrict__ c, int* __restrict__ nbr,
                                                               int* __restrict__ pos, int* __restrict__ cand, int* mate,
-                                                              int* __restrict__ longer, int* __restrict__ nlonger) {
+                                                              int* __restrict__ longer, int* __restrict__ nlonger,
+                                                              int* __restrict__ spos) {
     extern __shared__ long long esm[];
     long long* WK = esm;
     int* U = reinterpret_cast<int*>(esm + CAP);
@@ -432,7 +436,10 @@ __global__ void __launch_bounds__(LONG_TPB) k_sort_edges_long(const int* __restr
                 }
                 __syncthreads();
             }
-        for (int s = tid; s < len; s += LONG_TPB) nbr[b + s] = U[s] != 0x7fffffff ? U[s] : -1;
+        for (int s = tid; s < len; s += LONG_TPB) {
+            nbr[b + s] = U[s] != 0x7fffffff ? U[s] : -1;
+            if (spos && U[s] != 0x7fffffff) spos[find_in_row(ptr, col, v, U[s])] = b + s;
+        }
         if (tid == 0) {
             pos[v] = b;
             const bool any = len > 0 && U[0] != 0x7fffffff;
@@ -627,6 +634,98 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
         if (__ldcg(err)) return;
         if (leader && __ldcg(cnt + (int)(r % 3)) > 0) cnt[8] += 1;
         ++r;
+    }
+}
+
+// ------------------------------------------------ matching by proposals ---
+// The same matching without rounds: every vertex proposes to its best
+// neighbour (first in its sorted list) that would take it, displacing that
+// neighbour's current suitor if the new proposal ranks higher; a displaced
+// vertex proposes again further down its own list. With a strict order on
+// the edges this ends in the greedy matching on that order, which is the
+// locally-dominant matching the rounds compute (each vertex is matched to
+// its suitor exactly when they are each other's suitor). The algorithm is
+// the Suitor method of Manne and Halappanavar (IPDPS 2014).
+//
+// A proposal of cur at sorted position k of its row, to v = nbr[k], is the
+// position q = mpos[k] of cur in v's sorted row: for a fixed v, positions
+// order v's edges exactly as the strict order does, so suitor[v] (the
+// smallest position proposed and not displaced, INT_MAX for none) is one
+// int and one atomicMin decides each proposal. Suitor values only decrease,
+// so a vertex never has to look back up its list: a displaced vertex y
+// resumes right after v, at mpos[old] + 1 in its own row. No thread waits
+// on another, and each vertex's list position only moves forward, so the
+// work is bounded by the entry count.
+//
+// mpos[s] for every sorted edge position s of row v: the sorted position of
+// v in the row of u = nbr[s]. spos[k] maps an original CSR position to its
+// sorted position (written by the edge sorts). Also resets suitor[].
+__global__ void k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const double* __restrict__ c, const int* __restrict__ spos, int* __restrict__ mpos,
+                             int* __restrict__ suitor, int* err) {
+    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        suitor[v] = 0x7fffffff;
+        const int e = ptr[v + 1];
+        for (int k = ptr[v]; k < e; ++k) {
+            if (c[k] == NEG_INF) continue;          // not an edge (diagonal, zero pair)
+            const int u = col[k];
+            const int km = find_in_row(ptr, col, u, v);
+            if (km < 0) {                            // no mirror entry: pattern not symmetric
+                mpos[spos[k]] = -1;
+                atomicOr(err, 1);
+                continue;
+            }
+            mpos[spos[k]] = spos[km];
+        }
+    }
+}
+
+// One thread per vertex: its chain of proposals, and those of the vertices
+// it displaces. err |= 2 if a thread takes more steps than there are
+// entries (impossible for a valid mirror map; a guard, not a wait).
+__global__ void __launch_bounds__(256) k_suitor(int n, long long nnz, const int* __restrict__ ptr,
+                                                const int* __restrict__ nbr, const int* __restrict__ mpos,
+                                                int* suitor, int* err) {
+    const int u0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u0 >= n) return;
+    int k = __ldg(ptr + u0), e = __ldg(ptr + u0 + 1);
+    long long steps = 0;
+    for (;;) {
+        if (k >= e) return;
+        const int v = __ldg(nbr + k);
+        if (v < 0) return;                           // the row's edges are exhausted: unmatched so far
+        const int q = __ldg(mpos + k);
+        if (++steps > nnz || q < 0) {
+            atomicOr(err, 2);
+            return;
+        }
+        const int old = atomicMin(suitor + v, q);
+        if (old < q) {                               // v holds a better proposal: next candidate
+            ++k;
+            continue;
+        }
+        if (old == 0x7fffffff) return;              // first suitor of v: this chain ends
+        // old's vertex y is displaced; it continues after v in its own row
+        const int y = __ldg(nbr + old);
+        k = __ldg(mpos + old) + 1;
+        e = __ldg(ptr + y + 1);
+    }
+}
+
+// mate[v] = the vertex at v's suitor position, -1 without a suitor; the
+// relation must be mutual (err |= 4 otherwise).
+__global__ void k_suitor_mate(int n, const int* __restrict__ nbr, const int* __restrict__ mpos,
+                              const int* __restrict__ suitor, int* __restrict__ mate, int* err) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int s = suitor[v];
+        if (s == 0x7fffffff) {
+            mate[v] = -1;
+            continue;
+        }
+        const int u = nbr[s];
+        mate[v] = u;
+        if (suitor[u] != mpos[s]) atomicOr(err, 4);
     }
 }
 
@@ -1635,6 +1734,8 @@ struct Scratch {
     int* off = nullptr;       // n + 1
     int* skey = nullptr;      // nnz
     double* sval = nullptr;   // nnz
+    int* spos = nullptr;      // nnz: sorted position of each entry (matching by proposals)
+    int* mpos = nullptr;      // nnz: mirror's sorted position per sorted entry
     long long cap_nnz = 0;    // entries c, skey and sval hold
     int* scan_tmp = nullptr;
     int* host = nullptr;      // pinned
@@ -1679,46 +1780,74 @@ void launch_rows_long(amg_hierarchy* h, Scratch& S, int nrows, const int* list, 
     KERNEL_CHECK();
 }
 
-// Locally-dominant matching by frontier rounds. Returns the number of rounds.
-// All rounds run in one cooperative launch when the device allows it; else
-// each round is one launch pair with a host check every 16 rounds.
+// Each row's edges sorted by the strict edge order into nbr (S.skey), the
+// position pointer pos (S.flag), first candidates and isolated vertices; with
+// spos set, also the sorted position of every original entry.
+void sort_edges(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* spos) {
+    cudaStream_t st = h->stream;
+    const int n = A.n;
+    int* nbr = S.skey;
+    double* sc = S.sval;
+    int* pos = S.flag;
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 9, 0, sizeof(int), st));
+    const int G = rows_group(A.nnz, n);
+    const int gblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
+    if (G == 8)
+        k_sort_edges_group<8><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                       S.cnt + 9, spos);
+    else if (G == 16)
+        k_sort_edges_group<16><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                        S.cnt + 9, spos);
+    else
+        k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
+                                                        S.cnt + 9, spos);
+    KERNEL_CHECK();
+    // long rows: a block each in two capacities, then a thread each
+    constexpr int eb = (int)(sizeof(long long) + sizeof(int));
+    CUDA_CHECK(cudaFuncSetAttribute(k_sort_edges_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    EDGE_CAPS[1] * eb));
+    k_sort_edges_long<<<h->num_sms * 4, LONG_TPB, EDGE_CAPS[0] * eb, st>>>(
+        S.list1, S.cnt + 9, EDGE_CAPS[0], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.qid, S.cnt + 13, spos);
+    KERNEL_CHECK();
+    k_sort_edges_long<<<h->num_sms, LONG_TPB, EDGE_CAPS[1] * eb, st>>>(
+        S.qid, S.cnt + 13, EDGE_CAPS[1], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.heads, S.cnt + 14, spos);
+    KERNEL_CHECK();
+    k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate, S.heads,
+                                                 S.cnt + 14, spos);
+    KERNEL_CHECK();
+}
+
+// The matching of one sweep into S.mate (partner, or < 0 unmatched).
+// Returns the number of locally-dominant rounds (0 for the proposal method,
+// which has none). match_kernel 0: proposals (k_suitor); 1: one launch pair
+// per round with a host check every 16 rounds; 2: all rounds in one
+// cooperative launch when the device allows it (else as 1).
 int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
     cudaStream_t st = h->stream;
     const int n = A.n;
     CUDA_CHECK(cudaMemsetAsync(S.mate, 0xff, sizeof(int) * n, st));   // all -1
-    if (h->opt.match_kernel == 0 && h->coop_blocks > 0) {
-        int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
-        double* sc = S.sval;
-        int* pos = S.flag;
-        CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 64, st));
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 9, 0, sizeof(int), st));
-        const int G = rows_group(A.nnz, n);
-        const int gblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
-        if (G == 8)
-            k_sort_edges_group<8><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                           S.cnt + 9);
-        else if (G == 16)
-            k_sort_edges_group<16><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                            S.cnt + 9);
-        else
-            k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                            S.cnt + 9);
+    if (h->opt.match_kernel == 0) {
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 4 * sizeof(int), st));   // [13, 14] long-row lists, [16] error
+        sort_edges(h, S, A, S.spos);
+        int* err = S.cnt + 16;
+        k_mirror_pos<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mpos, S.cand, err);
         KERNEL_CHECK();
-        {
-            // long rows: a block each in two capacities, then a thread each
-            constexpr int eb = (int)(sizeof(long long) + sizeof(int));
-            CUDA_CHECK(cudaFuncSetAttribute(k_sort_edges_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            EDGE_CAPS[1] * eb));
-            k_sort_edges_long<<<h->num_sms * 4, LONG_TPB, EDGE_CAPS[0] * eb, st>>>(
-                S.list1, S.cnt + 9, EDGE_CAPS[0], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.qid, S.cnt + 13);
-            KERNEL_CHECK();
-            k_sort_edges_long<<<h->num_sms, LONG_TPB, EDGE_CAPS[1] * eb, st>>>(
-                S.qid, S.cnt + 13, EDGE_CAPS[1], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.heads, S.cnt + 14);
+        if (n > 0) {
+            k_suitor<<<(n + 255) / 256, 256, 0, st>>>(n, (long long)A.nnz, A.ptr, S.skey, S.mpos, S.cand, err);
             KERNEL_CHECK();
         }
-        k_sort_edges<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, sc, nbr, pos, S.cand, S.mate, S.heads,
-                                                     S.cnt + 14);
+        k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.skey, S.mpos, S.cand, S.mate, err);
         KERNEL_CHECK();
+        const int e = read_int(err, S.host, st);
+        if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
+        if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
+        return 0;
+    }
+    if (h->opt.match_kernel == 2 && h->coop_blocks > 0) {
+        int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
+        int* pos = S.flag;
+        CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 64, st));
+        sort_edges(h, S, A, nullptr);
         int nn = n;
         const int* ptr = A.ptr;
         const int* col = A.col;
@@ -1924,9 +2053,13 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.mem.release(S.c);
     S.mem.release(S.skey);
     S.mem.release(S.sval);
+    S.mem.release(S.spos);
+    S.mem.release(S.mpos);
     S.c = S.mem.alloc<double>(nnz);
     S.skey = S.mem.alloc<int>(nnz);
     S.sval = S.mem.alloc<double>(nnz);
+    S.spos = S.mem.alloc<int>(nnz);
+    S.mpos = S.mem.alloc<int>(nnz);
     S.cap_nnz = nnz;
 }
 
@@ -2155,6 +2288,8 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.off = S.mem.alloc<int>(n0 + 2);
     S.skey = S.mem.alloc<int>(nnz0);
     S.sval = S.mem.alloc<double>(nnz0);
+    S.spos = S.mem.alloc<int>(nnz0);
+    S.mpos = S.mem.alloc<int>(nnz0);
     S.cap_nnz = nnz0;
     S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
 
@@ -2453,14 +2588,15 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
 // ---------------------------------------------------------------------------
 // Matching without any allocation (amg_match_noalloc).
 //
-// Some callers cannot call cudaMalloc at the point where they need a matching:
-// code running while a stream is being captured into a CUDA graph, callers
-// that own all device memory through their own pool or budget, and hosts that
-// forbid allocation after start-up. For them this entry point computes the
-// Eq. 3 weights and the locally-dominant matching of one matrix using only a
-// fixed scratch area that is part of the library image (a file-scope
-// __device__ array, resident on every GPU that loads the library until the
-// process exits). The caller passes A, w and the output array.
+// Some callers cannot call cudaMalloc at the point where they need a
+// matching: applications that reserve all device memory at start-up and hand
+// it out from their own pool or budget, and latency-bound hosts that forbid
+// allocation after start-up (cudaMalloc and cudaFree can synchronise the
+// device). For them this entry point computes the same edge weights and
+// locally-dominant matching as the first sweep of amg_setup using only a fixed
+// scratch area that is part of the library image (a file-scope __device__
+// array, resident on every GPU that loads the library until the process
+// exits). The caller passes A, w and the output array.
 // ---------------------------------------------------------------------------
 namespace {
 

@@ -30,3 +30,14 @@ def vcycle(h, r):
     amg.amg_vcycle(h, dev(r), z)
     torch.cuda.synchronize()
     return z.cpu().numpy()
+
+
+def assert_same_solution(H, b, xg, ig, xo, io, flexible=False, tol=1e-10):
+    """The GPU solution equals the oracle's to `tol` relative, whatever the
+    iteration counts. When the counts differ (by one, near the stop test),
+    the oracle is run again for exactly the GPU's number of iterations
+    (rtol = 0 never stops it earlier), so the same iterate is compared."""
+    ref = xo
+    if ig["iterations"] != io["iterations"]:
+        ref, _ = H.pcg(b, rtol=0.0, maxit=ig["iterations"], flexible=flexible)
+    assert np.linalg.norm(xg - ref) <= tol * np.linalg.norm(ref), (ig["iterations"], io["iterations"])

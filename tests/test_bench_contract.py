@@ -1,5 +1,6 @@
 """bench.py's host-side parts on CPU: the reference arm (the oracle timed on
-the host cores) prints one JSON line with the contract's keys, from rank 0
+the host cores, on the full instance of the workload it names, here 40^3)
+prints one JSON line with the contract's keys and the steps it ran, from rank 0
 only when launched as two ranks with torch.distributed.run (the other rank
 exits 0 without work); the clock sampler parses nvidia-smi's samples (a
 stand-in script here)."""
@@ -21,7 +22,7 @@ def _free_port():
 def test_reference_arm_two_ranks_prints_one_line():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3", "--grid", "40"]
     out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -29,10 +30,12 @@ def test_reference_arm_two_ranks_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "ms" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["ms_per_step"] == d["value"] and d["n_gpus"] == 2
-    assert d["steps"] == 1 and d["warmup"] == 3
-    assert d["config"]["workload"].startswith("poisson3d_256^3")
+    assert d["steps"] == 2 and d["steps_requested"] == 2 and d["warmup"] == 3
+    assert d["timed_wall_ms"] >= d["steps"] * d["ms_per_step"] * 0.999
+    assert d["config"]["workload"].startswith("poisson3d_40^3")
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host_cores"] >= 1 and "not scaled" in cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

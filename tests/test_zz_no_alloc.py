@@ -1,14 +1,20 @@
-"""The allocation-free matching entry point agrees with amg_setup's own first
-matching sweep.
+"""The allocation-free matching entry point (amg_match_noalloc) against the
+oracle's greedy matching and against amg_setup's own first matching sweep.
 
 amg_match_noalloc exists for callers that may not allocate device memory
-when they need a matching (during CUDA-graph stream capture, or under an
-external memory pool or budget); it works in a fixed scratch array inside the
-library. Matchings are compared bit for bit, like every matching test here.
-The calls are made back to back on different inputs and then repeated, so a
-stale counter or list left in the shared scratch array by the previous call
-would show up as a mismatch. This file is collected last on purpose.
+when they need a matching: applications that reserve all device memory at
+start-up for their own pool or budget, and hosts that forbid allocation after
+start-up (cudaMalloc can synchronise the device). It works in a fixed scratch
+array inside the library. Matchings are compared bit for bit, like every
+matching test here. The calls are made back to back on different inputs and
+then repeated, so a stale counter or list left in the shared scratch array by
+the previous call would show up as a mismatch. The device's default memory
+pool (where the library's stream-ordered allocations come from) and torch's
+allocator are read before and after the calls: neither may grow. This file is
+collected last on purpose.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -17,6 +23,35 @@ from paper_2006_16147_gb300 import workloads as W
 from gpu_util import dev, setup
 
 pytestmark = pytest.mark.gpu
+
+_RESERVED_CURRENT, _USED_CURRENT, _USED_HIGH = 0x5, 0x7, 0x8   # cudaMemPoolAttr values (driver_types.h)
+
+
+def _cudart():
+    for line in open("/proc/self/maps"):
+        path = line.split()[-1]
+        if "libcudart.so" in path:
+            return ctypes.CDLL(path)
+    return ctypes.CDLL("libcudart.so")
+
+
+class _DefaultPool:
+    """Reads the attributes of the current device's default memory pool."""
+
+    def __init__(self):
+        import torch
+        self.rt = _cudart()
+        self.pool = ctypes.c_void_p()
+        assert self.rt.cudaDeviceGetDefaultMemPool(ctypes.byref(self.pool), torch.cuda.current_device()) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        z = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolSetAttribute(self.pool, _USED_HIGH, ctypes.byref(z)) == 0
 
 
 def _reference_mate(A, w):
@@ -28,37 +63,50 @@ def _reference_mate(A, w):
     return m, rounds
 
 
-def _noalloc_mate(A, w):
+def _inputs():
+    rng = np.random.default_rng(11)
+    A1 = W.random_spd(3000, 0.003, 5)
+    w1 = rng.uniform(0.5, 2.0, 3000) * rng.choice([-1.0, 1.0], 3000)
+    return [(W.poisson3d(32), np.ones(32 ** 3)), (A1, w1), (W.varcoef3d(20, seed=4), np.ones(20 ** 3))]
+
+
+def test_noalloc_matching_equals_oracle_and_setup_sweep_without_allocating(orc):
     import torch
     from paper_2006_16147_gb300 import amg
-    mate = torch.full((A.n,), 7, dtype=torch.int32, device="cuda:0")
-    rounds = amg.amg_match_noalloc(dev(A.row_ptr), dev(A.col), dev(A.val), dev(w), mate)
-    torch.cuda.synchronize()
-    return mate.cpu().numpy(), rounds
-
-
-def test_noalloc_matching_equals_setup_sweep_on_consecutive_calls():
-    rng = np.random.default_rng(11)
-    inputs = [
-        (W.poisson3d(32), np.ones(32 ** 3)),
-        (W.random_spd(3000, 0.003, 5), None),
-        (W.varcoef3d(20, seed=4), np.ones(20 ** 3)),
-    ]
-    inputs[1] = (inputs[1][0], rng.uniform(0.5, 2.0, 3000) * rng.choice([-1.0, 1.0], 3000))
+    inputs = _inputs()
+    oracle_mates = [orc.match_greedy(A, w) for A, w in inputs]
     refs = [_reference_mate(A, w) for A, w in inputs]
+    # device copies of every input and output before any measurement
+    args = [(dev(A.row_ptr), dev(A.col), dev(A.val), dev(w)) for A, w in inputs]
+    mates = [torch.full((A.n,), 7, dtype=torch.int32, device="cuda:0") for A, _ in inputs]
+    amg.amg_match_noalloc(*args[0], mates[0])        # first call on this device: looks up the array
+    torch.cuda.synchronize()
+    pool = _DefaultPool()
+    used0, reserved0 = pool.get(_USED_CURRENT), pool.get(_RESERVED_CURRENT)
+    torch_alloc0 = torch.cuda.memory_allocated()
+    pool.reset_high()
     # two passes over the inputs: every call follows a call on a different matrix
     for _ in range(2):
-        for (A, w), (ref, ref_rounds) in zip(inputs, refs):
-            got, rounds = _noalloc_mate(A, w)
+        for a, m, om, (ref, ref_rounds) in zip(args, mates, oracle_mates, refs):
+            m.fill_(7)
+            rounds = amg.amg_match_noalloc(*a, m)
+            torch.cuda.synchronize()
+            got = m.cpu().numpy()
+            assert np.array_equal(got, np.where(om >= 0, om, -1))
             assert np.array_equal(got, ref)
             assert rounds == ref_rounds
+    torch.cuda.synchronize()
+    assert pool.get(_USED_CURRENT) == used0
+    assert pool.get(_RESERVED_CURRENT) == reserved0
+    assert pool.get(_USED_HIGH) <= used0
+    assert torch.cuda.memory_allocated() == torch_alloc0
 
 
 def test_noalloc_rejects_sizes_beyond_the_limit():
+    import torch
     from paper_2006_16147_gb300 import amg
     A = W.poisson3d(41)                      # n = 68921 > 65536
     assert A.n > amg.NOALLOC_MAX_N
-    import torch
     mate = torch.empty(A.n, dtype=torch.int32, device="cuda:0")
     with pytest.raises(amg.AmgError) as e:
         amg.amg_match_noalloc(dev(A.row_ptr), dev(A.col), dev(A.val), dev(np.ones(A.n)), mate)
