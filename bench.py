@@ -46,6 +46,10 @@ def _args():
                          "aniso3d: -(100 u_xx + 100 u_yy + u_zz)")
     ap.add_argument("--smooth-p", type=int, default=0, choices=[0, 1],
                     help="1: smoothed prolongator Pbar = (I - omega D^-1 A) P (the paper's VA3 setting)")
+    ap.add_argument("--pre", type=int, default=1, help="l1-Jacobi sweeps before the coarse correction")
+    ap.add_argument("--post", type=int, default=1, help="l1-Jacobi sweeps after the coarse correction")
+    ap.add_argument("--omega-rule", type=int, default=0, choices=[0, 1],
+                    help="smoothed prolongator weight: 0 = 4 / (3 ||D^-1 A||), 1 = 1 / ||D^-1 A|| (the text's)")
     ap.add_argument("--smooth-w", type=int, default=0,
                     help="> 0: w = that many l1-Jacobi sweeps on A w = 0 from ones (amg_smooth_vector, inside the step)")
     ap.add_argument("--krylov", type=int, default=0, help="0 PCG, 1 flexible CG")
@@ -199,7 +203,9 @@ def _workload_name(args):
             "varcoef": f"varcoef3d_{args.grid}^3_sigma2_{args.precision}vcycle",
             "aniso3d": f"aniso3d_{args.grid}^3_k100-100-1_{args.precision}vcycle"}[args.workload]
     return (base + "_setup+solve" + (f"_kcycle{args.kdepth}" if args.cycle == "k" else "") +
-            ("_smoothedP" if args.smooth_p else "") + (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
+            ("_smoothedP" if args.smooth_p else "") + ("_omega1/eta" if args.smooth_p and args.omega_rule else "") +
+            (f"_l1jacobi{args.pre}+{args.post}" if (args.pre, args.post) != (1, 1) else "") +
+            (f"_smoothw{args.smooth_w}" if args.smooth_w > 0 else ""))
 
 
 def _host_info():
@@ -220,12 +226,12 @@ def _host_info():
     return {"host_cores": os.cpu_count(), "cpu_model": model, "compiler": cxx + " -O2 -ffp-contract=off"}
 
 
-def _oracle_run(A, b, rtol, flexible=False, cycle=0, smooth_w=0, smooth_p=False):
+def _oracle_run(A, b, rtol, flexible=False, cycle=0, smooth_w=0, smooth_p=False, pre=1, post=1, omega_rule=0):
     """Oracle (plain FP64, 1 thread) setup + PCG on (A, b); setup and solve timed separately."""
     import oracle
     t0 = time.perf_counter()
     w = oracle.smooth_vector(A, np.ones(A.n), smooth_w) if smooth_w > 0 else None
-    H = oracle.Hierarchy(A, w, cycle=cycle, smooth_p=smooth_p)
+    H = oracle.Hierarchy(A, w, cycle=cycle, smooth_p=smooth_p, pre=pre, post=post, omega_rule=omega_rule)
     t1 = time.perf_counter()
     x, info = H.pcg(b, rtol=rtol, flexible=flexible or cycle > 0)
     t2 = time.perf_counter()
@@ -236,7 +242,8 @@ def _oracle_run(A, b, rtol, flexible=False, cycle=0, smooth_w=0, smooth_p=False)
 
 def _oracle_kw(args):
     return dict(flexible=args.krylov == 1, cycle=args.kdepth if args.cycle == "k" else 0,
-                smooth_w=args.smooth_w, smooth_p=bool(args.smooth_p))
+                smooth_w=args.smooth_w, smooth_p=bool(args.smooth_p), pre=args.pre, post=args.post,
+                omega_rule=args.omega_rule)
 
 
 REF_BUDGET_S = 150.0   # timed full-size oracle steps stop once the next one would pass this
@@ -737,7 +744,8 @@ def main():
              if args.smooth_w > 0 else d_w)
         h = amg.amg_setup(d_ptr, d_col, d_val, w, precision=prec, profile=profile, krylov=args.krylov,
                           autotune=args.autotune, cycle=args.kdepth if args.cycle == "k" else 0,
-                          smooth_p=args.smooth_p, stream=stream.cuda_stream)
+                          smooth_p=args.smooth_p, pre=args.pre, post=args.post, omega_rule=args.omega_rule,
+                          stream=stream.cuda_stream)
         info = amg.amg_solve(h, d_b, d_x, rtol=args.rtol, maxit=1000)
         if keep:
             return h, info
@@ -801,7 +809,8 @@ def main():
     # ---- accuracy of a mixed-precision or non-default run: error against an
     # FP64 solve of the same system to rel-res 1e-10, and iterations at 1e-8
     accuracy = None
-    if args.precision == "fp32" or args.workload != "poisson" or args.cycle == "k" or args.smooth_p:
+    if (args.precision == "fp32" or args.workload != "poisson" or args.cycle == "k" or args.smooth_p
+            or (args.pre, args.post) != (1, 1)):
         accuracy = {}
         h64 = amg.amg_setup(d_ptr, d_col, d_val, d_w, stream=stream.cuda_stream)
         xr = torch.zeros_like(d_x)
@@ -810,6 +819,7 @@ def main():
         for tol in (args.rtol, 1e-8):
             hh = amg.amg_setup(d_ptr, d_col, d_val, d_w, precision=prec, krylov=args.krylov,
                                cycle=args.kdepth if args.cycle == "k" else 0, smooth_p=args.smooth_p,
+                               pre=args.pre, post=args.post, omega_rule=args.omega_rule,
                                stream=stream.cuda_stream)
             xt = torch.zeros_like(d_x)
             inf = amg.amg_solve(hh, d_b, xt, rtol=tol, maxit=2000)
@@ -843,15 +853,15 @@ def main():
         xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
         e2e_steps = max(1, min(3, args.steps))
         kc = args.kdepth if args.cycle == "k" else 0
-        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
-                                   cycle=kc, smooth_p=args.smooth_p)
+        hopt = dict(precision=prec, krylov=args.krylov, cycle=kc, smooth_p=args.smooth_p, pre=args.pre,
+                    post=args.post, omega_rule=args.omega_rule)
+        amg_h = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], **hopt)
         amg_h.close()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             xh[:] = 0.0
-            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], precision=prec, krylov=args.krylov,
-                                    cycle=kc, smooth_p=args.smooth_p)
+            hh = amg.amg_setup_host(hp["ptr"], hp["col"], hp["val"], hp["w"], **hopt)
             amg.amg_solve_host(hh, hp["b"], xh, rtol=args.rtol, maxit=1000)
             hh.close()
         barrier()
@@ -887,7 +897,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": _workload_name(args),
                        "grid": args.grid, "cycle": args.cycle, "kdepth": args.kdepth if args.cycle == "k" else None,
-                       "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": "l1-jacobi 1+1",
+                       "n": A.n, "nnz": A.nnz, "rtol": args.rtol, "sweeps": 3, "smoother": f"l1-jacobi {args.pre}+{args.post}",
                        "coarse": "dense cholesky", "l2": "inputs (1.4 GB) larger than L2, no flush",
                        "precision": args.precision, "autotune": args.autotune,
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -95,15 +95,18 @@ typedef struct {
                           preconditioner is then not linear, so the outer solver is flexible CG whatever
                           `krylov` says. Requires pre = post = 1; single right-hand-side solves only */
     int smooth_p;      /* [0] 1: smoothed prolongator Pbar = (I - omega D^-1 A) P on every level, omega =
-                          4 / (3 ||D^-1 A||_inf), coarse matrices Pbar^T A Pbar (Section 3.2; the paper's VA3
-                          setting, with the weight that reproduces its smoothed-aggregation constants). V-cycle
-                          (cycle = 0), pre = post = 1, single right-hand-side solves only. A row of A Pbar or
+                          4 / (3 ||D^-1 A||_inf) (see omega_rule), coarse matrices Pbar^T A Pbar (Section 3.2;
+                          the paper's VA3 setting; its GPU runs use l1-Jacobi with pre = post = 4). V-cycle
+                          (cycle = 0), any pre/post, single right-hand-side solves only. A row of A Pbar or
                           of Pbar^T A Pbar may hold up to 8192 entries (else AMG_ERR_TOO_LARGE); the
                           environment variable AMG_SPGEMM_CAP_SHIFT = k (0..3) divides that limit and the
                           product's internal capacity tiers by 2^k, so small tests reach every tier */
     int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */
+    int omega_rule;    /* [0] prolongator smoothing weight of smooth_p: 0 = 4 / (3 ||D^-1 A||_inf), the weight
+                          that reproduces the paper's smoothed-aggregation convergence constants; 1 =
+                          1 / ||D^-1 A||_inf, the weight the text of Section 3.2 states */
     double min_ratio;  /* [1.5] stop coarsening after a level with n_l / n_{l+1} below this (stalled matching) */
     void* stream;      /* [NULL] cudaStream_t for every device operation and for the hierarchy's stream-ordered
                           allocations; NULL = legacy default. Must stay valid until amg_free */

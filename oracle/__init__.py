@@ -51,7 +51,8 @@ def lib():
             L.orc_setup_seg.restype = ctypes.c_void_p
             L.orc_setup_seg.argtypes = [ctypes.c_int, _i32p, _i32p, _f64p, _f64p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int, _ip]
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int, ctypes.c_int,
+                                        _ip]
             L.orc_level_pbar_nnz.restype = ctypes.c_int64
             L.orc_level_pbar_nnz.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_level_pbar.restype = ctypes.c_double
@@ -143,7 +144,7 @@ class Hierarchy:
     """Oracle hierarchy: setup in the constructor, then V-cycle and PCG."""
 
     def __init__(self, A, w=None, sweeps=3, max_coarse=200, max_levels=32, pre=1, post=1, omega=1.0,
-                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None, cycle=0, smooth_p=False):
+                 use_ld=False, min_ratio=1.5, max_dense=4096, seg=None, cycle=0, smooth_p=False, omega_rule=0):
         rp, cl, vl = _csr_args(A)
         w = np.ones(A.n) if w is None else np.ascontiguousarray(w, dtype=np.float64)
         st = ctypes.c_int(0)
@@ -151,7 +152,7 @@ class Hierarchy:
         self._h = lib().orc_setup_seg(A.n, _p(rp, _i32p), _p(cl, _i32p), _p(vl, _f64p), _p(w, _f64p), sweeps,
                                       max_coarse, max_levels, pre, post, float(omega), int(use_ld), float(min_ratio),
                                       int(max_dense), 0 if seg is None else len(sg) - 1, _p(sg, _i32p),
-                                      int(smooth_p), ctypes.byref(st))
+                                      int(smooth_p), int(omega_rule), ctypes.byref(st))
         if not self._h:
             raise OracleError(f"orc_setup failed: {st.value}")
         lib().orc_set_cycle(self._h, int(cycle))

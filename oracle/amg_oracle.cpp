@@ -292,15 +292,17 @@ struct Hierarchy {
     int smooth_p = 0;              // 1: smoothed prolongator Pbar = (I - omega D^-1 A) P (Section 3.2)                // c > 0: K-cycle, two FCG iterations as the coarse correction on levels 1..c
     double omega = 1.0;
     int use_ld = 0;
+    int omega_rule = 0;            // prolongator smoothing weight: 0 = 4 / (3 eta), 1 = 1 / eta
 };
 
 // ------------------------------- smoothed prolongator (Section 3.2) -------
 // Pbar = (I - omega D^-1 A) P with D = diag(A). The paper's text takes
 // omega = 1 / ||D^-1 A||_inf; its table of two-level constants for the
 // smoothed prolongator is reproduced with 4/3 of that (2/3 on the Laplacian),
-// the reading taken here: omega = 4 / (3 eta), eta = max_i sum_j |a_ij| / a_ii
-// (each row's sum in column order, one division per row).
-double smoothing_weight(const Csr& A) {
+// the default reading here (rule 0): omega = 4 / (3 eta), eta = max_i
+// sum_j |a_ij| / a_ii (each row's sum in column order, one division per
+// row). Rule 1 is the text's omega = 1 / eta.
+double smoothing_weight(const Csr& A, int rule) {
     double eta = 0.0;
     for (int i = 0; i < A.n; ++i) {
         double s = 0.0, d = 0.0;
@@ -310,7 +312,7 @@ double smoothing_weight(const Csr& A) {
         }
         eta = std::max(eta, s / d);
     }
-    return 4.0 / (3.0 * eta);
+    return rule == 1 ? 1.0 / eta : 4.0 / (3.0 * eta);
 }
 
 // Row i of A P (P: one nonzero p_j in column agg_j per row): the terms
@@ -519,7 +521,7 @@ int build(Hierarchy& H, const Csr& A0, const std::vector<double>& w0, int sweeps
             // smoothed prolongator of the level's aggregates; the next level
             // matrix is Pbar^T A Pbar (the smooth vector stays the tentative one)
             const int ncl = A.n;
-            cur.omega_p = smoothing_weight(cur.A);
+            cur.omega_p = smoothing_weight(cur.A, H.omega_rule);
             cur.pbar = smoothed_prolongator(cur.A, agg, p, ncl, cur.omega_p);
             cur.pbar_t = transpose_csr(cur.pbar, ncl);
             A = galerkin_general(cur.A, cur.pbar, cur.pbar_t);
@@ -844,20 +846,21 @@ int orc_match_ld(int n, const int32_t* ptr, const int32_t* col, const double* va
 // null; *status receives 0 or a negative code.
 void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                     int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
-                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int* status);
+                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int omega_rule, int* status);
 
 void* orc_setup(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                 int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
                 int max_dense, int* status) {
     return orc_setup_seg(n, ptr, col, val, w, sweeps, max_coarse, max_levels, pre, post, omega, use_ld, min_ratio,
-                         max_dense, 0, nullptr, 0, status);
+                         max_dense, 0, nullptr, 0, 0, status);
 }
 
 // As orc_setup for the block-diagonal union of nseg systems with row offsets
 // seg[0..nseg] (the largest system decides when coarsening stops).
+// smooth_p != 0 smooths every prolongator with the weight of omega_rule.
 void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double* val, const double* w, int sweeps,
                     int max_coarse, int max_levels, int pre, int post, double omega, int use_ld, double min_ratio,
-                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int* status) {
+                    int max_dense, int nseg, const int32_t* seg, int smooth_p, int omega_rule, int* status) {
     Csr A = make_csr(n, ptr, col, val);
     int e = validate(A);
     for (int i = 0; e == 0 && i < n; ++i)
@@ -865,6 +868,7 @@ void* orc_setup_seg(int n, const int32_t* ptr, const int32_t* col, const double*
     if (e) { *status = e; return nullptr; }
     Hierarchy* H = new Hierarchy;
     H->pre = pre; H->post = post; H->omega = omega; H->use_ld = use_ld; H->smooth_p = smooth_p;
+    H->omega_rule = omega_rule;
     std::vector<int> sv;
     if (nseg > 0) sv.assign(seg, seg + nseg + 1);
     e = build(*H, A, std::vector<double>(w, w + n), sweeps, max_coarse, max_levels, min_ratio, max_dense,

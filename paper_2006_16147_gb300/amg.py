@@ -55,7 +55,7 @@ class amg_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_dense", ctypes.c_int), ("keep_sweeps", ctypes.c_int),
                 ("profile", ctypes.c_int), ("match_kernel", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("smooth_p", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("omega_rule", ctypes.c_int), ("min_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class amg_solve_info(ctypes.Structure):

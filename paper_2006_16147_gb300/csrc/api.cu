@@ -64,7 +64,7 @@ amg_status setup_common(const amg_csr* A, const double* w, const amg_options* op
         o.post < 0 || !(o.omega > 0.0) || (o.precision != AMG_FP64 && o.precision != AMG_FP32_VCYCLE) ||
         o.max_dense < 1 || o.krylov < 0 || o.krylov > 1 || !(o.min_ratio >= 1.0) || o.autotune < 0 ||
         o.autotune > 1 || o.cycle < 0 || o.cycle > AMG_KCYCLE_FULL || (o.cycle > 0 && (o.pre != 1 || o.post != 1)) ||
-        o.smooth_p < 0 || o.smooth_p > 1 || (o.smooth_p && (o.cycle != 0 || o.pre != 1 || o.post != 1)))
+        o.smooth_p < 0 || o.smooth_p > 1 || (o.smooth_p && o.cycle != 0) || o.omega_rule < 0 || o.omega_rule > 1)
         return fail(AMG_ERR_ARG, "invalid options");
     if (many && (o.cycle != 0 || o.smooth_p)) return fail(AMG_ERR_ARG, "batches of systems use the unsmoothed V-cycle");
     amg_hierarchy* h = new amg_hierarchy;

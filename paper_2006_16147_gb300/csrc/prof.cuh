@@ -30,6 +30,7 @@ enum KernelId : int {
     S_VALIDATE,
     S_WEIGHTS,
     S_MATCH,
+    S_MATCH_SORT,
     S_AGGREGATE,
     S_GALERKIN,
     S_COMPOSE,
@@ -44,7 +45,7 @@ inline const char* kernel_name(int id) {
     static const char* names[K_COUNT] = {
         "pre_residual",   "pre_residual_l0", "pre_step",     "restrict",  "coarse_solve", "post_smooth",
         "post_smooth_l0", "smooth",          "spmv_dot",     "update_xr", "update_p",     "residual",
-        "dot",            "convert_l0",      "kcycle_fcg",   "setup_validate",  "setup_weights", "setup_match", "setup_aggregate", "setup_galerkin",
+        "dot",            "convert_l0",      "kcycle_fcg",   "setup_validate",  "setup_weights", "setup_match", "setup_match_sort", "setup_aggregate", "setup_galerkin",
         "setup_compose",  "setup_smoother",  "setup_format", "setup_coarse", "setup_smooth_p"};
     return (id >= 0 && id < K_COUNT) ? names[id] : "";
 }

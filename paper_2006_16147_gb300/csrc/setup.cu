@@ -647,37 +647,46 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
 // its suitor exactly when they are each other's suitor). The algorithm is
 // the Suitor method of Manne and Halappanavar (IPDPS 2014).
 //
-// A proposal of cur at sorted position k of its row, to v = nbr[k], is the
-// position q = mpos[k] of cur in v's sorted row: for a fixed v, positions
-// order v's edges exactly as the strict order does, so suitor[v] (the
-// smallest position proposed and not displaced, INT_MAX for none) is one
-// int and one atomicMin decides each proposal. Suitor values only decrease,
-// so a vertex never has to look back up its list: a displaced vertex y
-// resumes right after v, at mpos[old] + 1 in its own row. No thread waits
+// A proposal of cur, from sorted position k of its own row, to v is the
+// position q of cur in v's sorted row: for a fixed v, positions order v's
+// edges exactly as the strict order does. suitor[v] holds q << 32 | k of the
+// best proposal not yet displaced (all ones for none), so one 64-bit
+// atomicMin decides a proposal and returns, on a displacement, where the
+// displaced vertex resumes: right after v in its own row (suitor values only
+// decrease, so a vertex never has to look back up its list). No thread waits
 // on another, and each vertex's list position only moves forward, so the
 // work is bounded by the entry count.
 //
-// mpos[s] for every sorted edge position s of row v: the sorted position of
-// v in the row of u = nbr[s]. spos[k] maps an original CSR position to its
-// sorted position (written by the edge sorts). Also resets suitor[].
+// nq[s] for every sorted position s of row v: (u, position of v in u's
+// sorted row) for an edge to u, (-1, -1) for the non-edges after the edges.
+// Every row holds its diagonal, a non-edge, so every row ends in (-1, -1)
+// and a scan never leaves its row (checked here: err |= 8 otherwise).
+// spos[k] maps an original CSR position to its sorted position (written by
+// the edge sorts for every edge). Also resets suitor[].
+constexpr unsigned long long NO_SUITOR = ~0ull;
+
 __global__ void k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                             const double* __restrict__ c, const int* __restrict__ spos, int* __restrict__ mpos,
-                             int* __restrict__ suitor, int* err) {
+                             const double* __restrict__ c, const int* __restrict__ spos, int2* __restrict__ nq,
+                             unsigned long long* __restrict__ suitor, int* err) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        suitor[v] = 0x7fffffff;
-        const int e = ptr[v + 1];
-        for (int k = ptr[v]; k < e; ++k) {
+        suitor[v] = NO_SUITOR;
+        const int b = ptr[v], e = ptr[v + 1];
+        int edges = 0;
+        for (int k = b; k < e; ++k) {
             if (c[k] == NEG_INF) continue;          // not an edge (diagonal, zero pair)
+            ++edges;
             const int u = col[k];
             const int km = find_in_row(ptr, col, u, v);
             if (km < 0) {                            // no mirror entry: pattern not symmetric
-                mpos[spos[k]] = -1;
+                nq[spos[k]] = make_int2(-1, -1);
                 atomicOr(err, 1);
                 continue;
             }
-            mpos[spos[k]] = spos[km];
+            nq[spos[k]] = make_int2(u, spos[km]);
         }
+        if (edges == e - b) atomicOr(err, 8);       // no non-edge ends the row
+        for (int k = b + edges; k < e; ++k) nq[k] = make_int2(-1, -1);
     }
 }
 
@@ -685,47 +694,45 @@ __global__ void k_mirror_pos(int n, const int* __restrict__ ptr, const int* __re
 // it displaces. err |= 2 if a thread takes more steps than there are
 // entries (impossible for a valid mirror map; a guard, not a wait).
 __global__ void __launch_bounds__(256) k_suitor(int n, long long nnz, const int* __restrict__ ptr,
-                                                const int* __restrict__ nbr, const int* __restrict__ mpos,
-                                                int* suitor, int* err) {
+                                                const int2* __restrict__ nq, unsigned long long* suitor, int* err) {
     const int u0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u0 >= n) return;
-    int k = __ldg(ptr + u0), e = __ldg(ptr + u0 + 1);
+    if (u0 >= n || *err) return;
+    int k = __ldg(ptr + u0);
+    int2 cur = __ldg(nq + k);
     long long steps = 0;
     for (;;) {
-        if (k >= e) return;
-        const int v = __ldg(nbr + k);
-        if (v < 0) return;                           // the row's edges are exhausted: unmatched so far
-        const int q = __ldg(mpos + k);
-        if (++steps > nnz || q < 0) {
+        if (cur.x < 0) return;                       // the row's edges are exhausted: no partner so far
+        const int2 nxt = __ldg(nq + k + 1);          // in the row: its (-1, -1) end follows every edge
+        if (++steps > nnz) {
             atomicOr(err, 2);
             return;
         }
-        const int old = atomicMin(suitor + v, q);
-        if (old < q) {                               // v holds a better proposal: next candidate
+        const unsigned long long mine = ((unsigned long long)(unsigned)cur.y << 32) | (unsigned)k;
+        const unsigned long long old = atomicMin(suitor + cur.x, mine);
+        if (old > mine) {
+            if (old == NO_SUITOR) return;            // first suitor of v: this chain ends
+            k = (int)(unsigned)(old & 0xffffffffu) + 1;   // the displaced vertex, after v in its own row
+            cur = __ldg(nq + k);
+        } else {                                     // v holds a better proposal: next candidate
             ++k;
-            continue;
+            cur = nxt;
         }
-        if (old == 0x7fffffff) return;              // first suitor of v: this chain ends
-        // old's vertex y is displaced; it continues after v in its own row
-        const int y = __ldg(nbr + old);
-        k = __ldg(mpos + old) + 1;
-        e = __ldg(ptr + y + 1);
     }
 }
 
 // mate[v] = the vertex at v's suitor position, -1 without a suitor; the
 // relation must be mutual (err |= 4 otherwise).
-__global__ void k_suitor_mate(int n, const int* __restrict__ nbr, const int* __restrict__ mpos,
-                              const int* __restrict__ suitor, int* __restrict__ mate, int* err) {
+__global__ void k_suitor_mate(int n, const int2* __restrict__ nq, const unsigned long long* __restrict__ suitor,
+                              int* __restrict__ mate, int* err) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const int s = suitor[v];
-        if (s == 0x7fffffff) {
+        const unsigned long long s = suitor[v];
+        if (s == NO_SUITOR) {
             mate[v] = -1;
             continue;
         }
-        const int u = nbr[s];
-        mate[v] = u;
-        if (suitor[u] != mpos[s]) atomicOr(err, 4);
+        const int2 e = nq[(int)(s >> 32)];           // v's edge to its suitor u: (u, position of v in u's row)
+        mate[v] = e.x;
+        if ((int)(suitor[e.x] >> 32) != e.y) atomicOr(err, 4);
     }
 }
 
@@ -1735,7 +1742,8 @@ struct Scratch {
     int* skey = nullptr;      // nnz
     double* sval = nullptr;   // nnz
     int* spos = nullptr;      // nnz: sorted position of each entry (matching by proposals)
-    int* mpos = nullptr;      // nnz: mirror's sorted position per sorted entry
+    int2* nq = nullptr;       // nnz: (neighbour, mirror's sorted position) per sorted entry
+    unsigned long long* suitor = nullptr;   // n
     long long cap_nnz = 0;    // entries c, skey and sval hold
     int* scan_tmp = nullptr;
     int* host = nullptr;      // pinned
@@ -1826,20 +1834,28 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
     cudaStream_t st = h->stream;
     const int n = A.n;
     CUDA_CHECK(cudaMemsetAsync(S.mate, 0xff, sizeof(int) * n, st));   // all -1
+    // algorithmic bytes of the edge sort (c, col in; nbr, spos out) and of
+    // the mirror map (c, col, spos in, the mirror's spos gathered, nq out)
+    const double sort_bytes = 20.0 * A.nnz + 8.0 * n, mirror_bytes = 28.0 * A.nnz + 16.0 * n;
     if (h->opt.match_kernel == 0) {
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 4 * sizeof(int), st));   // [13, 14] long-row lists, [16] error
-        sort_edges(h, S, A, S.spos);
         int* err = S.cnt + 16;
-        k_mirror_pos<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mpos, S.cand, err);
-        KERNEL_CHECK();
-        if (n > 0) {
-            k_suitor<<<(n + 255) / 256, 256, 0, st>>>(n, (long long)A.nnz, A.ptr, S.skey, S.mpos, S.cand, err);
+        {
+            Scope sc_(&h->prof, st, S_MATCH_SORT, sort_bytes + mirror_bytes);
+            CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 4 * sizeof(int), st));   // [13, 14] long-row lists, [16] error
+            sort_edges(h, S, A, S.spos);
+            k_mirror_pos<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             KERNEL_CHECK();
         }
-        k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.skey, S.mpos, S.cand, S.mate, err);
+        Scope sc_(&h->prof, st, S_MATCH, 0.0);
+        if (n > 0) {
+            k_suitor<<<(n + 255) / 256, 256, 0, st>>>(n, (long long)A.nnz, A.ptr, S.nq, S.suitor, err);
+            KERNEL_CHECK();
+        }
+        k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.nq, S.suitor, S.mate, err);
         KERNEL_CHECK();
         const int e = read_int(err, S.host, st);
         if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
+        if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
         if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
         return 0;
     }
@@ -1847,7 +1863,11 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
         int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
         int* pos = S.flag;
         CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 64, st));
-        sort_edges(h, S, A, nullptr);
+        {
+            Scope sc_(&h->prof, st, S_MATCH_SORT, sort_bytes);
+            sort_edges(h, S, A, nullptr);
+        }
+        Scope sc_(&h->prof, st, S_MATCH, 0.0);
         int nn = n;
         const int* ptr = A.ptr;
         const int* col = A.col;
@@ -1867,6 +1887,7 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
         if (hc[7] == 2) AMG_THROW(AMG_ERR_TIMEOUT, "matching did not settle after n rounds");
         return hc[8];
     }
+    Scope sc_(&h->prof, st, S_MATCH, 0.0);
     CUDA_CHECK(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 5, st));
     k_ld_init<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.cand, S.mate);
     KERNEL_CHECK();
@@ -2054,12 +2075,12 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.mem.release(S.skey);
     S.mem.release(S.sval);
     S.mem.release(S.spos);
-    S.mem.release(S.mpos);
+    S.mem.release(S.nq);
     S.c = S.mem.alloc<double>(nnz);
     S.skey = S.mem.alloc<int>(nnz);
     S.sval = S.mem.alloc<double>(nnz);
     S.spos = S.mem.alloc<int>(nnz);
-    S.mpos = S.mem.alloc<int>(nnz);
+    S.nq = S.mem.alloc<int2>(nnz);
     S.cap_nnz = nnz;
 }
 
@@ -2173,7 +2194,8 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
 
 // Smoothed prolongator of level L (aggregates agg/p to nc coarse rows) and
 // the coarse matrix Pbar^T A Pbar (Section 3.2), the oracle's operation
-// order throughout: omega from eta = max_i sum_j |a_ij| / a_ii, Pbar rows from
+// order throughout: omega = 4 / (3 eta) (omega_rule 0) or 1 / eta (omega_rule
+// 1, the text's weight) from eta = max_i sum_j |a_ij| / a_ii, Pbar rows from
 // the rows of A P, the transpose with ascending rows, then the product.
 DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     cudaStream_t st = h->stream;
@@ -2189,7 +2211,7 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     S.mem.release(eta_bits);
     double eta;
     std::memcpy(&eta, &eb, sizeof(eta));
-    const double omega = 4.0 / (3.0 * eta);
+    const double omega = h->opt.omega_rule == 1 ? 1.0 / eta : 4.0 / (3.0 * eta);
     L.omega_p = omega;
 
     // rows of A P (canonical), compacted, then turned into rows of Pbar
@@ -2289,7 +2311,8 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.skey = S.mem.alloc<int>(nnz0);
     S.sval = S.mem.alloc<double>(nnz0);
     S.spos = S.mem.alloc<int>(nnz0);
-    S.mpos = S.mem.alloc<int>(nnz0);
+    S.nq = S.mem.alloc<int2>(nnz0);
+    S.suitor = S.mem.alloc<unsigned long long>(n0);
     S.cap_nnz = nnz0;
     S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
 
@@ -2367,11 +2390,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 k_weights<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag, w, S.c);
                 KERNEL_CHECK();
             }
-            int rr = 0;
-            {
-                Scope sc_(&h->prof, st, S_MATCH, 0.0);
-                rr = ld_match(h, S, A);
-            }
+            const int rr = ld_match(h, S, A);
             int nc = 0;
             {
                 Scope sc_(&h->prof, st, S_AGGREGATE, 0.0);

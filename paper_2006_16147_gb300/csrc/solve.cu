@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(TPB) k_sell_spmv(SellView S, const T* __restri
 //   W_ADD     y_i = y_i + s_i                        (prolongation x + Pbar e)
 //   W_PRE     y_i = b_i - omega s_i, xo_i = wm_i b_i (pre-smoothing from zero)
 //   W_SMOOTH  y_i = x_i + omega m_i (b_i - s_i)      (smoothing sweep)
-enum WideOp : int { W_SPMV = 0, W_ADD = 1, W_PRE = 2, W_SMOOTH = 3 };
+//   W_STEP    x'_i = x_i + omega m_i r_i, y_i = b_i - sum_j a_ij x'_j with x'_j
+//             formed on the fly (an extra pre-smoothing sweep; wm holds r, xo x')
+enum WideOp : int { W_SPMV = 0, W_ADD = 1, W_PRE = 2, W_SMOOTH = 3, W_STEP = 4 };
 constexpr int WIDE_MIN_A = 64;   // mean entries per row from which a level matrix takes this path
 constexpr int WIDE_MIN_P = 64;   // the same for Pbar and its transpose
 template <int OP>
@@ -373,17 +375,19 @@ __global__ void __launch_bounds__(TPB) k_wide(int n, const int* __restrict__ ptr
         const int kb = ptr[i], ke = ptr[i + 1];
         double acc0 = 0.0, acc1 = 0.0;
         int k = kb + lane;
+        // the neighbour value: x_j, or for an extra pre-smoothing sweep x_j + omega m_j r_j
+        auto xv = [&](int j) { return OP == W_STEP ? fma(omega * ld(minv + j), ld(wm + j), ld(x + j)) : ld(x + j); };
         for (; k + 32 < ke; k += 64) {
             const int j0 = col[k], j1 = col[k + 32];
             const double v0 = OP == W_PRE ? val[k] * minv[j0] : val[k];
             const double v1 = OP == W_PRE ? val[k + 32] * minv[j1] : val[k + 32];
-            acc0 = fma(v0, ld(x + j0), acc0);
-            acc1 = fma(v1, ld(x + j1), acc1);
+            acc0 = fma(v0, xv(j0), acc0);
+            acc1 = fma(v1, xv(j1), acc1);
         }
         if (k < ke) {
             const int j0 = col[k];
             const double v0 = OP == W_PRE ? val[k] * minv[j0] : val[k];
-            acc0 = fma(v0, ld(x + j0), acc0);
+            acc0 = fma(v0, xv(j0), acc0);
         }
         double acc = acc0 + acc1;
 #pragma unroll
@@ -397,6 +401,10 @@ __global__ void __launch_bounds__(TPB) k_wide(int n, const int* __restrict__ ptr
                 xo[i] = wm[i] * bi;
             }
             if (OP == W_SMOOTH) y[i] = fma(omega * minv[i], b[i] - acc, x[i]);
+            if (OP == W_STEP) {
+                xo[i] = fma(omega * minv[i], wm[i], x[i]);
+                y[i] = b[i] - acc;
+            }
         }
     }
 }
@@ -879,7 +887,11 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         }
         for (int k = 1; k < pre; ++k) {
             Scope sc_(&h->prof, st, K_PRE_STEP, by_pre_step(Lv, V, Vb));
-            if (l == 0) k_pre_step<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra, xb, rb);
+            if (wideA)
+                k_wide<W_STEP><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
+                    Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xa, Lv.minv, (const double*)ra,
+                    (double)omega, l == 0 ? r : (const double*)vec(Lv, VB), (double*)rb, (double*)xb);
+            else if (l == 0) k_pre_step<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra, xb, rb);
             else k_pre_step<T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra, xb, rb);
             KERNEL_CHECK();
             std::swap(xa, xb);
@@ -934,22 +946,35 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
                         SPB, f32 ? (const T*)Lv.PB.val32 : (const T*)Lv.PB.val, e, xcur[l]);
                 KERNEL_CHECK();
             }
+            // post sweeps alternate between y and the x buffer the pre-smoother left free
+            T* cur = xcur[l];
+            T* bufs[2] = {vec(Lv, VY), spare[l]};
             if (l > 0) {
-                T* ya = vec(Lv, VY);
-                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
-                if (!f32 && wide(Lv.A, WIDE_MIN_A))
-                    k_wide<W_SMOOTH><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
-                        Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xcur[l], Lv.minv, nullptr,
-                        (double)omega, (const double*)vec(Lv, VB), (double*)ya, nullptr);
-                else
-                    k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xcur[l], ya);
-                KERNEL_CHECK();
-                out[l] = ya;
+                for (int k = 0; k < post; ++k) {
+                    T* dst = bufs[k & 1];
+                    Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, V, V));
+                    if (!f32 && wide(Lv.A, WIDE_MIN_A))
+                        k_wide<W_SMOOTH><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
+                            Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)cur, Lv.minv, nullptr,
+                            (double)omega, (const double*)vec(Lv, VB), (double*)dst, nullptr);
+                    else
+                        k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), cur, dst);
+                    KERNEL_CHECK();
+                    cur = dst;
+                }
+                out[l] = cur;
                 continue;
+            }
+            for (int k = 0; k + 1 < post; ++k) {
+                T* dst = bufs[k & 1];
+                Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, V));
+                k_smooth<T, double, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, cur, dst);
+                KERNEL_CHECK();
+                cur = dst;
             }
             {
                 Scope sc_(&h->prof, st, K_SMOOTH, by_smooth(Lv, V, 8, 8));
-                k_smooth<T, double, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xcur[0], z);
+                k_smooth<T, double, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, cur, z);
                 KERNEL_CHECK();
             }
             if (rz_mode != FIN_NONE) {

@@ -4,7 +4,9 @@ through the C ABI against the oracle built with smooth_p=True.
 Bars: every level's matrix, smooth vector, l1-Jacobi diagonal, tentative
 aggregates, the smoothed prolongator and its weight bit for bit (the
 coarse matrix Pbar^T A Pbar is summed in the oracle's order); the V-cycle
-within 1e-12 relative; PCG within +-1 iteration and 1e-10 in the solution.
+within 1e-12 relative; PCG within +-1 iteration and 1e-10 in the solution;
+the same with four l1-Jacobi sweeps before and after (the paper's GPU runs)
+and with the text's smoothing weight.
 """
 import numpy as np
 import pytest
@@ -104,6 +106,42 @@ def test_smoothed_fp32_and_fewer_iterations():
     assert abs(its[(1, 1)] - its[(1, 0)]) <= 2
 
 
+@pytest.mark.parametrize("pre,post,rule", [(4, 4, 0), (4, 4, 1), (2, 3, 0)])
+@pytest.mark.parametrize("name", ["poisson24", "aniso3d", "spd_wide_coarse"])
+def test_va3_sweeps_and_omega_rule_parity(orc, name, pre, post, rule):
+    # the paper's GPU setting (VA3 with l1-Jacobi 4 + 4) and the text's
+    # smoothing weight 1 / ||D^-1 A||_inf (rule 1); spd_wide_coarse runs the
+    # extra sweeps of its dense coarse levels through the warp-per-row kernels
+    from paper_2006_16147_gb300 import amg
+    mk, seed, mc = CASES[name]
+    A = mk()
+    w = _w(A, seed)
+    H = orc.Hierarchy(A, w, max_coarse=mc, smooth_p=True, pre=pre, post=post, omega_rule=rule)
+    h = setup(A, w, max_coarse=mc, smooth_p=1, pre=pre, post=post, omega_rule=rule)
+    assert amg.amg_hierarchy_info(h)["n"] == [s[0] for s in H.sizes()]
+    for l in range(H.num_levels - 1):
+        Pb, om = H.pbar(l)
+        gp = amg.amg_export_pbar(h, l)
+        assert gp["omega"] == om and np.array_equal(Pb.val, gp["val"]), l
+    r = np.random.default_rng(5).normal(size=A.n)
+    zo = H.vcycle(r)
+    zg = vcycle(h, r)
+    assert np.linalg.norm(zg - zo) <= 1e-12 * np.linalg.norm(zo)
+    b, _ = W.rhs_uniform(A, 2)
+    xo, io = H.pcg(b, rtol=1e-6, maxit=500)
+    xg, ig = solve(h, b, rtol=1e-6, maxit=500)
+    assert io["status"] == 0 and ig["status"] == 0
+    assert abs(ig["iterations"] - io["iterations"]) <= 1
+    assert_same_solution(H, b, xg, ig, xo, io)
+    h.close()
+    # the FP32 V-cycle with the same sweeps converges to the same tolerance
+    h = setup(A, w, max_coarse=mc, smooth_p=1, pre=pre, post=post, omega_rule=rule, precision=1, krylov=1)
+    x32, i32 = solve(h, b, rtol=1e-6, maxit=500)
+    assert i32["status"] == 0 and np.linalg.norm(b - A.scipy() @ x32) <= 1e-6 * np.linalg.norm(b)
+    assert i32["iterations"] <= io["iterations"] + 2
+    h.close()
+
+
 def test_smoothed_option_checks():
     import torch
     from paper_2006_16147_gb300 import amg
@@ -112,6 +150,8 @@ def test_smoothed_option_checks():
         setup(A, smooth_p=1, cycle=1)
     with pytest.raises(amg.AmgError):
         setup(A, smooth_p=2)
+    with pytest.raises(amg.AmgError):
+        setup(A, smooth_p=1, omega_rule=2)
     h = setup(A, smooth_p=1)
     X = torch.zeros(A.n, 2, dtype=torch.float64, device="cuda:0")
     with pytest.raises(amg.AmgError):
