@@ -34,6 +34,12 @@ __device__ __forceinline__ int find_in_row(const int* __restrict__ ptr, const in
     return (lo < ptr[row + 1] && col[lo] == j) ? lo : -1;
 }
 
+// Edge weights mark non-edges with -inf. Tested on the bits: a double
+// compare issues on this GPU's FP64 pipe (1/64 of the FP32 rate), an integer
+// compare does not.
+constexpr long long NEG_INF_BITS = (long long)0xfff0000000000000ULL;
+__device__ __forceinline__ bool is_edge(double cw) { return __double_as_longlong(cw) != NEG_INF_BITS; }
+
 // Row pointers first: monotone, starting at 0, ending at nnz.
 __global__ void k_check_ptr(int n, int nnz, const int* __restrict__ ptr, int* flags) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n; i += (long long)gridDim.x * blockDim.x) {
@@ -96,16 +102,22 @@ __global__ void k_dww(int n, double* __restrict__ diag, const double* __restrict
 // (2 a) w_i w_j is formed as (a (2 w_i)) w_j, the same single rounding of
 // the same exact product. FP64 work per edge: one add, two multiplies, the
 // division and the subtraction (this GPU's FP64 pipe bounds this kernel).
-__global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                          const double* __restrict__ val, const double* __restrict__ dww,
-                          const double* __restrict__ w, double* __restrict__ c) {
+// A group of G lanes per row (G = 1, 8, 16 or 32 by the mean row length),
+// the row's entries strided over the group, so long rows are shared out.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                 const double* __restrict__ val, const double* __restrict__ dww,
+                                                 const double* __restrict__ w, double* __restrict__ c) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int gl = threadIdx.x & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) / G; i < n; i += ng) {
         const double wi = w[i], si = dww[i];
         const double w2i = wi + wi;
-        for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int e = ptr[i + 1];
+        for (int k = ptr[i] + gl; k < e; k += G) {
             const int j = col[k];
-            if (j < i) continue;                 // written by the thread of row j
+            if (j < i) continue;                 // written by the group of row j
             if (j == i) { c[k] = NEG_INF; continue; }
             const double a = val[k];
             double cw = NEG_INF;
@@ -149,7 +161,7 @@ __device__ __forceinline__ int best_free(int v, const int* __restrict__ ptr, con
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
         const double cw = c[k];
-        if (cw == NEG_INF) continue;
+        if (!is_edge(cw)) continue;
         const int u = col[k];
         if (mate[u] != -1) continue;
         const int lo = min(u, v), hi = max(u, v);
@@ -210,7 +222,7 @@ __global__ void k_ld_update(int n, const int* __restrict__ ptr, const int* __res
         for (int k = ptr[m]; k < ptr[m + 1]; ++k) {
             bool take = false;
             int x = col[k];
-            if (c[k] != NEG_INF && mate[x] == -1 && cand[x] == m) {
+            if (is_edge(c[k]) && mate[x] == -1 && cand[x] == m) {
                 const int b = best_free(x, ptr, col, c, mate);
                 cand[x] = b;
                 if (b < 0) mate[x] = -2;
@@ -283,7 +295,7 @@ __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __re
         int m = b;
         for (int k = b; k < e; ++k) {
             const double cw = c[k];
-            if (cw == NEG_INF) continue;
+            if (!is_edge(cw)) continue;
             const int u = col[k];
             int d = m - 1;
             // insert (cw, u) keeping the order: larger weight, then smaller (lo, hi)
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __re
         if (gl < len) {
             const double cw = c[b + gl];
             u = col[b + gl];
-            edge = cw != NEG_INF;
+            edge = is_edge(cw);
             if (edge) {
                 wk = weight_order(cw);
                 uk = u;
@@ -407,7 +419,7 @@ __global__ void __launch_bounds__(LONG_TPB) k_sort_edges_long(const int* __restr
         while (m2 < len) m2 <<= 1;
         for (int s = tid; s < m2; s += LONG_TPB) {
             const double cw = s < len ? c[b + s] : NEG_INF;
-            const bool edge = cw != NEG_INF;
+            const bool edge = is_edge(cw);
             WK[s] = edge ? weight_order(cw) : (long long)0x8000000000000000ULL;
             U[s] = edge ? col[b + s] : 0x7fffffff;
         }
@@ -665,16 +677,28 @@ __global__ void __launch_bounds__(1024) k_ld_persistent(int n, const int* __rest
 // the edge sorts for every edge). Also resets suitor[].
 constexpr unsigned long long NO_SUITOR = ~0ull;
 
-__global__ void k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                             const double* __restrict__ c, const int* __restrict__ spos, int2* __restrict__ nq,
-                             unsigned long long* __restrict__ suitor, int* err) {
+template <int G>
+__global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                    const double* __restrict__ c, const int* __restrict__ spos,
+                                                    int2* __restrict__ nq, unsigned long long* __restrict__ suitor,
+                                                    int* err) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        suitor[v] = NO_SUITOR;
-        const int b = ptr[v], e = ptr[v + 1];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int v0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int warp_first = v0 - (lane - gl) / G;     // every lane of a warp runs the same iterations
+    for (int it = 0; warp_first + it * ng < n; ++it) {
+        const int v = v0 + it * ng;
+        int b = 0, e = 0;
+        if (v < n) {
+            b = ptr[v];
+            e = ptr[v + 1];
+            if (gl == 0) suitor[v] = NO_SUITOR;
+        }
         int edges = 0;
-        for (int k = b; k < e; ++k) {
-            if (c[k] == NEG_INF) continue;          // not an edge (diagonal, zero pair)
+        for (int k = b + gl; k < e; k += G) {
+            if (!is_edge(c[k])) continue;           // not an edge (diagonal, zero pair)
             ++edges;
             const int u = col[k];
             const int km = find_in_row(ptr, col, u, v);
@@ -685,8 +709,12 @@ __global__ void k_mirror_pos(int n, const int* __restrict__ ptr, const int* __re
             }
             nq[spos[k]] = make_int2(u, spos[km]);
         }
-        if (edges == e - b) atomicOr(err, 8);       // no non-edge ends the row
-        for (int k = b + edges; k < e; ++k) nq[k] = make_int2(-1, -1);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) edges += __shfl_xor_sync(FULL_MASK, edges, o, G);
+        if (v < n) {
+            if (gl == 0 && edges == e - b) atomicOr(err, 8);   // no non-edge ends the row
+            for (int k = b + edges + gl; k < e; k += G) nq[k] = make_int2(-1, -1);
+        }
     }
 }
 
@@ -1052,6 +1080,25 @@ __global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restr
 int rows_group(long long terms, long long rows) {
     const double avg = rows > 0 ? (double)terms / (double)rows : 0.0;
     return avg <= 7.0 ? 8 : (avg <= 14.0 ? 16 : 32);
+}
+
+// Eq. 3 weights of every stored pair. The kernel is bound by the FP64
+// division of each upper entry: with short rows one thread per row keeps
+// every lane dividing (rows of a stencil have their upper entries at the
+// same positions); long rows take a group of lanes each.
+int weights_group(long long nnz, long long n) {
+    const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
+    return mean < 24.0 ? 1 : (mean < 48.0 ? 8 : (mean < 96.0 ? 16 : 32));
+}
+
+void launch_weights(int G, int grid_cap, cudaStream_t st, int n, const int* ptr, const int* col, const double* val,
+                    const double* dww, const double* w, double* c) {
+    const int blocks = blocks_for((long long)n * G, TPB, grid_cap);
+    if (G == 1) k_weights<1><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else if (G == 8) k_weights<8><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else if (G == 16) k_weights<16><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else k_weights<32><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    KERNEL_CHECK();
 }
 
 template <bool RAP>
@@ -1843,7 +1890,14 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
             Scope sc_(&h->prof, st, S_MATCH_SORT, sort_bytes + mirror_bytes);
             CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 4 * sizeof(int), st));   // [13, 14] long-row lists, [16] error
             sort_edges(h, S, A, S.spos);
-            k_mirror_pos<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+            const int G = rows_group(A.nnz, n);
+            const int mblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
+            if (G == 8)
+                k_mirror_pos<8><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+            else if (G == 16)
+                k_mirror_pos<16><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+            else
+                k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             KERNEL_CHECK();
         }
         Scope sc_(&h->prof, st, S_MATCH, 0.0);
@@ -2387,8 +2441,8 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 Scope sc_(&h->prof, st, S_WEIGHTS, 20.0 * A.nnz + 24.0 * n);
                 k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
                 KERNEL_CHECK();
-                k_weights<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, S.diag, w, S.c);
-                KERNEL_CHECK();
+                launch_weights(weights_group(A.nnz, n), h->num_sms * 16, st, n, A.ptr, A.col, A.val, S.diag, w,
+                               S.c);
             }
             const int rr = ld_match(h, S, A);
             int nc = 0;
@@ -2699,8 +2753,7 @@ amg_status match_noalloc(const amg_csr* A, const double* w, int32_t* mate, void*
 
     k_dww<<<grid, TPB, 0, st>>>(n, diag, w);
     KERNEL_CHECK();
-    k_weights<<<grid, TPB, 0, st>>>(n, ptr, col, val, diag, w, c);
-    KERNEL_CHECK();
+    launch_weights(weights_group(nnz, n), sms * 16, st, n, ptr, col, val, diag, w, c);
     CUDA_CHECK(cudaMemsetAsync(mate, 0xff, sizeof(int) * n, st));
     k_ld_init<<<grid, TPB, 0, st>>>(n, ptr, col, c, cand, mate);
     KERNEL_CHECK();

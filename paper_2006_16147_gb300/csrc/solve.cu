@@ -358,9 +358,8 @@ __global__ void __launch_bounds__(TPB) k_sell_spmv(SellView S, const T* __restri
 //   W_ADD     y_i = y_i + s_i                        (prolongation x + Pbar e)
 //   W_PRE     y_i = b_i - omega s_i, xo_i = wm_i b_i (pre-smoothing from zero)
 //   W_SMOOTH  y_i = x_i + omega m_i (b_i - s_i)      (smoothing sweep)
-//   W_STEP    x'_i = x_i + omega m_i r_i, y_i = b_i - sum_j a_ij x'_j with x'_j
-//             formed on the fly (an extra pre-smoothing sweep; wm holds r, xo x')
-enum WideOp : int { W_SPMV = 0, W_ADD = 1, W_PRE = 2, W_SMOOTH = 3, W_STEP = 4 };
+//   W_RES     y_i = b_i - s_i                           (residual)
+enum WideOp : int { W_SPMV = 0, W_ADD = 1, W_PRE = 2, W_SMOOTH = 3, W_RES = 4 };
 constexpr int WIDE_MIN_A = 64;   // mean entries per row from which a level matrix takes this path
 constexpr int WIDE_MIN_P = 64;   // the same for Pbar and its transpose
 template <int OP>
@@ -375,8 +374,7 @@ __global__ void __launch_bounds__(TPB) k_wide(int n, const int* __restrict__ ptr
         const int kb = ptr[i], ke = ptr[i + 1];
         double acc0 = 0.0, acc1 = 0.0;
         int k = kb + lane;
-        // the neighbour value: x_j, or for an extra pre-smoothing sweep x_j + omega m_j r_j
-        auto xv = [&](int j) { return OP == W_STEP ? fma(omega * ld(minv + j), ld(wm + j), ld(x + j)) : ld(x + j); };
+        auto xv = [&](int j) { return ld(x + j); };
         for (; k + 32 < ke; k += 64) {
             const int j0 = col[k], j1 = col[k + 32];
             const double v0 = OP == W_PRE ? val[k] * minv[j0] : val[k];
@@ -401,10 +399,7 @@ __global__ void __launch_bounds__(TPB) k_wide(int n, const int* __restrict__ ptr
                 xo[i] = wm[i] * bi;
             }
             if (OP == W_SMOOTH) y[i] = fma(omega * minv[i], b[i] - acc, x[i]);
-            if (OP == W_STEP) {
-                xo[i] = fma(omega * minv[i], wm[i], x[i]);
-                y[i] = b[i] - acc;
-            }
+            if (OP == W_RES) y[i] = b[i] - acc;
         }
     }
 }
@@ -440,21 +435,20 @@ __global__ void __launch_bounds__(TPB) k_to_f32(int n, const double* __restrict_
     if (i < n) b[i] = (float)a[i];
 }
 
-// Extra pre-smoothing sweep from (x, r = b - A x):
-//   x' = x + omega M^-1 r,  r' = b - A x'  (x' of neighbours recomputed).
+// Residual after the last of several pre-smoothing sweeps: r = b - A x.
+// (Sweeps between the first and the last are k_smooth, the first is k_pre
+// storing x + omega M^-1 r; each reads one gathered vector, one FMA per
+// stored entry.)
 template <typename T, typename TB>
-__global__ void __launch_bounds__(TPB) k_pre_step(SellView S, const T* __restrict__ val, const T* __restrict__ minv,
-                                                  T omega, const TB* __restrict__ b, const T* __restrict__ xin,
-                                                  const T* __restrict__ rin, T* __restrict__ xout,
-                                                  T* __restrict__ rout) {
+__global__ void __launch_bounds__(TPB) k_resid(SellView S, const T* __restrict__ val, const TB* __restrict__ b,
+                                               const T* __restrict__ x, T* __restrict__ r) {
     SELL_LOOP(S) {
         const T acc = sell_row(S.col, val, (long long)S.sptr[s] * 32 + lane, S.sptr[s + 1] - S.sptr[s],
-                               [&](int j) { return fma(omega * ld(minv + j), ld(rin + j), ld(xin + j)); });
+                               [&](int j) { return ld(x + j); });
         const int ip = s * 32 + lane;
         if (ip < S.n) {
             const int i = sell_rowid(S, ip);
-            xout[i] = fma(omega * minv[i], rin[i], xin[i]);
-            rout[i] = (T)b[i] - acc;
+            r[i] = (T)b[i] - acc;
         }
     }
 }
@@ -743,7 +737,7 @@ double by_post2(const Level& L, int nc, int V, int Vo, bool dot, bool u) {
     return (double)L.ap_nnz * (V + 4) + (double)L.A.n * ((u ? 2.0 : 4.0) * V + 4 + Vo + (dot ? 8 : 0)) +
            (double)nc * V;
 }
-double by_pre_step(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 5.0 * V); }
+double by_resid(const Level& L, int V, int Vb) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (Vb + 2.0 * V); }
 double by_restrict(int n, int nc, int V) { return (double)n * (4 + 2.0 * V) + (double)nc * (4 + V); }
 double by_smooth(const Level& L, int V, int Vb, int Vo) { return (double)L.A.nnz * (V + 4) + (double)L.A.n * (2.0 * V + Vb + Vo); }
 double by_coarse(int nc, int Vi, int Vo) { return 8.0 * nc * nc + (double)nc * (Vi + Vo); }
@@ -865,7 +859,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         Level& Lv = h->lev[l];
         const SellView S = view(Lv);
         const int g = Lv.grid_pre[f32] ? Lv.grid_pre[f32] : sell_grid(h, S.nslices);
-        T *xa = vec(Lv, VX), *ra = vec(Lv, VR), *xb = vec(Lv, VT), *rb = vec(Lv, VU);
+        T *xa = vec(Lv, VX), *ra = vec(Lv, VR), *xb = vec(Lv, VT);
         const int Vb = l == 0 ? 8 : V;
         if (l == 0 && f32) {
             Scope sc_(&h->prof, st, K_CONVERT, 12.0 * Lv.A.n);
@@ -873,6 +867,11 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             KERNEL_CHECK();
         }
         const bool wideA = SA && !f32 && wide(Lv.A, WIDE_MIN_A);       // dense coarse level of a smoothed hierarchy
+        // pre sweeps: x_1 = omega M^-1 b with r_1 = b - A x_1 (k_pre, which with
+        // more sweeps to come stores x_2 = x_1 + omega M^-1 r_1 instead of x_1),
+        // x_{k+1} = x_k + omega M^-1 (b - A x_k) for k = 2 .. pre - 1, then the
+        // residual r = b - A x_pre
+        const bool more = pre > 1;
         if (wideA) {
             Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 ? 8 : V));
             const double* bl = l == 0 ? r : (const double*)vec(Lv, VB);
@@ -882,20 +881,30 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
             KERNEL_CHECK();
         } else {
             Scope sc_(&h->prof, st, l == 0 ? K_PRE_L0 : K_PRE, by_pre(Lv, V, l == 0 && !f32 ? 8 : V));
-            if (l == 0 && !f32) launch_pre<T, double>(U, g, st, S, valm(Lv), wm(Lv), omega, r, xa, ra);
-            else launch_pre<T, T>(U, g, st, S, valm(Lv), wm(Lv), omega, vec(Lv, VB), xa, ra);
+            if (l == 0 && !f32) launch_pre<T, double>(U || more, g, st, S, valm(Lv), wm(Lv), omega, r, xa, ra);
+            else launch_pre<T, T>(U || more, g, st, S, valm(Lv), wm(Lv), omega, vec(Lv, VB), xa, ra);
         }
-        for (int k = 1; k < pre; ++k) {
-            Scope sc_(&h->prof, st, K_PRE_STEP, by_pre_step(Lv, V, Vb));
+        // the dense-level path stored x_1: it takes one sweep more here
+        for (int k = wideA ? 1 : 2; k < pre; ++k) {
+            Scope sc_(&h->prof, st, K_PRE_STEP, by_smooth(Lv, V, Vb, V));
             if (wideA)
-                k_wide<W_STEP><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
-                    Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xa, Lv.minv, (const double*)ra,
-                    (double)omega, l == 0 ? r : (const double*)vec(Lv, VB), (double*)rb, (double*)xb);
-            else if (l == 0) k_pre_step<T, double><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, ra, xb, rb);
-            else k_pre_step<T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, ra, xb, rb);
+                k_wide<W_SMOOTH><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
+                    Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xa, Lv.minv, nullptr, (double)omega,
+                    l == 0 ? r : (const double*)vec(Lv, VB), (double*)xb, nullptr);
+            else if (l == 0) k_smooth<T, double, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, r, xa, xb);
+            else k_smooth<T, T, T><<<g, TPB, 0, st>>>(S, val(Lv), minv(Lv), omega, vec(Lv, VB), xa, xb);
             KERNEL_CHECK();
             std::swap(xa, xb);
-            std::swap(ra, rb);
+        }
+        if (more) {
+            Scope sc_(&h->prof, st, K_PRE_STEP, by_resid(Lv, V, Vb));
+            if (wideA)
+                k_wide<W_RES><<<wide_grid(h, Lv.A.n), TPB, 0, st>>>(
+                    Lv.A.n, Lv.A.ptr, Lv.A.col, Lv.A.val, (const double*)xa, nullptr, nullptr, 0.0,
+                    l == 0 ? r : (const double*)vec(Lv, VB), (double*)ra, nullptr);
+            else if (l == 0) k_resid<T, double><<<g, TPB, 0, st>>>(S, val(Lv), r, xa, ra);
+            else k_resid<T, T><<<g, TPB, 0, st>>>(S, val(Lv), vec(Lv, VB), xa, ra);
+            KERNEL_CHECK();
         }
         xcur[l] = xa;
         rcur[l] = ra;
