@@ -96,6 +96,7 @@ struct DevCsr {
     int* ptr = nullptr;
     int* col = nullptr;
     double* val = nullptr;
+    int max_row = 0;   // entries of the longest row (0: not known)
 };
 
 // SELL-32 (sliced ELLPACK, slice height 32, no row sorting): slice s holds

@@ -38,6 +38,19 @@ __device__ __forceinline__ int block_sum_int(int v) {
     return t;
 }
 
+// Block-wide maximum (any blockDim multiple of 32, <= 1024). All threads get it.
+__device__ __forceinline__ int block_max_int(int v) {
+    __shared__ int wm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max_int(v);
+    if (lane == 0) wm[wid] = v;
+    __syncthreads();
+    int t = (lane < nw) ? wm[lane] : 0;
+    t = warp_max_int(t);
+    __syncthreads();
+    return t;
+}
+
 // Block-wide sum in a fixed combination order (deterministic for a fixed
 // blockDim). All threads get the result.
 __device__ __forceinline__ double block_sum(double v) {

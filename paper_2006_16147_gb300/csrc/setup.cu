@@ -75,6 +75,15 @@ __global__ void k_check_rows(int n, const int* __restrict__ ptr, const int* __re
     }
 }
 
+// *mx = max(*mx, longest row): a block maximum, then one atomic per block.
+__global__ void k_max_row(int n, const int* __restrict__ ptr, int* mx) {
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, ptr[i + 1] - ptr[i]);
+    m = block_max_int(m);
+    if (threadIdx.x == 0 && m > 0) atomicMax(mx, m);
+}
+
 // dww[i] = (a_ii w_i) w_i, the per-vertex half of the weight denominator
 // (the same rounded value in every edge of i).
 __global__ void k_diag(int n, const int* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
@@ -714,6 +723,77 @@ __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict
         if (v < n) {
             if (gl == 0 && edges == e - b) atomicOr(err, 8);   // no non-edge ends the row
             for (int k = b + edges + gl; k < e; k += G) nq[k] = make_int2(-1, -1);
+        }
+    }
+}
+
+// The same (nq, suitor reset, row-end check) in one pass for a matrix whose
+// rows all hold at most G entries: a group of G lanes per row, lane t holds
+// entry t; its rank in the row comes from a shuffle sweep as in the edge
+// sort, and the mirror position, the rank of v in the row of u, from a scan
+// of u's (short) row: the entries of u's row that precede (c_uv, v) under
+// the strict order (larger weight, then smaller neighbour). c is symmetric,
+// so the scan compares against the same weight.
+template <int G>
+__global__ void __launch_bounds__(TPB) k_sort_mirror(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                     const double* __restrict__ c, int2* __restrict__ nq,
+                                                     unsigned long long* __restrict__ suitor, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int ng = (gridDim.x * blockDim.x) / G;
+    const int v0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int warp_first = v0 - (lane - gl) / G;     // every lane of a warp runs the same iterations
+    for (int it = 0; warp_first + it * ng < n; ++it) {
+        const int v = v0 + it * ng;
+        int b = 0, len = 0;
+        if (v < n) {
+            b = ptr[v];
+            len = ptr[v + 1] - b;
+            if (len > G) {                           // not a short-row matrix: the caller's bound is wrong
+                if (gl == 0) atomicOr(err, 16);
+                len = 0;
+            }
+        }
+        long long wk = (long long)0x8000000000000000ULL;
+        int u = -1, uk = 0x7fffffff;
+        bool edge = false;
+        if (gl < len) {
+            const double cw = c[b + gl];
+            u = col[b + gl];
+            edge = is_edge(cw);
+            if (edge) {
+                wk = weight_order(cw);
+                uk = u;
+            }
+        }
+        int better = 0, nedge = 0, nonedge_before = 0;
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            const long long wt = __shfl_sync(FULL_MASK, wk, t, G);
+            const int ut = __shfl_sync(FULL_MASK, uk, t, G);
+            const bool et = ut != 0x7fffffff;
+            nedge += et;
+            better += et && (wt > wk || (wt == wk && ut < uk));
+            nonedge_before += (t < gl && t < len && !et);
+        }
+        if (gl < len) {
+            int2 e = make_int2(-1, -1);
+            if (edge) {
+                const int bu = ptr[u], eu = ptr[u + 1];
+                int mr = 0;
+                for (int t = bu; t < eu; ++t) {
+                    const double cu = c[t];
+                    if (!is_edge(cu)) continue;
+                    const long long ku = weight_order(cu);
+                    mr += ku > wk || (ku == wk && col[t] < v);
+                }
+                e = make_int2(u, bu + mr);
+            }
+            nq[b + (edge ? better : nedge + nonedge_before)] = e;
+        }
+        if (gl == 0 && v < n) {
+            suitor[v] = NO_SUITOR;
+            if (nedge == len) atomicOr(err, 8);      // no non-edge ends the row
         }
     }
 }
@@ -1807,6 +1887,22 @@ int read_int(const int* dev, int* host, cudaStream_t st) {
     return *host;
 }
 
+// C.nnz from C.ptr[n] and C.max_row from a row-length maximum, with one
+// stream synchronisation.
+void finish_csr(amg_hierarchy* h, Scratch& S, DevCsr& C) {
+    cudaStream_t st = h->stream;
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 19, 0, sizeof(int), st));
+    if (C.n > 0) {
+        k_max_row<<<grid_for(h, C.n), TPB, 0, st>>>(C.n, C.ptr, S.cnt + 19);
+        KERNEL_CHECK();
+    }
+    CUDA_CHECK(cudaMemcpyAsync(S.host, C.ptr + C.n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(S.host + 1, S.cnt + 19, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    C.nnz = S.host[0];
+    C.max_row = S.host[1];
+}
+
 // The rows of a row product that the group kernel listed in (list, *nlist):
 // a block each up to ROW_CAPS[0] terms (rows left listed in S.qid, counted in
 // S.cnt[13]), then up to ROW_CAPS[1] (rows left in S.list0, S.cnt[14]), then
@@ -1872,6 +1968,25 @@ void sort_edges(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* spos) {
     KERNEL_CHECK();
 }
 
+// Proposals over the sorted rows in S.nq (suitor words reset), then mate.
+int suitor_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* err) {
+    cudaStream_t st = h->stream;
+    const int n = A.n;
+    Scope sc_(&h->prof, st, S_MATCH, 0.0);
+    if (n > 0) {
+        k_suitor<<<(n + 255) / 256, 256, 0, st>>>(n, (long long)A.nnz, A.ptr, S.nq, S.suitor, err);
+        KERNEL_CHECK();
+    }
+    k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.nq, S.suitor, S.mate, err);
+    KERNEL_CHECK();
+    const int e = read_int(err, S.host, st);
+    if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
+    if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
+    if (e & 16) AMG_THROW(AMG_ERR_CUDA, "matching: a row longer than the level's recorded longest row");
+    if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
+    return 0;
+}
+
 // The matching of one sweep into S.mate (partner, or < 0 unmatched).
 // Returns the number of locally-dominant rounds (0 for the proposal method,
 // which has none). match_kernel 0: proposals (k_suitor); 1: one launch pair
@@ -1884,6 +1999,22 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
     // algorithmic bytes of the edge sort (c, col in; nbr, spos out) and of
     // the mirror map (c, col, spos in, the mirror's spos gathered, nq out)
     const double sort_bytes = 20.0 * A.nnz + 8.0 * n, mirror_bytes = 28.0 * A.nnz + 16.0 * n;
+    if (h->opt.match_kernel == 0 && A.max_row > 0 && A.max_row <= 32) {
+        // short rows: edge order and mirror positions in one pass (c, col of
+        // the row and of its neighbours' rows in, nq out)
+        int* err = S.cnt + 16;
+        const int G = A.max_row <= 8 ? 8 : (A.max_row <= 16 ? 16 : 32);
+        {
+            Scope sc_(&h->prof, st, S_MATCH_SORT, 12.0 * A.nnz + 8.0 * A.nnz + 16.0 * n);
+            CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
+            const int blocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
+            if (G == 8) k_sort_mirror<8><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
+            else if (G == 16) k_sort_mirror<16><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
+            else k_sort_mirror<32><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
+            KERNEL_CHECK();
+        }
+        return suitor_match(h, S, A, err);
+    }
     if (h->opt.match_kernel == 0) {
         int* err = S.cnt + 16;
         {
@@ -1900,18 +2031,7 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
                 k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             KERNEL_CHECK();
         }
-        Scope sc_(&h->prof, st, S_MATCH, 0.0);
-        if (n > 0) {
-            k_suitor<<<(n + 255) / 256, 256, 0, st>>>(n, (long long)A.nnz, A.ptr, S.nq, S.suitor, err);
-            KERNEL_CHECK();
-        }
-        k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.nq, S.suitor, S.mate, err);
-        KERNEL_CHECK();
-        const int e = read_int(err, S.host, st);
-        if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
-        if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
-        if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
-        return 0;
+        return suitor_match(h, S, A, err);
     }
     if (h->opt.match_kernel == 2 && h->coop_blocks > 0) {
         int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
@@ -1991,7 +2111,7 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     C.n = nc;
     C.ptr = owner.alloc<int>(nc + 1);
     scan_exclusive(S.ub, C.ptr, nc, C.ptr + nc, st, S.scan_tmp);
-    C.nnz = read_int(C.ptr + nc, S.host, st);
+    finish_csr(h, S, C);
     C.col = owner.alloc<int>(C.nnz);
     C.val = owner.alloc<double>(C.nnz);
     launch_copy(h, C.nnz, nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val, st);
@@ -2224,7 +2344,7 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
     X.n = n;
     X.ptr = scratch ? S.mem.alloc<int>(n + 1) : h->mem.alloc<int>(n + 1);
     scan_exclusive(S.ub, X.ptr, n, X.ptr + n, st, S.scan_tmp);
-    X.nnz = read_int(X.ptr + n, S.host, st);
+    finish_csr(h, S, X);
     X.col = scratch ? S.mem.alloc<int>(X.nnz) : h->mem.alloc<int>(X.nnz);
     X.val = scratch ? S.mem.alloc<double>(X.nnz) : h->mem.alloc<double>(X.nnz);
     for (int t = 0; t < SPG_TIERS && rows[t] > 0; ++t) {
@@ -2393,7 +2513,17 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "row_ptr is not a valid CSR row pointer");
         k_check_rows<<<grid_for(h, n0), TPB, 0, st>>>(n0, L0.A.ptr, L0.A.col, L0.A.val, L0.w, S.diag, S.cnt + 5);
         KERNEL_CHECK();
-        f = read_int(S.cnt + 5, S.host, st);
+        // the flags and the longest row, one synchronisation
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 19, 0, sizeof(int), st));
+        if (n0 > 0) {
+            k_max_row<<<grid_for(h, n0), TPB, 0, st>>>(n0, L0.A.ptr, S.cnt + 19);
+            KERNEL_CHECK();
+        }
+        CUDA_CHECK(cudaMemcpyAsync(S.host, S.cnt + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_CHECK(cudaMemcpyAsync(S.host + 1, S.cnt + 19, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_CHECK(cudaStreamSynchronize(st));
+        f = S.host[0];
+        L0.A.max_row = S.host[1];
         if (f & F_SHAPE) AMG_THROW(AMG_ERR_ARG, "CSR columns unsorted, out of range, or pattern not symmetric");
         if (f & F_NOT_SPD) AMG_THROW(AMG_ERR_NOT_SPD, "non-finite value or diagonal entry missing or <= 0");
         if (f & F_BAD_W) AMG_THROW(AMG_ERR_BAD_W, "smooth vector w has a zero or non-finite entry");
