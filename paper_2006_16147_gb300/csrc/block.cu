@@ -3,10 +3,11 @@
 // Every column runs its own preconditioned CG (its own alpha, beta, rho and
 // convergence), while each sparse product and the V-cycle (Eq. 2) serve all k
 // columns in one pass over the matrices: the matrix is read once per k
-// columns. Vectors are row-major n x k. A group of G lanes (G = the power of
-// two >= k, at most 32) handles one row; lane gl owns columns gl, gl + G, ...
-// so the group reads each matrix entry once (broadcast) and the k values of a
-// gathered row of X as one coalesced segment.
+// columns. Vectors are row-major n x k. A group of G lanes handles one row;
+// lane gl owns the CPL consecutive columns gl * CPL .. gl * CPL + CPL - 1, so
+// the group reads each matrix entry once (broadcast) and a gathered row of X
+// as one coalesced segment, each lane's part as one vector load (float4,
+// float2 or double2) when the row stride is a multiple of CPL.
 //
 // Columns carry a state (ColMode): START columns enter at the V-cycle half of
 // a step (r given, z = B r, p = z), ACTIVE columns take a full CG step, a
@@ -16,6 +17,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 #include "device_util.cuh"
@@ -62,14 +64,98 @@ __device__ __forceinline__ Grp make_grp(int G) {
     return g;
 }
 
-// acc[m] += sum_e val_e * xv(col_e, c) for the row at SELL position ip, in
-// entry order. Four entries at a time (the last group predicated): their
-// indices and values are loaded first and the four gathered rows of X are in
-// flight together, so a row costs about two memory latencies per four
-// entries instead of two per entry.
-template <typename T, int CPL, typename XV>
-__device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__ val, int ip, const Grp& g, int k,
-                                           XV&& xv, T (&acc)[CPL]) {
+// The CPL consecutive values at p (a lane's columns of one row; lim of them
+// are live columns). With VEC the row stride is a multiple of CPL, so the
+// address is aligned to CPL values and all CPL lie inside the row: the loads
+// are vectors. Without VEC only the live columns are read. CG reads through
+// L2 only (values other blocks write during the launch).
+template <bool VEC, bool CG, int CPL, typename T>
+__device__ __forceinline__ void ld_cols(const T* p, T (&v)[CPL], int lim) {
+    if constexpr (VEC && std::is_same<T, float>::value && CPL >= 4) {
+#pragma unroll
+        for (int q = 0; q < CPL / 4; ++q) {
+            const float4 f = CG ? __ldcg(reinterpret_cast<const float4*>(p) + q)
+                                : __ldg(reinterpret_cast<const float4*>(p) + q);
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else if constexpr (VEC && std::is_same<T, float>::value && CPL == 2) {
+        const float2 f = CG ? __ldcg(reinterpret_cast<const float2*>(p)) : __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = f.x; v[1] = f.y;
+    } else if constexpr (VEC && std::is_same<T, double>::value && CPL >= 2) {
+#pragma unroll
+        for (int q = 0; q < CPL / 2; ++q) {
+            const double2 f = CG ? __ldcg(reinterpret_cast<const double2*>(p) + q)
+                                 : __ldg(reinterpret_cast<const double2*>(p) + q);
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) v[m] = m < lim ? (CG ? __ldcg(p + m) : __ldg(p + m)) : T(0);
+    }
+}
+
+// Plain loads of a lane's columns of a row that this kernel also writes.
+template <bool VEC, int CPL, typename T>
+__device__ __forceinline__ void ld_own(const T* p, T (&v)[CPL], int lim) {
+    if constexpr (VEC && std::is_same<T, float>::value && CPL >= 4) {
+#pragma unroll
+        for (int q = 0; q < CPL / 4; ++q) {
+            const float4 f = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        }
+    } else if constexpr (VEC && std::is_same<T, float>::value && CPL == 2) {
+        const float2 f = *reinterpret_cast<const float2*>(p);
+        v[0] = f.x; v[1] = f.y;
+    } else if constexpr (VEC && std::is_same<T, double>::value && CPL >= 2) {
+#pragma unroll
+        for (int q = 0; q < CPL / 2; ++q) {
+            const double2 f = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = f.x; v[2 * q + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < CPL; ++m) v[m] = m < lim ? p[m] : T(0);
+    }
+}
+
+// Stores a lane's columns of a row: one vector store when VEC and all of them
+// are live columns (c0 + CPL <= k), else one store per live column.
+template <bool VEC, int CPL, typename T>
+__device__ __forceinline__ void st_cols(T* p, const T (&v)[CPL], int c0, int k) {
+    if constexpr (VEC && std::is_same<T, float>::value && CPL >= 4) {
+        if (c0 + CPL <= k) {
+#pragma unroll
+            for (int q = 0; q < CPL / 4; ++q)
+                reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            return;
+        }
+    } else if constexpr (VEC && std::is_same<T, float>::value && CPL == 2) {
+        if (c0 + CPL <= k) {
+            *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+            return;
+        }
+    } else if constexpr (VEC && std::is_same<T, double>::value && CPL >= 2) {
+        if (c0 + CPL <= k) {
+#pragma unroll
+            for (int q = 0; q < CPL / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < CPL; ++m)
+        if (c0 + m < k) p[m] = v[m];
+}
+
+// acc[m] += sum_e val_e * X[col_e * ld + c0 + m] for the row at SELL position
+// ip, in entry order (a lane's columns c0 .. c0 + CPL - 1; a lane without a
+// live column returns at once). Four entries at a time (the last group
+// predicated): their indices and values are loaded first and the four
+// gathered rows of X are in flight together, so a row costs about two memory
+// latencies per four entries instead of two per entry.
+template <bool VEC, bool CG, int CPL, typename T>
+__device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__ val, int ip, int c0, int k,
+                                           const T* X, int ld, T (&acc)[CPL]) {
+    if (c0 >= k) return;
     const int s = ip >> 5, r = ip & 31;
     const int s0 = __ldg(S.sptr + s);
     const int w = __ldg(S.sptr + s + 1) - s0;
@@ -83,17 +169,13 @@ __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__
             j[u] = __ldg(S.col + base + 32 * u);
             a[u] = __ldg(val + base + 32 * u);
         }
+        T xs[4][CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) {
-                T xs[4];
+        for (int u = 0; u < 4; ++u) ld_cols<VEC, CG, CPL>(X + (size_t)j[u] * ld + c0, xs[u], k - c0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) xs[u] = xv(j[u], c);
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[m] = fma(a[u], xs[u], acc[m]);
-            }
-        }
+            for (int m = 0; m < CPL; ++m) acc[m] = fma(a[u], xs[u][m], acc[m]);
     }
     if (e < w) {                      // the last 1-3 entries as one predicated group of four
         int j[4];
@@ -104,18 +186,19 @@ __device__ __forceinline__ void sell_row_k(const SellV& S, const T* __restrict__
             j[u] = ok ? __ldg(S.col + base + 32 * u) : 0;
             a[u] = ok ? __ldg(val + base + 32 * u) : T(0);
         }
+        T xs[4][CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) {
-                T xs[4];
+        for (int u = 0; u < 4; ++u) {
+            if (e + u < w) ld_cols<VEC, CG, CPL>(X + (size_t)j[u] * ld + c0, xs[u], k - c0);
+            else
 #pragma unroll
-                for (int u = 0; u < 4; ++u) xs[u] = e + u < w ? xv(j[u], c) : T(0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (e + u < w) acc[m] = fma(a[u], xs[u], acc[m]);
-            }
+                for (int m = 0; m < CPL; ++m) xs[u][m] = T(0);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e + u < w)
+#pragma unroll
+                for (int m = 0; m < CPL; ++m) acc[m] = fma(a[u], xs[u][m], acc[m]);
     }
 }
 
@@ -138,7 +221,7 @@ __device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], co
     if (lane < g.G) {
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = lane + m * g.G;
+            const int c = lane * CPL + m;
             if (c < k) {
                 sm[warp][0][c] = v0[m];
                 sm[warp][1][c] = v1[m];
@@ -190,28 +273,30 @@ __device__ __forceinline__ void colsum2(double (&v0)[CPL], double (&v1)[CPL], co
 }
 
 // ---------------------------------------------------------- V-cycle --------
-template <typename T, typename TB, int CPL>
+template <typename T, int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_pre(SellV S, const T* __restrict__ valm, const T* __restrict__ minv, T omega,
-                                              const TB* __restrict__ B, T* __restrict__ X, T* __restrict__ R, int k, int ld,
+                                              const T* __restrict__ B, T* __restrict__ X, T* __restrict__ R, int k, int ld,
                                               int G) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
+    if (c0 >= k) return;
     for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
         T acc[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) acc[m] = 0;
-        sell_row_k<T, CPL>(S, valm, ip, g, k, [&](int j, int c) { return (T)__ldg(B + (size_t)j * ld + c); }, acc);
+        sell_row_k<VEC, false, CPL>(S, valm, ip, c0, k, B, ld, acc);
         const int i = rowid(S, ip);
         const T mi = omega * minv[i];
+        const size_t o = (size_t)i * ld + c0;
+        T bi[CPL], xo[CPL], ro[CPL];
+        ld_cols<VEC, false, CPL>(B + o, bi, k - c0);
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) {
-                const size_t o = (size_t)i * ld + c;
-                const T bi = (T)B[o];
-                X[o] = mi * bi;
-                R[o] = fma(-omega, acc[m], bi);
-            }
+            xo[m] = mi * bi[m];
+            ro[m] = fma(-omega, acc[m], bi[m]);
         }
+        st_cols<VEC, CPL>(X + o, xo, c0, k);
+        st_cols<VEC, CPL>(R + o, ro, c0, k);
     }
 }
 
@@ -225,11 +310,13 @@ __global__ void __launch_bounds__(TPB) bk_to_f32(long long n, int k, int ld, con
         if (k == ld || (int)(t % ld) < k) b[t] = (float)a[t];
 }
 
-template <typename T, int CPL>
+template <typename T, int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_restrict(int nc, const int* __restrict__ pt_ptr,
                                                    const int* __restrict__ pt_idx, const T* __restrict__ p,
                                                    const T* __restrict__ R, T* __restrict__ Bc, int k, int ld, int G) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
+    if (c0 >= k) return;
     for (int q = g.gw; q < nc; q += g.ngroups) {
         T acc[CPL];
 #pragma unroll
@@ -237,25 +324,22 @@ __global__ void __launch_bounds__(TPB) bk_restrict(int nc, const int* __restrict
         for (int e = pt_ptr[q]; e < pt_ptr[q + 1]; ++e) {
             const int i = __ldg(pt_idx + e);
             const T pi = __ldg(p + i);
+            T rv[CPL];
+            ld_cols<VEC, false, CPL>(R + (size_t)i * ld + c0, rv, k - c0);
 #pragma unroll
-            for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
-                if (c < k) acc[m] = fma(pi, __ldg(R + (size_t)i * ld + c), acc[m]);
-            }
+            for (int m = 0; m < CPL; ++m) acc[m] = fma(pi, rv[m], acc[m]);
         }
-#pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) Bc[(size_t)q * ld + c] = acc[m];
-        }
+        st_cols<VEC, CPL>(Bc + (size_t)q * ld + c0, acc, c0, k);
     }
 }
 
 // X = A_L^{-1} B on the coarsest level, FP64 arithmetic.
-template <typename TI, typename TO, int CPL>
+template <typename TI, typename TO, int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_coarse_dense(int n, const double* __restrict__ Ainv, const TI* __restrict__ B,
                                                        TO* __restrict__ X, int k, int ld, int G) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
+    if (c0 >= k) return;
     for (int i = g.gw; i < n; i += g.ngroups) {
         double acc[CPL];
 #pragma unroll
@@ -263,17 +347,15 @@ __global__ void __launch_bounds__(TPB) bk_coarse_dense(int n, const double* __re
         const double* row = Ainv + (size_t)i * n;
         for (int j = 0; j < n; ++j) {
             const double a = __ldg(row + j);
+            TI bv[CPL];
+            ld_cols<VEC, false, CPL>(B + (size_t)j * ld + c0, bv, k - c0);
 #pragma unroll
-            for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
-                if (c < k) acc[m] = fma(a, (double)__ldg(B + (size_t)j * ld + c), acc[m]);
-            }
+            for (int m = 0; m < CPL; ++m) acc[m] = fma(a, (double)bv[m], acc[m]);
         }
+        TO xo[CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) X[(size_t)i * ld + c] = (TO)acc[m];
-        }
+        for (int m = 0; m < CPL; ++m) xo[m] = (TO)acc[m];
+        st_cols<VEC, CPL>(X + (size_t)i * ld + c0, xo, c0, k);
     }
 }
 
@@ -296,7 +378,7 @@ __device__ __forceinline__ void fin_rz(const BlockScalars& sc, int c, double rz,
 // out = x + P e + omega M^-1 r - (omega M^-1 A P) e (the stored A P values
 // carry the row scaling); on level 0 also r_cg . out and
 // (flexible CG) q . out per column.
-template <typename T, typename TO, int CPL, bool DOT>
+template <typename T, typename TO, int CPL, bool DOT, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ apval, const T* __restrict__ minv,
                                                T omega, const int* __restrict__ agg, const T* __restrict__ p,
                                                const T* __restrict__ E, const T* __restrict__ X,
@@ -304,29 +386,41 @@ __global__ void __launch_bounds__(TPB) bk_post(SellV SAP, const T* __restrict__ 
                                                const double* __restrict__ Q2, TO* __restrict__ Out, int k, int ld, int G,
                                                double* partial, unsigned* ticket, BlockScalars sc, int flexible) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
     double d0[CPL], d1[CPL];
 #pragma unroll
     for (int m = 0; m < CPL; ++m) d0[m] = d1[m] = 0.0;
-    for (int ip = g.gw; ip < SAP.n; ip += g.ngroups) {
-        T acc[CPL];
+    if (c0 < k) {
+        for (int ip = g.gw; ip < SAP.n; ip += g.ngroups) {
+            T acc[CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) acc[m] = 0;
-        sell_row_k<T, CPL>(SAP, apval, ip, g, k, [&](int q, int c) { return __ldg(E + (size_t)q * ld + c); }, acc);
-        const int i = rowid(SAP, ip);
-        const int a = agg[i];
-        const T pi = p[i];
-        const T mi = omega * minv[i];
+            for (int m = 0; m < CPL; ++m) acc[m] = 0;
+            sell_row_k<VEC, false, CPL>(SAP, apval, ip, c0, k, E, ld, acc);
+            const int i = rowid(SAP, ip);
+            const int a = agg[i];
+            const T pi = p[i];
+            const T mi = omega * minv[i];
+            const size_t o = (size_t)i * ld + c0;
+            T ev[CPL], xv[CPL], rv[CPL];
+            TO ov[CPL];
+            ld_cols<VEC, false, CPL>(E + (size_t)a * ld + c0, ev, k - c0);
+            ld_cols<VEC, false, CPL>(X + o, xv, k - c0);
+            ld_cols<VEC, false, CPL>(R + o, rv, k - c0);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) {
-                const size_t o = (size_t)i * ld + c;
-                const T y = fma(pi, E[(size_t)a * ld + c], X[o]);
-                const T v = fma(mi, R[o], y) - acc[m];          // acc: rows of omega M^-1 A P
-                Out[o] = (TO)v;
-                if (DOT) {
-                    d0[m] = fma(Bdot[o], (double)(TO)v, d0[m]);
-                    if (Q2) d1[m] = fma(Q2[o], (double)(TO)v, d1[m]);
+            for (int m = 0; m < CPL; ++m) {
+                const T y = fma(pi, ev[m], xv[m]);
+                ov[m] = (TO)(fma(mi, rv[m], y) - acc[m]);         // acc: rows of omega M^-1 A P
+            }
+            st_cols<VEC, CPL>(Out + o, ov, c0, k);
+            if (DOT) {
+                double bd[CPL], qd[CPL];
+                ld_cols<VEC, false, CPL>(Bdot + o, bd, k - c0);
+                if (Q2) ld_cols<VEC, false, CPL>(Q2 + o, qd, k - c0);
+#pragma unroll
+                for (int m = 0; m < CPL; ++m) {
+                    if (c0 + m >= k) continue;
+                    d0[m] = fma(bd[m], (double)ov[m], d0[m]);
+                    if (Q2) d1[m] = fma(qd[m], (double)ov[m], d1[m]);
                 }
             }
         }
@@ -379,7 +473,7 @@ __device__ __forceinline__ void bk_colpart(double (&v)[CPL], const Grp& g, int k
     if (lane < g.G) {
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = lane + m * g.G;
+            const int c = lane * CPL + m;
             if (c < k) sm[warp][c] = v[m];
         }
     }
@@ -432,7 +526,7 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
         const double mi = minv[i];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
+            const int c = g.gl * CPL + m;
             if (c >= k) continue;
             const size_t o = (size_t)i * ld + c;
             const double bi = (double)B[o];
@@ -469,12 +563,11 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
             double acc[CPL];
 #pragma unroll
             for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
-            sell_row_k<double, CPL>(S, sval, ip, g, k, [&](int j, int c) { return __ldcg(p + (size_t)j * ld + c); },
-                                    acc);
+            sell_row_k<false, true, CPL>(S, sval, ip, g.gl * CPL, k, (const double*)p, ld, acc);
             const int i = rowid(S, ip);
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
+                const int c = g.gl * CPL + m;
                 if (c >= k) continue;
                 const size_t o = (size_t)i * ld + c;
                 q[o] = acc[m];
@@ -490,9 +583,10 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
                 a = warp_sum(a);
                 const size_t o = (size_t)i * ld + c;
                 if (lane == 0) q[o] = a;
+                // the first group of the warp carries the long rows' share of p . q
 #pragma unroll
                 for (int m = 0; m < CPL; ++m)
-                    if (lane + m * G == c) d0[m] = fma(__ldcg(p + o), a, d0[m]);
+                    if (lane < G && lane * CPL + m == c) d0[m] = fma(__ldcg(p + o), a, d0[m]);
             }
         }
         bk_colpart<CPL>(d0, g, k, slot());
@@ -504,14 +598,14 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
         double al[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
+            const int c = g.gl * CPL + m;
             al[m] = (c < k && s_live[c]) ? s_rho[c] / s_t[c] : 0.0;
             d0[m] = 0.0;
         }
         for (int i = g.gw; i < n; i += g.ngroups) {
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
+                const int c = g.gl * CPL + m;
                 if (c >= k || al[m] == 0.0) continue;
                 const size_t o = (size_t)i * ld + c;
                 x[o] = fma(al[m], __ldcg(p + o), x[o]);
@@ -535,7 +629,7 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
             const double mi = minv[i];
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
+                const int c = g.gl * CPL + m;
                 if (c >= k || !s_live[c]) continue;
                 const size_t o = (size_t)i * ld + c;
                 const double zi = mi * r[o];
@@ -551,7 +645,7 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
         double be[CPL];
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
+            const int c = g.gl * CPL + m;
             be[m] = (c < k && s_live[c]) ? s_t[c] / s_rho[c] : 0.0;
         }
         __syncthreads();
@@ -560,7 +654,7 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
         for (int i = g.gw; i < n; i += g.ngroups) {
 #pragma unroll
             for (int m = 0; m < CPL; ++m) {
-                const int c = g.gl + m * g.G;
+                const int c = g.gl * CPL + m;
                 if (c >= k || !s_live[c]) continue;
                 const size_t o = (size_t)i * ld + c;
                 p[o] = fma(be[m], p[o], z[o]);
@@ -572,7 +666,7 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
     for (int i = g.gw; i < n; i += g.ngroups) {
 #pragma unroll
         for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
+            const int c = g.gl * CPL + m;
             if (c < k) Xo[(size_t)i * ld + c] = (TO)x[(size_t)i * ld + c];
         }
     }
@@ -580,28 +674,29 @@ __global__ void __launch_bounds__(TPB) bk_coarse_cg(SellV S, const double* __res
 
 // ------------------------------------------------------------- CG ----------
 // Q = A P; p . q per column; alpha = rho / p.q for ACTIVE columns, else 0.
-template <int CPL>
+template <int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __restrict__ val,
                                                    const double* __restrict__ P, double* __restrict__ Q, int k, int ld, int G,
                                                    double* partial, unsigned* ticket, BlockScalars sc) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
     double d0[CPL], d1[CPL];
 #pragma unroll
     for (int m = 0; m < CPL; ++m) d0[m] = d1[m] = 0.0;
-    for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
-        double acc[CPL];
+    if (c0 < k) {
+        for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
+            double acc[CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
-        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(P + (size_t)j * ld + c); }, acc);
-        const int i = rowid(S, ip);
+            for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
+            sell_row_k<VEC, false, CPL>(S, val, ip, c0, k, P, ld, acc);
+            const int i = rowid(S, ip);
+            const size_t o = (size_t)i * ld + c0;
+            double pv[CPL];
+            ld_cols<VEC, false, CPL>(P + o, pv, k - c0);
+            st_cols<VEC, CPL>(Q + o, acc, c0, k);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            const int c = g.gl + m * g.G;
-            if (c < k) {
-                const size_t o = (size_t)i * ld + c;
-                Q[o] = acc[m];
-                d0[m] = fma(P[o], acc[m], d0[m]);
-            }
+            for (int m = 0; m < CPL; ++m)
+                if (c0 + m < k) d0[m] = fma(pv[m], acc[m], d0[m]);
         }
     }
     colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double pq, double) {
@@ -621,31 +716,43 @@ __global__ void __launch_bounds__(TPB) bk_spmv_dot(SellV S, const double* __rest
 }
 
 // ACTIVE columns: X += alpha P, R -= alpha Q, ||R||^2; convergence -> CHECK.
-template <int CPL>
+// Other columns are written back unchanged when a vector store covers them.
+template <int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restrict__ P, const double* __restrict__ Q,
                                                     double* __restrict__ X, double* __restrict__ R, int k, int ld, int G,
                                                     double* partial, unsigned* ticket, BlockScalars sc) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
     double al[CPL];
     bool on[CPL];
+    bool any = false;
 #pragma unroll
     for (int m = 0; m < CPL; ++m) {
-        const int c = g.gl + m * g.G;
+        const int c = c0 + m;
         on[m] = c < k && sc.mode[c] == COL_ACTIVE;
         al[m] = on[m] ? sc.alpha[c] : 0.0;
+        any |= on[m];
     }
     double d0[CPL], d1[CPL];
 #pragma unroll
     for (int m = 0; m < CPL; ++m) d0[m] = d1[m] = 0.0;
-    for (int i = g.gw; i < n; i += g.ngroups) {
+    if (any) {
+        for (int i = g.gw; i < n; i += g.ngroups) {
+            const size_t o = (size_t)i * ld + c0;
+            double pv[CPL], qv[CPL], xv[CPL], rv[CPL];
+            ld_cols<VEC, false, CPL>(P + o, pv, k - c0);
+            ld_cols<VEC, false, CPL>(Q + o, qv, k - c0);
+            ld_own<VEC, CPL>(X + o, xv, k - c0);
+            ld_own<VEC, CPL>(R + o, rv, k - c0);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            if (!on[m]) continue;
-            const size_t o = (size_t)i * ld + g.gl + m * g.G;
-            X[o] = fma(al[m], P[o], X[o]);
-            const double ri = fma(-al[m], Q[o], R[o]);
-            R[o] = ri;
-            d0[m] = fma(ri, ri, d0[m]);
+            for (int m = 0; m < CPL; ++m) {
+                if (!on[m]) continue;
+                xv[m] = fma(al[m], pv[m], xv[m]);
+                rv[m] = fma(-al[m], qv[m], rv[m]);
+                d0[m] = fma(rv[m], rv[m], d0[m]);
+            }
+            st_cols<VEC, CPL>(X + o, xv, c0, k);
+            st_cols<VEC, CPL>(R + o, rv, c0, k);
         }
     }
     colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double rr, double) {
@@ -657,25 +764,31 @@ __global__ void __launch_bounds__(TPB) bk_update_xr(int n, const double* __restr
 }
 
 // ACTIVE columns: P = Z + beta P (P = Z when beta = 0, whatever P held).
-template <int CPL>
+template <int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_update_p(int n, const double* __restrict__ Z, double* __restrict__ P, int k,
                                                    int ld, int G, BlockScalars sc) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
     double be[CPL];
     bool on[CPL];
+    bool any = false;
 #pragma unroll
     for (int m = 0; m < CPL; ++m) {
-        const int c = g.gl + m * g.G;
+        const int c = c0 + m;
         on[m] = c < k && sc.mode[c] == COL_ACTIVE;
         be[m] = on[m] ? sc.beta[c] : 0.0;
+        any |= on[m];
     }
+    if (!any) return;
     for (int i = g.gw; i < n; i += g.ngroups) {
+        const size_t o = (size_t)i * ld + c0;
+        double zv[CPL], pv[CPL];
+        ld_cols<VEC, false, CPL>(Z + o, zv, k - c0);
+        ld_own<VEC, CPL>(P + o, pv, k - c0);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            if (!on[m]) continue;
-            const size_t o = (size_t)i * ld + g.gl + m * g.G;
-            P[o] = be[m] == 0.0 ? Z[o] : fma(be[m], P[o], Z[o]);
-        }
+        for (int m = 0; m < CPL; ++m)
+            if (on[m]) pv[m] = be[m] == 0.0 ? zv[m] : fma(be[m], pv[m], zv[m]);
+        st_cols<VEC, CPL>(P + o, pv, c0, k);
     }
 }
 
@@ -685,37 +798,45 @@ __global__ void __launch_bounds__(TPB) bk_update_p(int n, const double* __restri
 //   stage 1 (check): CHECK columns; true residual below rtol -> DONE, else the
 //                    column restarts from R (START).
 //   stage 2 (report): every column; only records ||R||^2 in rr.
-template <int CPL>
+// Columns not selected keep their R when a vector store covers them.
+template <int CPL, bool VEC>
 __global__ void __launch_bounds__(TPB) bk_residual(SellV S, const double* __restrict__ val,
                                                    const double* __restrict__ X, const double* __restrict__ B,
                                                    double* __restrict__ R, int k, int ld, int G, double* partial,
                                                    unsigned* ticket, BlockScalars sc, int stage) {
     const Grp g = make_grp(G);
+    const int c0 = g.gl * CPL;
     bool on[CPL];
+    bool any = false;
 #pragma unroll
     for (int m = 0; m < CPL; ++m) {
-        const int c = g.gl + m * g.G;
+        const int c = c0 + m;
         const int md = c < k ? sc.mode[c] : COL_IDLE;
         on[m] = c < k && (stage == 0 ? md == COL_INIT : (stage == 1 ? md == COL_CHECK : true));
+        any |= on[m];
     }
     double d0[CPL], d1[CPL];
 #pragma unroll
     for (int m = 0; m < CPL; ++m) d0[m] = d1[m] = 0.0;
-    for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
-        double acc[CPL];
+    if (any) {
+        for (int ip = g.gw; ip < S.n; ip += g.ngroups) {
+            double acc[CPL];
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
-        sell_row_k<double, CPL>(S, val, ip, g, k, [&](int j, int c) { return __ldg(X + (size_t)j * ld + c); }, acc);
-        const int i = rowid(S, ip);
+            for (int m = 0; m < CPL; ++m) acc[m] = 0.0;
+            sell_row_k<VEC, false, CPL>(S, val, ip, c0, k, X, ld, acc);
+            const int i = rowid(S, ip);
+            const size_t o = (size_t)i * ld + c0;
+            double bv[CPL], rv[CPL];
+            ld_cols<VEC, false, CPL>(B + o, bv, k - c0);
+            ld_own<VEC, CPL>(R + o, rv, k - c0);
 #pragma unroll
-        for (int m = 0; m < CPL; ++m) {
-            if (!on[m]) continue;
-            const size_t o = (size_t)i * ld + g.gl + m * g.G;
-            const double bi = B[o];
-            const double ri = bi - acc[m];
-            R[o] = ri;
-            d0[m] = fma(ri, ri, d0[m]);
-            d1[m] = fma(bi, bi, d1[m]);
+            for (int m = 0; m < CPL; ++m) {
+                if (!on[m]) continue;
+                rv[m] = bv[m] - acc[m];
+                d0[m] = fma(rv[m], rv[m], d0[m]);
+                d1[m] = fma(bv[m], bv[m], d1[m]);
+            }
+            st_cols<VEC, CPL>(R + o, rv, c0, k);
         }
     }
     colsum2<CPL>(d0, d1, g, k, ld, partial, ticket, [&](int c, double rr, double bb) {
@@ -791,13 +912,20 @@ void group_shape(const BlockWork& W, int k, int* G, int* cpl) {
     *cpl = pow2_at_least((k + g - 1) / g);
 }
 
-#define DISPATCH_CPL(cpl, ...)                          \
-    switch (cpl) {                                      \
-        case 1: { constexpr int CPL = 1; __VA_ARGS__; } break; \
-        case 2: { constexpr int CPL = 2; __VA_ARGS__; } break; \
-        case 4: { constexpr int CPL = 4; __VA_ARGS__; } break; \
-        default: { constexpr int CPL = 8; __VA_ARGS__; } break; \
-    }
+// CPL columns per lane, as vectors (VEC) when the row stride ld is a multiple of CPL.
+#define DISPATCH_ONE(cpl_, vec, ...)                                                               \
+    if (vec) { constexpr int CPL = cpl_; constexpr bool VEC = true; (void)VEC; __VA_ARGS__; }        \
+    else { constexpr int CPL = cpl_; constexpr bool VEC = false; (void)VEC; __VA_ARGS__; }
+#define DISPATCH_CPL(cpl, ld, ...)                                                                 \
+    do {                                                                                           \
+        const bool vec_ = (cpl) > 1 && (ld) % (cpl) == 0;                                          \
+        switch (cpl) {                                                                             \
+            case 1: { constexpr int CPL = 1; constexpr bool VEC = false; (void)VEC; __VA_ARGS__; } break; \
+            case 2: { DISPATCH_ONE(2, vec_, __VA_ARGS__) } break;                                   \
+            case 4: { DISPATCH_ONE(4, vec_, __VA_ARGS__) } break;                                   \
+            default: { DISPATCH_ONE(8, vec_, __VA_ARGS__) } break;                                  \
+        }                                                                                          \
+    } while (0)
 
 int grid_rows(const amg_hierarchy* h, long long rows, int G) {
     const long long groups_per_block = (long long)WARPS * (32 / G);
@@ -828,23 +956,23 @@ void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
             KERNEL_CHECK();
         }
         if (l == 0 && !f32)
-            DISPATCH_CPL(cpl, bk_pre<T, double, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, W.R, lv(W.x, 0),
-                                                                       lv(W.r, 0), k, ld, G))
+            DISPATCH_CPL(cpl, ld, bk_pre<T, CPL, VEC><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, (const T*)W.R, lv(W.x, 0),
+                                                                       lv(W.r, 0), k, ld, G));
         else
-            DISPATCH_CPL(cpl, bk_pre<T, T, CPL><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, lv(W.b, l), lv(W.x, l),
-                                                                  lv(W.r, l), k, ld, G))
+            DISPATCH_CPL(cpl, ld, bk_pre<T, CPL, VEC><<<g, TPB, 0, st>>>(sv(Lv.S), valm, minv, omega, lv(W.b, l), lv(W.x, l),
+                                                                  lv(W.r, l), k, ld, G));
         KERNEL_CHECK();
         const int nc = h->lev[l + 1].A.n;
         const T* p = f32 ? (const T*)Lv.p32 : (const T*)Lv.p;
-        DISPATCH_CPL(cpl, bk_restrict<T, CPL><<<grid_rows(h, nc, G), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, p,
-                                                                                   lv(W.r, l), lv(W.b, l + 1), k, ld, G))
+        DISPATCH_CPL(cpl, ld, bk_restrict<T, CPL, VEC><<<grid_rows(h, nc, G), TPB, 0, st>>>(nc, Lv.pt_ptr, Lv.pt_idx, p,
+                                                                                   lv(W.r, l), lv(W.b, l + 1), k, ld, G));
         KERNEL_CHECK();
     }
     {
         Scope sc_(&h->prof, st, K_COARSE, 8.0 * h->nc * h->nc + 16.0 * h->nc * k);
         if (!h->coarse_cg) {
-            DISPATCH_CPL(cpl, bk_coarse_dense<T, T, CPL><<<grid_rows(h, h->nc, G), TPB, 0, st>>>(
-                                  h->nc, h->coarse_inv, lv(W.b, L), lv(W.x, L), k, ld, G))
+            DISPATCH_CPL(cpl, ld, bk_coarse_dense<T, T, CPL, VEC><<<grid_rows(h, h->nc, G), TPB, 0, st>>>(
+                                  h->nc, h->coarse_inv, lv(W.b, L), lv(W.x, L), k, ld, G));
             KERNEL_CHECK();
         } else {
             Level& Lc = h->lev[L];
@@ -866,7 +994,7 @@ void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
                             (void*)&cval, (void*)&cminv, (void*)&bin, (void*)&xout, &kk, &ldd, &GG, &W.cw[0],
                             &W.cw[1], &W.cw[2], &W.cw[3], &W.cw[4], &W.cpart, &bar, &err, &maxit, &rtol};
             const void* fn = nullptr;
-            DISPATCH_CPL(cpl, fn = (const void*)bk_coarse_cg<T, T, CPL>)
+            DISPATCH_CPL(cpl, ld, fn = (const void*)bk_coarse_cg<T, T, CPL>);
             CUDA_CHECK(cudaLaunchCooperativeKernel(fn, dim3(h->num_sms), dim3(TPB), args, 0, st));
             KERNEL_CHECK();
         }
@@ -881,13 +1009,13 @@ void block_vcycle(amg_hierarchy* h, BlockWork& W, int k, int flexible) {
         Scope sc_(&h->prof, st, l == 0 ? K_POST_L0 : K_POST,
                   (double)Lv.ap_nnz * (sizeof(T) + 4) + (double)Lv.A.n * k * (4.0 * sizeof(T) + 8));
         if (l > 0)
-            DISPATCH_CPL(cpl, bk_post<T, T, CPL, false><<<g, TPB, 0, st>>>(
+            DISPATCH_CPL(cpl, ld, bk_post<T, T, CPL, false, VEC><<<g, TPB, 0, st>>>(
                                   sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, l), lv(W.r, l), nullptr, nullptr,
-                                  lv(W.y, l), k, ld, G, W.partial, W.ticket, W.sc, flexible))
+                                  lv(W.y, l), k, ld, G, W.partial, W.ticket, W.sc, flexible));
         else
-            DISPATCH_CPL(cpl, bk_post<T, double, CPL, true><<<W.grid, TPB, 0, st>>>(
+            DISPATCH_CPL(cpl, ld, bk_post<T, double, CPL, true, VEC><<<W.grid, TPB, 0, st>>>(
                                   sv(Lv.AP), apv, minv, omega, Lv.agg, p, e, lv(W.x, 0), lv(W.r, 0), W.R,
-                                  flexible ? W.Q : nullptr, W.Z, k, ld, G, W.partial, W.ticket, W.sc, flexible))
+                                  flexible ? W.Q : nullptr, W.Z, k, ld, G, W.partial, W.ticket, W.sc, flexible));
         KERNEL_CHECK();
     }
 }
@@ -1028,8 +1156,8 @@ void block_init_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     int G, cpl;
     group_shape(W, k, &G, &cpl);
     Level& L0 = h->lev[0];
-    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G, W.partial,
-                                                             W.ticket, W.sc, 0))
+    DISPATCH_CPL(cpl, W.K, bk_residual<CPL, VEC><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G, W.partial,
+                                                             W.ticket, W.sc, 0));
     KERNEL_CHECK();
     bk_zero_cols<<<blocks_for((long long)L0.A.n * k, TPB, h->num_sms * 8), TPB, 0, st>>>(L0.A.n, X, k, W.K, W.sc.mode,
                                                                                       W.sc.bb);
@@ -1053,14 +1181,14 @@ void block_step_kernels(amg_hierarchy* h, double* X, int k, bool any_active) {
     if (any_active) {
         {
             Scope sc_(&h->prof, st, K_SPMV_DOT, 12.0 * nnz + 16.0 * n * k);
-            DISPATCH_CPL(cpl, bk_spmv_dot<CPL><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, W.P, W.Q, k, ld, G,
-                                                                     W.partial, W.ticket, W.sc))
+            DISPATCH_CPL(cpl, ld, bk_spmv_dot<CPL, VEC><<<W.grid, TPB, 0, st>>>(sv(L0.S), L0.S.val, W.P, W.Q, k, ld, G,
+                                                                     W.partial, W.ticket, W.sc));
             KERNEL_CHECK();
         }
         {
             Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n * k);
-            DISPATCH_CPL(cpl, bk_update_xr<CPL><<<W.grid, TPB, 0, st>>>(n, W.P, W.Q, X, W.R, k, ld, G, W.partial,
-                                                                      W.ticket, W.sc))
+            DISPATCH_CPL(cpl, ld, bk_update_xr<CPL, VEC><<<W.grid, TPB, 0, st>>>(n, W.P, W.Q, X, W.R, k, ld, G, W.partial,
+                                                                      W.ticket, W.sc));
             KERNEL_CHECK();
         }
     }
@@ -1068,7 +1196,7 @@ void block_step_kernels(amg_hierarchy* h, double* X, int k, bool any_active) {
     else block_vcycle<double>(h, W, k, flexible);
     {
         Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n * k);
-        DISPATCH_CPL(cpl, bk_update_p<CPL><<<grid_rows(h, n, G), TPB, 0, st>>>(n, W.Z, W.P, k, ld, G, W.sc))
+        DISPATCH_CPL(cpl, ld, bk_update_p<CPL, VEC><<<grid_rows(h, n, G), TPB, 0, st>>>(n, W.Z, W.P, k, ld, G, W.sc));
         KERNEL_CHECK();
     }
 }
@@ -1153,8 +1281,8 @@ bool block_check_launch(amg_hierarchy* h, const double* B, double* X, int k) {
     Level& L0 = h->lev[0];
     const double nnz = (double)L0.A.nnz;
     Scope sc_(&h->prof, h->stream, K_RESIDUAL, 12.0 * nnz + 24.0 * L0.A.n * k);
-    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G,
-                                                                    W.partial, W.ticket, W.sc, 1))
+    DISPATCH_CPL(cpl, W.K, bk_residual<CPL, VEC><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.R, k, W.K, G,
+                                                                    W.partial, W.ticket, W.sc, 1));
     KERNEL_CHECK();
     copy_state_async(h, W);
     return true;
@@ -1165,8 +1293,8 @@ void block_report_launch(amg_hierarchy* h, const double* B, const double* X, int
     int G, cpl;
     group_shape(W, k, &G, &cpl);
     Level& L0 = h->lev[0];
-    DISPATCH_CPL(cpl, bk_residual<CPL><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.T, k, W.K, G,
-                                                                    W.partial, W.ticket, W.sc, 2))
+    DISPATCH_CPL(cpl, W.K, bk_residual<CPL, VEC><<<W.grid, TPB, 0, h->stream>>>(sv(L0.S), L0.S.val, X, B, W.T, k, W.K, G,
+                                                                    W.partial, W.ticket, W.sc, 2));
     KERNEL_CHECK();
     copy_state_async(h, W);
 }

@@ -329,22 +329,25 @@ __global__ void k_sort_edges(int n, const int* __restrict__ ptr, const int* __re
 // The same for rows of at most G entries, one group of G lanes per row: lane
 // t holds entry t, its rank among the row's edges under the strict order comes
 // from a shuffle sweep (edges have distinct keys), non-edges follow the edges
-// in position order; entries are written to their ranks. Longer rows are
-// listed in long_list for k_sort_edges.
+// in position order; entries are written to their ranks. With `list` set,
+// only the listed rows. Longer rows are listed in long_list for a pass with
+// more lanes or the block-per-row kernels.
 template <int G>
-__global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __restrict__ ptr,
+__global__ void __launch_bounds__(TPB) k_sort_edges_group(int n, const int* __restrict__ list,
+                                                         const int* __restrict__ nlist, const int* __restrict__ ptr,
                                                          const int* __restrict__ col, const double* __restrict__ c,
                                                          int* __restrict__ nbr, int* __restrict__ pos,
                                                          int* __restrict__ cand, int* mate, int* __restrict__ long_list,
                                                          int* __restrict__ nlong, int* __restrict__ spos) {
-    const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const int ng = (gridDim.x * blockDim.x) / G;
     const int v0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int warp_first = v0 - (lane - gl) / G;     // every lane of a warp runs the same iterations
-    for (int it = 0; warp_first + it * ng < n; ++it) {
-        const int v = v0 + it * ng;
+    const int nr = list ? min(*nlist, n) : n;        // with a list, only the rows list[0 .. *nlist)
+    for (int it = 0; warp_first + it * ng < nr; ++it) {
+        const int t = v0 + it * ng;
+        const int v = t < nr ? (list ? list[t] : t) : n;
         int b = 0, len = 0;
         if (v < n) {
             b = ptr[v];
@@ -727,77 +730,6 @@ __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict
     }
 }
 
-// The same (nq, suitor reset, row-end check) in one pass for a matrix whose
-// rows all hold at most G entries: a group of G lanes per row, lane t holds
-// entry t; its rank in the row comes from a shuffle sweep as in the edge
-// sort, and the mirror position, the rank of v in the row of u, from a scan
-// of u's (short) row: the entries of u's row that precede (c_uv, v) under
-// the strict order (larger weight, then smaller neighbour). c is symmetric,
-// so the scan compares against the same weight.
-template <int G>
-__global__ void __launch_bounds__(TPB) k_sort_mirror(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                                                     const double* __restrict__ c, int2* __restrict__ nq,
-                                                     unsigned long long* __restrict__ suitor, int* err) {
-    const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int ng = (gridDim.x * blockDim.x) / G;
-    const int v0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int warp_first = v0 - (lane - gl) / G;     // every lane of a warp runs the same iterations
-    for (int it = 0; warp_first + it * ng < n; ++it) {
-        const int v = v0 + it * ng;
-        int b = 0, len = 0;
-        if (v < n) {
-            b = ptr[v];
-            len = ptr[v + 1] - b;
-            if (len > G) {                           // not a short-row matrix: the caller's bound is wrong
-                if (gl == 0) atomicOr(err, 16);
-                len = 0;
-            }
-        }
-        long long wk = (long long)0x8000000000000000ULL;
-        int u = -1, uk = 0x7fffffff;
-        bool edge = false;
-        if (gl < len) {
-            const double cw = c[b + gl];
-            u = col[b + gl];
-            edge = is_edge(cw);
-            if (edge) {
-                wk = weight_order(cw);
-                uk = u;
-            }
-        }
-        int better = 0, nedge = 0, nonedge_before = 0;
-#pragma unroll
-        for (int t = 0; t < G; ++t) {
-            const long long wt = __shfl_sync(FULL_MASK, wk, t, G);
-            const int ut = __shfl_sync(FULL_MASK, uk, t, G);
-            const bool et = ut != 0x7fffffff;
-            nedge += et;
-            better += et && (wt > wk || (wt == wk && ut < uk));
-            nonedge_before += (t < gl && t < len && !et);
-        }
-        if (gl < len) {
-            int2 e = make_int2(-1, -1);
-            if (edge) {
-                const int bu = ptr[u], eu = ptr[u + 1];
-                int mr = 0;
-                for (int t = bu; t < eu; ++t) {
-                    const double cu = c[t];
-                    if (!is_edge(cu)) continue;
-                    const long long ku = weight_order(cu);
-                    mr += ku > wk || (ku == wk && col[t] < v);
-                }
-                e = make_int2(u, bu + mr);
-            }
-            nq[b + (edge ? better : nedge + nonedge_before)] = e;
-        }
-        if (gl == 0 && v < n) {
-            suitor[v] = NO_SUITOR;
-            if (nedge == len) atomicOr(err, 8);      // no non-edge ends the row
-        }
-    }
-}
-
 // One thread per vertex: its chain of proposals, and those of the vertices
 // it displaces. err |= 2 if a thread takes more steps than there are
 // entries (impossible for a valid mirror map; a guard, not a wait).
@@ -1078,7 +1010,8 @@ __global__ void __launch_bounds__(TPB) k_rap_copy(int nc, const int* __restrict_
 // canonical order of the thread-per-row kernels, bit for bit. Rows with more
 // than G terms are listed in long_list for those kernels.
 template <bool RAP, int G>
-__global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restrict__ heads,
+__global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restrict__ list,
+                                                  const int* __restrict__ nlist, const int* __restrict__ heads,
                                                   const int* __restrict__ mate, const int* __restrict__ ptr,
                                                   const int* __restrict__ col, const double* __restrict__ val,
                                                   const int* __restrict__ agg, const double* __restrict__ p,
@@ -1097,8 +1030,10 @@ __global__ void __launch_bounds__(TPB) k_rows_warp(int nrows, const int* __restr
     const int q0 = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     // every lane of a warp runs the same number of iterations (shuffles)
     const int warp_first = q0 - (gshift / G);
-    for (int it = 0; warp_first + it * ng < nrows; ++it) {
-        const int q = q0 + it * ng;
+    const int nr = list ? min(*nlist, nrows) : nrows;   // with a list, only the rows list[0 .. *nlist)
+    for (int it = 0; warp_first + it * ng < nr; ++it) {
+        const int t = q0 + it * ng;
+        const int q = t < nr ? (list ? list[t] : t) : nrows;
         int len = 0, l0 = 0, b0 = 0, b1 = 0, h = q, m = -1;
         if (q < nrows) {
             if (RAP) {
@@ -1181,20 +1116,23 @@ void launch_weights(int G, int grid_cap, cudaStream_t st, int n, const int* ptr,
     KERNEL_CHECK();
 }
 
+// Row products with G lanes per row (rows of more than G terms are listed in
+// long_list); with `list` set, only the rows list[0 .. *nlist).
 template <bool RAP>
 void launch_rows(amg_hierarchy* h, int G, int nrows, const int* heads, const int* mate, const int* ptr,
                  const int* col, const double* val, const int* agg, const double* p, const int* off, int* skey,
-                 double* sval, int* cnt, int* long_list, int* nlong, const double* rowscale, cudaStream_t st) {
-    const int blocks = blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
+                 double* sval, int* cnt, int* long_list, int* nlong, const double* rowscale, cudaStream_t st,
+                 const int* list = nullptr, const int* nlist = nullptr) {
+    const int blocks = list ? h->num_sms * 16 : blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
     if (G == 8)
-        k_rows_warp<RAP, 8><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                    long_list, nlong, rowscale);
+        k_rows_warp<RAP, 8><<<blocks, TPB, 0, st>>>(nrows, list, nlist, heads, mate, ptr, col, val, agg, p, off, skey,
+                                                    sval, cnt, long_list, nlong, rowscale);
     else if (G == 16)
-        k_rows_warp<RAP, 16><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                     long_list, nlong, rowscale);
+        k_rows_warp<RAP, 16><<<blocks, TPB, 0, st>>>(nrows, list, nlist, heads, mate, ptr, col, val, agg, p, off,
+                                                     skey, sval, cnt, long_list, nlong, rowscale);
     else
-        k_rows_warp<RAP, 32><<<blocks, TPB, 0, st>>>(nrows, heads, mate, ptr, col, val, agg, p, off, skey, sval, cnt,
-                                                     long_list, nlong, rowscale);
+        k_rows_warp<RAP, 32><<<blocks, TPB, 0, st>>>(nrows, list, nlist, heads, mate, ptr, col, val, agg, p, off,
+                                                     skey, sval, cnt, long_list, nlong, rowscale);
     KERNEL_CHECK();
 }
 
@@ -1910,7 +1848,18 @@ void finish_csr(amg_hierarchy* h, Scratch& S, DevCsr& C) {
 template <bool RAP>
 void launch_rows_long(amg_hierarchy* h, Scratch& S, int nrows, const int* list, const int* nlist, const int* heads,
                       const int* mate, const int* ptr, const int* col, const double* val, const int* agg,
-                      const double* p, const int* off, int* cnt, const double* rowscale, cudaStream_t st) {
+                      const double* p, const int* off, int* cnt, const double* rowscale, cudaStream_t st, int G,
+                      int max_terms) {
+    if (G < 32) {
+        // rows of G+1 .. 32 terms: a warp each (a block per row would spend a
+        // whole block and its barriers on a few dozen terms); longer ones go on
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 12, 0, sizeof(int), st));
+        launch_rows<RAP>(h, 32, nrows, heads, mate, ptr, col, val, agg, p, off, S.skey, S.sval, cnt, S.flag,
+                         S.cnt + 12, rowscale, st, list, nlist);
+        if (max_terms > 0 && max_terms <= 32) return;
+        list = S.flag;
+        nlist = S.cnt + 12;
+    }
     constexpr int tb = (int)(sizeof(unsigned long long) + sizeof(double));
     CUDA_CHECK(cudaFuncSetAttribute(k_rows_long<RAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROW_CAPS[1] * tb));
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 2 * sizeof(int), st));
@@ -1944,21 +1893,35 @@ void sort_edges(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* spos) {
     const int G = rows_group(A.nnz, n);
     const int gblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
     if (G == 8)
-        k_sort_edges_group<8><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                       S.cnt + 9, spos);
+        k_sort_edges_group<8><<<gblocks, TPB, 0, st>>>(n, nullptr, nullptr, A.ptr, A.col, S.c, nbr, pos, S.cand,
+                                                       S.mate, S.list1, S.cnt + 9, spos);
     else if (G == 16)
-        k_sort_edges_group<16><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                        S.cnt + 9, spos);
+        k_sort_edges_group<16><<<gblocks, TPB, 0, st>>>(n, nullptr, nullptr, A.ptr, A.col, S.c, nbr, pos, S.cand,
+                                                        S.mate, S.list1, S.cnt + 9, spos);
     else
-        k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.list1,
-                                                        S.cnt + 9, spos);
+        k_sort_edges_group<32><<<gblocks, TPB, 0, st>>>(n, nullptr, nullptr, A.ptr, A.col, S.c, nbr, pos, S.cand,
+                                                        S.mate, S.list1, S.cnt + 9, spos);
     KERNEL_CHECK();
-    // long rows: a block each in two capacities, then a thread each
+    if (A.max_row > 0 && A.max_row <= G) return;       // no row left for the long-row kernels
+    // rows of G+1 .. 32 entries: a warp each (a block per row would spend
+    // a whole block and its barriers on a few dozen entries)
+    const int* lrows = S.list1;
+    const int* nlrows = S.cnt + 9;
+    if (G < 32) {
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 12, 0, sizeof(int), st));
+        k_sort_edges_group<32><<<h->num_sms * 16, TPB, 0, st>>>(n, S.list1, S.cnt + 9, A.ptr, A.col, S.c, nbr, pos,
+                                                                 S.cand, S.mate, S.list0, S.cnt + 12, spos);
+        KERNEL_CHECK();
+        if (A.max_row > 0 && A.max_row <= 32) return;
+        lrows = S.list0;
+        nlrows = S.cnt + 12;
+    }
+    // longer rows: a block each in two capacities, then a thread each
     constexpr int eb = (int)(sizeof(long long) + sizeof(int));
     CUDA_CHECK(cudaFuncSetAttribute(k_sort_edges_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     EDGE_CAPS[1] * eb));
     k_sort_edges_long<<<h->num_sms * 4, LONG_TPB, EDGE_CAPS[0] * eb, st>>>(
-        S.list1, S.cnt + 9, EDGE_CAPS[0], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.qid, S.cnt + 13, spos);
+        lrows, nlrows, EDGE_CAPS[0], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.qid, S.cnt + 13, spos);
     KERNEL_CHECK();
     k_sort_edges_long<<<h->num_sms, LONG_TPB, EDGE_CAPS[1] * eb, st>>>(
         S.qid, S.cnt + 13, EDGE_CAPS[1], A.ptr, A.col, S.c, nbr, pos, S.cand, S.mate, S.heads, S.cnt + 14, spos);
@@ -1982,7 +1945,6 @@ int suitor_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* err) {
     const int e = read_int(err, S.host, st);
     if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
     if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
-    if (e & 16) AMG_THROW(AMG_ERR_CUDA, "matching: a row longer than the level's recorded longest row");
     if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
     return 0;
 }
@@ -1999,22 +1961,6 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
     // algorithmic bytes of the edge sort (c, col in; nbr, spos out) and of
     // the mirror map (c, col, spos in, the mirror's spos gathered, nq out)
     const double sort_bytes = 20.0 * A.nnz + 8.0 * n, mirror_bytes = 28.0 * A.nnz + 16.0 * n;
-    if (h->opt.match_kernel == 0 && A.max_row > 0 && A.max_row <= 32) {
-        // short rows: edge order and mirror positions in one pass (c, col of
-        // the row and of its neighbours' rows in, nq out)
-        int* err = S.cnt + 16;
-        const int G = A.max_row <= 8 ? 8 : (A.max_row <= 16 ? 16 : 32);
-        {
-            Scope sc_(&h->prof, st, S_MATCH_SORT, 12.0 * A.nnz + 8.0 * A.nnz + 16.0 * n);
-            CUDA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), st));
-            const int blocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
-            if (G == 8) k_sort_mirror<8><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
-            else if (G == 16) k_sort_mirror<16><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
-            else k_sort_mirror<32><<<blocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.nq, S.suitor, err);
-            KERNEL_CHECK();
-        }
-        return suitor_match(h, S, A, err);
-    }
     if (h->opt.match_kernel == 0) {
         int* err = S.cnt + 16;
         {
@@ -2103,10 +2049,12 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     KERNEL_CHECK();
     scan_exclusive(S.ub, S.off, nc, S.cnt + 6, st, S.scan_tmp);
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
-    launch_rows<true>(h, rows_group(2LL * A.nnz, A.n), nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
-                      S.skey, S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
-    launch_rows_long<true>(h, S, nc, S.list1, S.cnt + 8, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off,
-                           S.ub, nullptr, st);
+    const int G = rows_group(2LL * A.nnz, A.n);
+    launch_rows<true>(h, G, nc, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p, S.off, S.skey, S.sval, S.ub,
+                      S.list1, S.cnt + 8, nullptr, st);
+    if (A.max_row == 0 || 2 * A.max_row > G)            // a coarse row gathers the rows of its (at most two) members
+        launch_rows_long<true>(h, S, nc, S.list1, S.cnt + 8, S.heads, S.mate, A.ptr, A.col, A.val, sw.agg, sw.p,
+                               S.off, S.ub, nullptr, st, G, 2 * A.max_row);
     DevCsr C;
     C.n = nc;
     C.ptr = owner.alloc<int>(nc + 1);
@@ -2204,10 +2152,12 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     cudaStream_t st = h->stream;
     const int n = L.A.n;
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
-    launch_rows<false>(h, rows_group(L.A.nnz, n), n, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
-                       L.A.ptr, S.skey, S.sval, S.ub, S.list1, S.cnt + 8, L.wminv, st);
-    launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p,
-                            L.A.ptr, S.ub, L.wminv, st);
+    const int G = rows_group(L.A.nnz, n);
+    launch_rows<false>(h, G, n, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg, L.p, L.A.ptr, S.skey, S.sval,
+                       S.ub, S.list1, S.cnt + 8, L.wminv, st);
+    if (L.A.max_row == 0 || L.A.max_row > G)
+        launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg,
+                                L.p, L.A.ptr, S.ub, L.wminv, st, G, L.A.max_row);
     DevCsr AP;
     AP.n = n;
     AP.ptr = S.mem.alloc<int>(n + 1);
@@ -2390,10 +2340,12 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
 
     // rows of A P (canonical), compacted, then turned into rows of Pbar
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 8, 0, sizeof(int), st));
-    launch_rows<false>(h, rows_group(A.nnz, n), n, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr, S.skey,
-                       S.sval, S.ub, S.list1, S.cnt + 8, nullptr, st);
-    launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr,
-                            S.ub, nullptr, st);
+    const int G = rows_group(A.nnz, n);
+    launch_rows<false>(h, G, n, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p, A.ptr, S.skey, S.sval, S.ub,
+                       S.list1, S.cnt + 8, nullptr, st);
+    if (A.max_row == 0 || A.max_row > G)
+        launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, A.ptr, A.col, A.val, L.agg, L.p,
+                                A.ptr, S.ub, nullptr, st, G, A.max_row);
     DevCsr& P = L.pbar;
     P.n = n;
     P.ptr = h->mem.alloc<int>(n + 1);

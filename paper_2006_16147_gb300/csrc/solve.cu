@@ -604,32 +604,27 @@ __global__ void __launch_bounds__(512) k_coarse_cg(SellView S, const double* __r
             if (__ldcg(err)) return;
             const double alpha = rho / cg_sum(slot(0), G);
             ++red;
-            double rr = 0.0;
+            // x += alpha p, r -= alpha q, z = M^-1 r: r . r and r . z in one
+            // reduction (z is formed even on the last step, where it is unused)
+            double rr = 0.0, rz = 0.0;
             for (int i = tid; i < n; i += stride) {
                 x[i] = fma(alpha, __ldcg(p + i), x[i]);
                 const double ri = fma(-alpha, __ldcg(q + i), r[i]);
                 r[i] = ri;
                 rr = fma(ri, ri, rr);
+                const double zi = minv[i] * ri;
+                z[i] = zi;
+                rz = fma(ri, zi, rz);
             }
             rr = block_sum(rr);
-            if (threadIdx.x == 0) slot(0)[blockIdx.x] = rr;
+            rz = block_sum(rz);
+            if (threadIdx.x == 0) { slot(0)[blockIdx.x] = rr; slot(1)[blockIdx.x] = rz; }
             cg_grid_sync(bar, ++epoch, err);
             if (__ldcg(err)) return;
             const double rr_all = cg_sum(slot(0), G);
+            const double rho_new = cg_sum(slot(1), G);
             ++red;
             if (rr_all <= stop2) break;
-            double rz = 0.0;
-            for (int i = tid; i < n; i += stride) {
-                const double zi = minv[i] * r[i];
-                z[i] = zi;
-                rz = fma(r[i], zi, rz);
-            }
-            rz = block_sum(rz);
-            if (threadIdx.x == 0) slot(0)[blockIdx.x] = rz;
-            cg_grid_sync(bar, ++epoch, err);
-            if (__ldcg(err)) return;
-            const double rho_new = cg_sum(slot(0), G);
-            ++red;
             const double beta = rho_new / rho;
             rho = rho_new;
             for (int i = tid; i < n; i += stride) p[i] = fma(beta, p[i], z[i]);
