@@ -322,7 +322,8 @@ amg_status amg_match_noalloc(const amg_csr* A, const double* w, int32_t* mate, v
  * whether it was served alone or in a mix.
  *
  * amg_serve_poll returns up to max completed requests (id, status, latency
- * from submit to completion in ms, iterations, worst true relative residual);
+ * in ms from submit until the result is in the request's host X, iterations,
+ * worst true relative residual);
  * any output pointer may be NULL. amg_serve_stats fills latency percentiles
  * and throughput over all completed requests.
  */

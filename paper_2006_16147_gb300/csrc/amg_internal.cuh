@@ -209,7 +209,8 @@ struct BlockScalars {
 // Workspace of a block solve with K column slots (all arrays row-major n x K).
 struct BlockWork {
     int K = 0;
-    bool fixed_width = false;           // 32 lanes per row whatever the column count
+    bool fixed_width = false;           // lanes per row set by K, whatever the column count in flight
+    int vec_cols = 1;                   // columns per vector load: 4 (float) or 2 (double)
     int tuned_G = 0;                    // lanes per row chosen by the autotuner (0: heuristic)
     DevArena mem;
     std::vector<void*> b, x, r, y;      // per level V-cycle vectors (float or double)

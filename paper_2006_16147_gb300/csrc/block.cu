@@ -905,8 +905,10 @@ int pow2_at_least(int v) {
 // Group width and columns per lane for k active columns. With a fixed width
 // (set by the slot count K, not by k) a column's arithmetic and reduction
 // order do not depend on how many columns are in flight.
+// The default width gives each lane one vector's worth of columns (4 floats
+// or 2 doubles) when the columns fill the group.
 void group_shape(const BlockWork& W, int k, int* G, int* cpl) {
-    int g = std::min(32, pow2_at_least(W.fixed_width ? W.K : k));
+    int g = std::min(32, std::max(1, pow2_at_least(W.fixed_width ? W.K : k) / W.vec_cols));
     if (W.tuned_G && !W.fixed_width) g = std::min(W.tuned_G, pow2_at_least(k));
     *G = g;
     *cpl = pow2_at_least((k + g - 1) / g);
@@ -1095,6 +1097,7 @@ BlockWork& block_ensure(amg_hierarchy* h, int K, bool fixed_width) {
     W->K = K;
     W->fixed_width = fixed_width;
     const bool f32 = h->opt.precision == AMG_FP32_VCYCLE;
+    W->vec_cols = f32 ? 4 : 2;
     const size_t V = f32 ? 4 : 8;
     for (auto& L : h->lev) {
         const size_t m = (size_t)L.A.n * K;

@@ -206,10 +206,11 @@ void push_states(Served& sv) {
     CUDA_CHECK(cudaMemcpyAsync(W.sc.rtol, sv.rtol_host, sizeof(double) * sv.K, cudaMemcpyHostToDevice, sv.stream));
 }
 
-// Finished columns: copy out, free the slot, complete requests.
-void retire(amg_server* S, Served& sv, int maxit) {
+// Finished columns: copy out, free the slot; a request whose last column
+// finished has its copy to the host queued and is listed in `finished` (its
+// completion time is taken once that copy is done).
+void retire(amg_server* S, Served& sv, int maxit, std::vector<int64_t>& finished) {
     BlockWork& W = *sv.h->blk;
-    const double t = now_ms();
     for (int c = 0; c < sv.K; ++c) {
         const int64_t id = sv.owner[c];
         if (id < 0) continue;
@@ -234,12 +235,8 @@ void retire(amg_server* S, Served& sv, int maxit) {
                                        sv.stream));
             CUDA_CHECK(cudaFreeAsync(r.dX, sv.stream));
             r.dX = nullptr;
-            r.t_done = t;
             S->used -= request_bytes(sv, r.k);
-            S->latencies.push_back(r.t_done - r.t_submit);
-            S->completed.push_back(id);
-            ++S->done;
-            S->t_last = t;
+            finished.push_back(id);
         }
     }
 }
@@ -269,10 +266,21 @@ int64_t serve_step(amg_server* S) {
     if (again)
         for (size_t i = 0; i < S->hs.size(); ++i)
             if (width[i]) CUDA_CHECK(cudaStreamSynchronize(S->hs[i].stream));
+    std::vector<int64_t> finished;
     for (size_t i = 0; i < S->hs.size(); ++i)
-        if (width[i]) retire(S, S->hs[i], S->maxit);
+        if (width[i]) retire(S, S->hs[i], S->maxit, finished);
     for (size_t i = 0; i < S->hs.size(); ++i)
         if (width[i]) CUDA_CHECK(cudaStreamSynchronize(S->hs[i].stream));
+    // latency = submission to result in the caller's host buffer
+    const double t = now_ms();
+    for (int64_t id : finished) {
+        Request& r = S->reqs[id];
+        r.t_done = t;
+        S->latencies.push_back(r.t_done - r.t_submit);
+        S->completed.push_back(id);
+        ++S->done;
+        S->t_last = t;
+    }
     int64_t pending = 0;
     for (auto& sv : S->hs) {
         for (int c = 0; c < sv.K; ++c) pending += sv.owner[c] >= 0;
