@@ -474,6 +474,79 @@ __global__ void __launch_bounds__(LONG_TPB) k_sort_edges_long(const int* __restr
     }
 }
 
+// The same as k_sort_edges_long for rows of up to WROW entries, one warp per
+// listed row: the warp sorts its row in its own slice of shared memory with
+// warp barriers between the bitonic stages (a block and its barriers would
+// be spent on a few hundred entries). Longer rows go to `longer`.
+constexpr int WROW = 256;
+constexpr int WPB = TPB / 32;
+__global__ void __launch_bounds__(TPB) k_sort_edges_warp(const int* __restrict__ list, const int* __restrict__ nlist,
+                                                         const int* __restrict__ ptr, const int* __restrict__ col,
+                                                         const double* __restrict__ c, int* __restrict__ nbr,
+                                                         int* __restrict__ pos, int* __restrict__ cand, int* mate,
+                                                         int* __restrict__ longer, int* __restrict__ nlonger,
+                                                         int* __restrict__ spos) {
+    __shared__ long long WKs[WPB][WROW];
+    __shared__ int Us[WPB][WROW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long* WK = WKs[w];
+    int* U = Us[w];
+    const int nr = *nlist;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nr; t += nwarps) {
+        const int v = list[t];
+        const int b = ptr[v], len = ptr[v + 1] - b;
+        if (len > WROW) {
+            if (lane == 0) longer[atomicAdd(nlonger, 1)] = v;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < len) m2 <<= 1;
+        for (int s = lane; s < m2; s += 32) {
+            const double cw = s < len ? c[b + s] : -__longlong_as_double(0x7ff0000000000000LL);
+            const bool edge = is_edge(cw);
+            WK[s] = edge ? weight_order(cw) : (long long)0x8000000000000000ULL;
+            U[s] = edge ? col[b + s] : 0x7fffffff;
+        }
+        __syncwarp();
+        // x before y: edges first, then larger weight order, then smaller neighbour
+        auto before = [](long long wx, int ux, long long wy, int uy) {
+            const bool ex = ux != 0x7fffffff, ey = uy != 0x7fffffff;
+            if (ex != ey) return ex;
+            if (wx != wy) return wx > wy;
+            return ux < uy;
+        };
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int u = lane; u < m2 / 2; u += 32) {
+                    const int lo = 2 * u - (u & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const long long wl = WK[lo], wh = WK[hi];
+                    const int ul = U[lo], uh = U[hi];
+                    if (up ? before(wh, uh, wl, ul) : before(wl, ul, wh, uh)) {
+                        WK[lo] = wh;
+                        WK[hi] = wl;
+                        U[lo] = uh;
+                        U[hi] = ul;
+                    }
+                }
+                __syncwarp();
+            }
+        for (int s = lane; s < len; s += 32) {
+            nbr[b + s] = U[s] != 0x7fffffff ? U[s] : -1;
+            if (spos && U[s] != 0x7fffffff) spos[find_in_row(ptr, col, v, U[s])] = b + s;
+        }
+        if (lane == 0) {
+            pos[v] = b;
+            const bool any = len > 0 && U[0] != 0x7fffffff;
+            cand[v] = any ? U[0] : -1;
+            if (!any) mate[v] = -2;
+        }
+        __syncwarp();
+    }
+}
+
 // Best free neighbour of v from its sorted list starting at k = pos[v]
 // (e = end of v's row); advances pos[v]. Four list entries and their mate
 // words are loaded together, so skipping matched neighbours costs two memory
@@ -980,6 +1053,94 @@ __global__ void __launch_bounds__(LONG_TPB) k_rows_long(const int* __restrict__ 
         }
         if (tid == 0) cnt[q] = base;
         __syncthreads();
+    }
+}
+
+// The same as k_rows_long for rows of up to WROW terms, one warp per listed
+// row in its own slice of shared memory (warp barriers between the bitonic
+// stages); the same keys (coarse column, term position) and run sums, so the
+// results are the same bits. Longer rows go to `longer`.
+template <bool RAP>
+__global__ void __launch_bounds__(TPB) k_rows_warp_sm(const int* __restrict__ list, const int* __restrict__ nlist,
+                                                      const int* __restrict__ heads, const int* __restrict__ mate,
+                                                      const int* __restrict__ ptr, const int* __restrict__ col,
+                                                      const double* __restrict__ val, const int* __restrict__ agg,
+                                                      const double* __restrict__ p, const int* __restrict__ off,
+                                                      int* __restrict__ skey, double* __restrict__ sval,
+                                                      int* __restrict__ cnt, int* __restrict__ longer,
+                                                      int* __restrict__ nlonger, const double* __restrict__ rowscale) {
+    __shared__ unsigned long long KSs[WPB][WROW];
+    __shared__ double VSs[WPB][WROW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long* KS = KSs[w];
+    double* VS = VSs[w];
+    const int nr = *nlist;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nr; t += nwarps) {
+        const int q = list[t];
+        int h = q, m = -1;
+        if (RAP) {
+            h = heads[q];
+            m = mate[h];
+        }
+        const int b0 = ptr[h], l0 = ptr[h + 1] - b0;
+        int b1 = 0, l1 = 0;
+        if (RAP && m > h) {
+            b1 = ptr[m];
+            l1 = ptr[m + 1] - b1;
+        }
+        const int len = l0 + l1;
+        if (len > WROW) {
+            if (lane == 0) longer[atomicAdd(nlonger, 1)] = q;
+            continue;
+        }
+        int m2 = 1;
+        while (m2 < len) m2 <<= 1;
+        for (int s = lane; s < m2; s += 32) {
+            if (s < len) {
+                const bool first = s < l0;
+                const int k = first ? b0 + s : b1 + s - l0;
+                const int j = col[k];
+                KS[s] = ((unsigned long long)(unsigned)agg[j] << 32) | (unsigned)s;
+                VS[s] = RAP ? __dmul_rn(__dmul_rn(p[first ? h : m], val[k]), p[j]) : __dmul_rn(val[k], p[j]);
+            } else {
+                KS[s] = ~0ull;
+            }
+        }
+        __syncwarp();
+        for (int size = 2; size <= m2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int u = lane; u < m2 / 2; u += 32) {
+                    const int lo = 2 * u - (u & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long a = KS[lo], bb = KS[hi];
+                    if ((a > bb) == up) {
+                        KS[lo] = bb;
+                        KS[hi] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        int base = 0;
+        for (int c0 = 0; c0 < len; c0 += 32) {
+            const int r = c0 + lane;
+            const bool head = r < len && (r == 0 || (KS[r] >> 32) != (KS[r - 1] >> 32));
+            const unsigned bal = __ballot_sync(FULL_MASK, head);
+            if (head) {
+                const unsigned key = (unsigned)(KS[r] >> 32);
+                double sum = VS[(unsigned)KS[r]];
+                for (int e = r + 1; e < len && (unsigned)(KS[e] >> 32) == key; ++e)
+                    sum = __dadd_rn(sum, VS[(unsigned)KS[e]]);
+                if (rowscale) sum = __dmul_rn(rowscale[q], sum);
+                const int u = base + __popc(bal & ((1u << lane) - 1u));
+                skey[off[q] + u] = (int)key;
+                sval[off[q] + u] = sum;
+            }
+            base += __popc(bal);
+        }
+        if (lane == 0) cnt[q] = base;
+        __syncwarp();
     }
 }
 
@@ -1850,16 +2011,29 @@ void launch_rows_long(amg_hierarchy* h, Scratch& S, int nrows, const int* list, 
                       const int* mate, const int* ptr, const int* col, const double* val, const int* agg,
                       const double* p, const int* off, int* cnt, const double* rowscale, cudaStream_t st, int G,
                       int max_terms) {
+    // rows of G+1 .. 32 terms: a warp each, 32 lanes (a block per row would
+    // spend a whole block and its barriers on a few dozen terms); then rows up
+    // to WROW terms: a warp each, sorted in shared memory. The passes
+    // alternate between the caller's list (list1 / cnt[8]) and flag / cnt[12].
+    int* lists[2] = {S.list1, S.flag};
+    int* counts[2] = {S.cnt + 8, S.cnt + 12};
+    int cur = 0;
     if (G < 32) {
-        // rows of G+1 .. 32 terms: a warp each (a block per row would spend a
-        // whole block and its barriers on a few dozen terms); longer ones go on
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 12, 0, sizeof(int), st));
-        launch_rows<RAP>(h, 32, nrows, heads, mate, ptr, col, val, agg, p, off, S.skey, S.sval, cnt, S.flag,
-                         S.cnt + 12, rowscale, st, list, nlist);
+        CUDA_CHECK(cudaMemsetAsync(counts[1], 0, sizeof(int), st));
+        launch_rows<RAP>(h, 32, nrows, heads, mate, ptr, col, val, agg, p, off, S.skey, S.sval, cnt, lists[1],
+                         counts[1], rowscale, st, lists[0], counts[0]);
         if (max_terms > 0 && max_terms <= 32) return;
-        list = S.flag;
-        nlist = S.cnt + 12;
+        cur = 1;
     }
+    CUDA_CHECK(cudaMemsetAsync(counts[cur ^ 1], 0, sizeof(int), st));
+    k_rows_warp_sm<RAP><<<h->num_sms * 8, TPB, 0, st>>>(lists[cur], counts[cur], heads, mate, ptr, col, val, agg, p,
+                                                        off, S.skey, S.sval, cnt, lists[cur ^ 1], counts[cur ^ 1],
+                                                        rowscale);
+    KERNEL_CHECK();
+    if (max_terms > 0 && max_terms <= WROW) return;
+    cur ^= 1;
+    list = lists[cur];
+    nlist = counts[cur];
     constexpr int tb = (int)(sizeof(unsigned long long) + sizeof(double));
     CUDA_CHECK(cudaFuncSetAttribute(k_rows_long<RAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROW_CAPS[1] * tb));
     CUDA_CHECK(cudaMemsetAsync(S.cnt + 13, 0, 2 * sizeof(int), st));
@@ -1903,19 +2077,29 @@ void sort_edges(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* spos) {
                                                         S.mate, S.list1, S.cnt + 9, spos);
     KERNEL_CHECK();
     if (A.max_row > 0 && A.max_row <= G) return;       // no row left for the long-row kernels
-    // rows of G+1 .. 32 entries: a warp each (a block per row would spend
-    // a whole block and its barriers on a few dozen entries)
-    const int* lrows = S.list1;
-    const int* nlrows = S.cnt + 9;
+    // rows of G+1 .. 32 entries: a warp each, 32 lanes (a block per row would
+    // spend a whole block and its barriers on a few dozen entries); then rows
+    // up to WROW entries: a warp each, sorted in shared memory. The passes
+    // alternate between two row lists (list1 / cnt[9] and list0 / cnt[12]).
+    int* lists[2] = {S.list1, S.list0};
+    int* counts[2] = {S.cnt + 9, S.cnt + 12};
+    int cur = 0;
     if (G < 32) {
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 12, 0, sizeof(int), st));
-        k_sort_edges_group<32><<<h->num_sms * 16, TPB, 0, st>>>(n, S.list1, S.cnt + 9, A.ptr, A.col, S.c, nbr, pos,
-                                                                 S.cand, S.mate, S.list0, S.cnt + 12, spos);
+        CUDA_CHECK(cudaMemsetAsync(counts[1], 0, sizeof(int), st));
+        k_sort_edges_group<32><<<h->num_sms * 16, TPB, 0, st>>>(n, lists[0], counts[0], A.ptr, A.col, S.c, nbr, pos,
+                                                                 S.cand, S.mate, lists[1], counts[1], spos);
         KERNEL_CHECK();
         if (A.max_row > 0 && A.max_row <= 32) return;
-        lrows = S.list0;
-        nlrows = S.cnt + 12;
+        cur = 1;
     }
+    CUDA_CHECK(cudaMemsetAsync(counts[cur ^ 1], 0, sizeof(int), st));
+    k_sort_edges_warp<<<h->num_sms * 8, TPB, 0, st>>>(lists[cur], counts[cur], A.ptr, A.col, S.c, nbr, pos, S.cand,
+                                                      S.mate, lists[cur ^ 1], counts[cur ^ 1], spos);
+    KERNEL_CHECK();
+    if (A.max_row > 0 && A.max_row <= WROW) return;
+    cur ^= 1;
+    const int* lrows = lists[cur];
+    const int* nlrows = counts[cur];
     // longer rows: a block each in two capacities, then a thread each
     constexpr int eb = (int)(sizeof(long long) + sizeof(int));
     CUDA_CHECK(cudaFuncSetAttribute(k_sort_edges_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
