@@ -27,6 +27,17 @@ enum : int { F_SHAPE = 1, F_NOT_SPD = 2, F_BAD_W = 4 };
 
 __device__ __forceinline__ int find_in_row(const int* __restrict__ ptr, const int* __restrict__ col, int row, int j) {
     int lo = ptr[row], hi = ptr[row + 1];
+    if (hi - lo <= 8) {
+        // a short row: its (at most 8) columns are loaded together, one
+        // memory latency instead of one per bisection step
+        int c[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) c[t] = lo + t < hi ? col[lo + t] : -1;
+        int at = -1;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) at = c[t] == j ? lo + t : at;
+        return at;
+    }
     while (lo < hi) {
         int mid = lo + ((hi - lo) >> 1);
         if (col[mid] < j) lo = mid + 1; else hi = mid;
@@ -1503,6 +1514,53 @@ __global__ void k_cholesky(int n, const double* __restrict__ D, double* __restri
     }
 }
 
+// The factor and its inverse for n <= SM_DENSE, both in shared memory and
+// both right-looking: as soon as column j of L (or row k of Y) is final, every
+// entry it touches takes its update at once. Each entry still sees the same
+// operations in the same order as in k_cholesky / k_lower_inverse (updates in
+// ascending k, the same roundings), so the bits are the same; the dependent
+// chain is O(n) barrier steps instead of O(n^2) serial operations.
+constexpr int SM_DENSE = 96;
+__global__ void k_dense_factor_sm(int n, const double* __restrict__ D, double* __restrict__ L,
+                                  double* __restrict__ Y, int* flag) {
+    extern __shared__ double sm_dense[];
+    double* M = sm_dense;                 // n x n column-major: D, then L in place
+    double* Ys = sm_dense + n * n;        // n x n column-major: partial sums, then L^{-1}
+    __shared__ double dg[SM_DENSE];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) { M[t] = D[t]; Ys[t] = 0.0; }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        double s = M[j * n + j];          // D_jj less l_jk^2 for every k < j
+        if (!(s > 0.0)) { if (threadIdx.x == 0) *flag = 1; s = 1.0; }
+        const double ljj = __dsqrt_rn(s);
+        if (threadIdx.x == 0) dg[j] = ljj;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[j * n + i] = __ddiv_rn(M[j * n + i], ljj);
+        __syncthreads();
+        const int m = n - j - 1;          // trailing lower triangle, columns j+1..n-1
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int c = j + 1 + t / m, i = j + 1 + t % m;
+            if (i >= c) M[c * n + i] = __dsub_rn(M[c * n + i], __dmul_rn(M[j * n + i], M[j * n + c]));
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < n; ++k) {
+        for (int c = threadIdx.x; c <= k; c += blockDim.x)   // row k of every column c <= k is final
+            Ys[c * n + k] = c == k ? 1.0 / dg[k] : -Ys[c * n + k] / dg[k];
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int t = threadIdx.x; t < (k + 1) * m; t += blockDim.x) {
+            const int c = t / m, i = k + 1 + t % m;
+            Ys[c * n + i] = fma(M[k * n + i], Ys[c * n + k], Ys[c * n + i]);
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int c = t / n, i = t % n;
+        L[t] = i > c ? M[t] : (i == c ? dg[c] : 0.0);
+        Y[t] = Ys[t];
+    }
+}
+
 // Y = L^{-1} (column-major, lower), one column per thread.
 __global__ void k_lower_inverse(int n, const double* __restrict__ L, double* __restrict__ Y) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2910,11 +2968,22 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
         k_dense_lower<<<grid_for(h, nc), TPB, 0, st>>>(nc, Lc.A.ptr, Lc.A.col, Lc.A.val, D);
         KERNEL_CHECK();
-        k_cholesky<<<1, 1024, 0, st>>>(nc, D, h->coarse_L, S.cnt + 5);
-        KERNEL_CHECK();
-        if (read_int(S.cnt + 5, S.host, st)) AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
-        k_lower_inverse<<<(nc + 127) / 128, 128, 0, st>>>(nc, h->coarse_L, Y);
-        KERNEL_CHECK();
+        if (nc <= SM_DENSE) {
+            const int smd = (int)(2 * sizeof(double) * (size_t)nc * nc);
+            CUDA_CHECK(cudaFuncSetAttribute(k_dense_factor_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(2 * sizeof(double) * SM_DENSE * SM_DENSE)));
+            k_dense_factor_sm<<<1, 1024, smd, st>>>(nc, D, h->coarse_L, Y, S.cnt + 5);
+            KERNEL_CHECK();
+            if (read_int(S.cnt + 5, S.host, st))
+                AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
+        } else {
+            k_cholesky<<<1, 1024, 0, st>>>(nc, D, h->coarse_L, S.cnt + 5);
+            KERNEL_CHECK();
+            if (read_int(S.cnt + 5, S.host, st))
+                AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
+            k_lower_inverse<<<(nc + 127) / 128, 128, 0, st>>>(nc, h->coarse_L, Y);
+            KERNEL_CHECK();
+        }
         k_gram<<<(int)(((long long)nc * nc + 255) / 256), 256, 0, st>>>(nc, Y, h->coarse_inv);
         KERNEL_CHECK();
     }

@@ -237,3 +237,20 @@ def test_match_kernel_modes_agree(orc, name):
             assert np.array_equal(a, b) and np.array_equal(a, c)
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("mk", [lambda: W.poisson3d(4), lambda: W.random_spd(96, 0.08, 2),
+                                lambda: W.poisson3d(5), lambda: W.varcoef3d(6, seed=1)],
+                         ids=["poisson64", "spd96", "poisson125", "varcoef216"])
+def test_dense_coarsest_solve(orc, mk):
+    # a single level (n <= max_coarse) is the coarsest: the V-cycle is the dense
+    # Cholesky solve; n <= 96 and n > 96 take the two factor kernels
+    A = mk()
+    H = orc.Hierarchy(A, max_coarse=1000)
+    h = setup(A, max_coarse=1000)
+    r = np.random.default_rng(5).normal(size=A.n)
+    zo = H.vcycle(r)
+    zg = vcycle(h, r)
+    assert np.linalg.norm(zg - zo) <= 1e-13 * np.linalg.norm(zo)
+    assert np.linalg.norm(A.scipy() @ zg - r) <= 1e-11 * np.linalg.norm(r)
+    h.close()
