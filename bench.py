@@ -497,14 +497,17 @@ def many_arm(args):
     prec = amg.AMG_FP32_VCYCLE if args.precision == "fp32" else amg.AMG_FP64
     m = len(mats)
 
-    def step():
+    def step(profile=0, marks=None):
         d_x.zero_()
         h = amg.amg_setup_many(systems, precision=prec, krylov=args.krylov, autotune=args.autotune,
-                               stream=stream.cuda_stream)
+                               profile=profile, stream=stream.cuda_stream)
+        if marks is not None:
+            marks[1].record(stream)
         infos = amg.amg_solve_many(h, d_b, d_x, m, rtol=args.rtol, maxit=1000)
         hi = amg.amg_hierarchy_info(h)
+        ks = amg.amg_kernel_stats(h) if profile else None
         h.close()
-        return infos, hi
+        return infos, hi, ks
 
     for _ in range(args.warmup):
         step()
@@ -521,7 +524,16 @@ def many_arm(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (amg.amg_launch_count() - launches0) // args.steps
     clocks = clk.summary()
-    infos, hi = runs[-1]
+    infos, hi, _ = runs[-1]
+    # one profiled step after the timed region: setup / solve split and the scope table
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    marks[0].record(stream)
+    _, _, ks = step(profile=1, marks=marks)
+    marks[2].record(stream)
+    torch.cuda.synchronize()
+    prof_setup_ms, prof_solve_ms = marks[0].elapsed_time(marks[1]), marks[1].elapsed_time(marks[2])
+    kernels = {name: {"launches": sc, "ms": round(kms, 4)}
+               for name, (sc, kms, by) in sorted(ks.items(), key=lambda kv: -kv[1][1])}
     xs = d_x.cpu().numpy()
     worst = 0.0
     for s, M in enumerate(mats):
@@ -597,6 +609,9 @@ def many_arm(args):
             "worst_numpy_relres": worst, "levels": hi["n"],
             "one_at_a_time_fp64_ms": round(solo_ms, 2), "speedup_vs_one_at_a_time": round(solo_ms / ms, 2),
             "gpu_launches": int(launches), "clocks": clocks,
+            "profiled_setup_ms": round(prof_setup_ms, 3), "profiled_solve_ms": round(prof_solve_ms, 3),
+            "kernels": kernels,
+            "kernel_stats": "CUDA events around every scope in one profiled step after the timed region",
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * ntot},
             "cpu_baseline": cpu,
         }

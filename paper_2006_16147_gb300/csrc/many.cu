@@ -56,29 +56,51 @@ __global__ void __launch_bounds__(TPB) m_spmv(SellM S, const double* __restrict_
 
 enum SegMode : int { SEG_NORMS = 0, SEG_PQ = 1, SEG_RR = 2, SEG_RZ = 3, SEG_CHECK = 4 };
 
-// One block per system: sums over the system's rows in a fixed order, then
-// the system's scalar update.
-__global__ void __launch_bounds__(TPB) m_seg_reduce(int m, const int* __restrict__ seg, const double* __restrict__ u,
+// Per-system sums in two passes. The rows are cut into chunks of at most
+// CHUNK rows that never cross a system boundary; pass 1 sums every chunk
+// (all SMs, one CTA per chunk, a fixed tree order), pass 2 adds each system's
+// chunk sums in ascending chunk order and applies the system's scalar update.
+// The order depends only on the system sizes, so results are reproducible.
+constexpr int CHUNK = 4096;
+
+__global__ void __launch_bounds__(TPB) m_chunk_sums(const int* __restrict__ ch_row, const double* __restrict__ u,
                                                     const double* __restrict__ v, const double* __restrict__ w,
-                                                    BlockScalars sc, int mode, int flexible) {
-    const int s = blockIdx.x;
-    if (s >= m) return;
+                                                    int mode, double* __restrict__ part_a, double* __restrict__ part_b) {
+    const int c = blockIdx.x;
+    const int r0 = ch_row[c], r1 = ch_row[c + 1];
     double a = 0.0, b = 0.0;
-    for (int i = seg[s] + threadIdx.x; i < seg[s + 1]; i += blockDim.x) {
-        const double ui = u[i];
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double ui = __ldg(u + i);
         if (mode == SEG_NORMS || mode == SEG_CHECK) {
+            const double vi = __ldg(v + i);
             a = fma(ui, ui, a);
-            b = fma(v[i], v[i], b);
+            b = fma(vi, vi, b);
         } else if (mode == SEG_RR) {
             a = fma(ui, ui, a);
         } else {
-            a = fma(ui, v[i], a);
-            if (w) b = fma(w[i], v[i], b);
+            const double vi = __ldg(v + i);
+            a = fma(ui, vi, a);
+            if (w) b = fma(__ldg(w + i), vi, b);
         }
     }
     a = block_sum(a);
     b = block_sum(b);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        part_a[c] = a;
+        part_b[c] = b;
+    }
+}
+
+// One thread per system: the system's sums, then its scalar update.
+__global__ void m_seg_update(int m, const int* __restrict__ sys_ch, const double* __restrict__ part_a,
+                             const double* __restrict__ part_b, BlockScalars sc, int mode, int flexible) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m) return;
+    double a = 0.0, b = 0.0;
+    for (int c = sys_ch[s]; c < sys_ch[s + 1]; ++c) {
+        a += part_a[c];
+        b += part_b[c];
+    }
     const int md = sc.mode[s];
     switch (mode) {
         case SEG_NORMS:   // u = r = b - A x0, v = b
@@ -129,6 +151,23 @@ __global__ void __launch_bounds__(TPB) m_seg_reduce(int m, const int* __restrict
         default: break;
     }
 }
+
+// The chunk table of a batch and the two passes over it.
+struct SegSums {
+    int m = 0, nch = 0;
+    int* ch_row = nullptr;      // nch + 1 row offsets
+    int* sys_ch = nullptr;      // m + 1 chunk offsets
+    double *part_a = nullptr, *part_b = nullptr;
+    void run(cudaStream_t st, const double* u, const double* v, const double* w, BlockScalars sc, int mode,
+             int flexible) const {
+        if (nch > 0) {
+            m_chunk_sums<<<nch, TPB, 0, st>>>(ch_row, u, v, w, mode, part_a, part_b);
+            KERNEL_CHECK();
+        }
+        m_seg_update<<<(m + 127) / 128, 128, 0, st>>>(m, sys_ch, part_a, part_b, sc, mode, flexible);
+        KERNEL_CHECK();
+    }
+};
 
 // x += alpha_s p, r -= alpha_s q for rows of ACTIVE systems.
 __global__ void __launch_bounds__(TPB) m_update_xr(int n, const int* __restrict__ seg_row,
@@ -220,7 +259,6 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
     M.sc.rr = M.mem.alloc<double>(m);
     M.sc.bb = M.mem.alloc<double>(m);
     M.sc.rtol = M.mem.alloc<double>(m);
-    int* seg0 = M.mem.alloc<int>(m + 1);
     CUDA_CHECK(cudaHostAlloc(&M.mode_host, sizeof(int) * m, cudaHostAllocDefault));
     CUDA_CHECK(cudaHostAlloc(&M.iters_host, sizeof(int) * m, cudaHostAllocDefault));
     CUDA_CHECK(cudaHostAlloc(&M.rr_host, sizeof(double) * m, cudaHostAllocDefault));
@@ -230,8 +268,25 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
         std::vector<double> rt(m, rtol);
         CUDA_CHECK(cudaMemcpyAsync(M.sc.mode, md.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
         CUDA_CHECK(cudaMemcpyAsync(M.sc.rtol, rt.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-        CUDA_CHECK(cudaMemcpyAsync(seg0, h->seg0.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
         CUDA_CHECK(cudaMemsetAsync(M.sc.iters, 0, sizeof(int) * m, st));
+        CUDA_CHECK(cudaStreamSynchronize(st));
+    }
+    SegSums R;
+    {
+        std::vector<int> ch_row{0}, sys_ch{0};
+        for (int s2 = 0; s2 < m; ++s2) {
+            for (int r0 = h->seg0[s2]; r0 < h->seg0[s2 + 1]; r0 += CHUNK)
+                ch_row.push_back(std::min(r0 + CHUNK, h->seg0[s2 + 1]));
+            sys_ch.push_back((int)ch_row.size() - 1);
+        }
+        R.m = m;
+        R.nch = (int)ch_row.size() - 1;
+        R.ch_row = M.mem.alloc<int>(R.nch + 1);
+        R.sys_ch = M.mem.alloc<int>(m + 1);
+        R.part_a = M.mem.alloc<double>(std::max(R.nch, 1));
+        R.part_b = M.mem.alloc<double>(std::max(R.nch, 1));
+        CUDA_CHECK(cudaMemcpyAsync(R.ch_row, ch_row.data(), sizeof(int) * (R.nch + 1), cudaMemcpyHostToDevice, st));
+        CUDA_CHECK(cudaMemcpyAsync(R.sys_ch, sys_ch.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
         CUDA_CHECK(cudaStreamSynchronize(st));
     }
     const int flexible = h->opt.krylov == 1;
@@ -242,8 +297,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
     // r = b - A x0, per-system norms
     m_spmv<<<sgrid, TPB, 0, st>>>(S, L0.S.val, x, b, r);
     KERNEL_CHECK();
-    m_seg_reduce<<<m, TPB, 0, st>>>(m, seg0, r, b, nullptr, M.sc, SEG_NORMS, flexible);
-    KERNEL_CHECK();
+    R.run(st, r, b, nullptr, M.sc, SEG_NORMS, flexible);
     m_zero_done<<<vgrid, TPB, 0, st>>>(n, h->seg_row0, x, M.sc);
     KERNEL_CHECK();
 
@@ -266,15 +320,12 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
         try {
             m_spmv<<<sgrid, TPB, 0, cs>>>(S, L0.S.val, p, nullptr, q);
             KERNEL_CHECK();
-            m_seg_reduce<<<m, TPB, 0, cs>>>(m, seg0, p, q, nullptr, M.sc, SEG_PQ, flexible);
-            KERNEL_CHECK();
+            R.run(cs, p, q, nullptr, M.sc, SEG_PQ, flexible);
             m_update_xr<<<vgrid, TPB, 0, cs>>>(n, h->seg_row0, p, q, x, r, M.sc);
             KERNEL_CHECK();
-            m_seg_reduce<<<m, TPB, 0, cs>>>(m, seg0, r, nullptr, nullptr, M.sc, SEG_RR, flexible);
-            KERNEL_CHECK();
+            R.run(cs, r, nullptr, nullptr, M.sc, SEG_RR, flexible);
             vcycle_plain(h, r, z);
-            m_seg_reduce<<<m, TPB, 0, cs>>>(m, seg0, r, z, flexible ? q : nullptr, M.sc, SEG_RZ, flexible);
-            KERNEL_CHECK();
+            R.run(cs, r, z, flexible ? q : nullptr, M.sc, SEG_RZ, flexible);
             m_update_p<<<vgrid, TPB, 0, cs>>>(n, h->seg_row0, z, p, M.sc);
             KERNEL_CHECK();
             M.step_kernels = launch_counter().load() - before;
@@ -312,8 +363,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
         if (check) {
             m_spmv<<<sgrid, TPB, 0, st>>>(S, L0.S.val, x, b, t);
             KERNEL_CHECK();
-            m_seg_reduce<<<m, TPB, 0, st>>>(m, seg0, t, b, nullptr, M.sc, SEG_CHECK, flexible);
-            KERNEL_CHECK();
+            R.run(st, t, b, nullptr, M.sc, SEG_CHECK, flexible);
             m_copy_restart<<<vgrid, TPB, 0, st>>>(n, h->seg_row0, t, r, M.sc);
             KERNEL_CHECK();
             copy_state(h, M, m);
@@ -326,8 +376,7 @@ amg_status solve_many(amg_hierarchy* h, const double* b, double* x, double rtol,
         std::vector<int> md(m, COL_CHECK);
         std::vector<int> keep(M.mode_host, M.mode_host + m);
         CUDA_CHECK(cudaMemcpyAsync(M.sc.mode, md.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
-        m_seg_reduce<<<m, TPB, 0, st>>>(m, seg0, t, b, nullptr, M.sc, SEG_CHECK, flexible);
-        KERNEL_CHECK();
+        R.run(st, t, b, nullptr, M.sc, SEG_CHECK, flexible);
         copy_state(h, M, m);
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         amg_status status = AMG_OK;

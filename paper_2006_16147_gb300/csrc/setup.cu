@@ -1514,26 +1514,47 @@ __global__ void k_cholesky(int n, const double* __restrict__ D, double* __restri
     }
 }
 
-// The factor and its inverse for n <= SM_DENSE, both in shared memory and
-// both right-looking: as soon as column j of L (or row k of Y) is final, every
-// entry it touches takes its update at once. Each entry still sees the same
-// operations in the same order as in k_cholesky / k_lower_inverse (updates in
-// ascending k, the same roundings), so the bits are the same; the dependent
-// chain is O(n) barrier steps instead of O(n^2) serial operations.
+// The whole coarsest-level inverse of one diagonal block per CTA: the dense
+// lower triangle from the block's CSR rows, the factor L, Y = L^{-1} and
+// A^{-1} = Y^T Y (row-major, at Ainv + blk[s]); L is also written when Lout
+// is set. Factor and inverse are right-looking: as soon as column j of L (or
+// row k of Y) is final, every entry it touches takes its update at once. Each
+// entry still sees the same operations in the same order as in k_cholesky /
+// k_lower_inverse / k_gram (updates in ascending k, the same roundings), so
+// the bits are the same; the dependent chain is O(n) barrier steps instead of
+// O(n^2) serial operations. A block of n <= SM_DENSE rows works in shared
+// memory, a larger one in gwork + gofs[s] (2 n^2 doubles). segp == nullptr
+// means a single block of rows [0, n0).
 constexpr int SM_DENSE = 96;
-__global__ void k_dense_factor_sm(int n, const double* __restrict__ D, double* __restrict__ L,
-                                  double* __restrict__ Y, int* flag) {
+__global__ void k_coarse_inverse_blocks(int n0, const int* __restrict__ segp, const long long* __restrict__ blk,
+                                        const long long* __restrict__ gofs, const int* __restrict__ ptr,
+                                        const int* __restrict__ col, const double* __restrict__ val,
+                                        double* __restrict__ gwork, double* __restrict__ Ainv,
+                                        double* __restrict__ Lout, int* flag) {
+    const int sg = blockIdx.x;
+    const int r0 = segp ? segp[sg] : 0;
+    const int n = segp ? segp[sg + 1] - r0 : n0;
+    if (n <= 0) return;
     extern __shared__ double sm_dense[];
-    double* M = sm_dense;                 // n x n column-major: D, then L in place
-    double* Ys = sm_dense + n * n;        // n x n column-major: partial sums, then L^{-1}
     __shared__ double dg[SM_DENSE];
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) { M[t] = D[t]; Ys[t] = 0.0; }
+    double* M;                            // n x n column-major: D, then L in place
+    double* Ys;                           // n x n column-major: partial sums, then L^{-1}
+    double* diag;                         // L_jj
+    if (n <= SM_DENSE) { M = sm_dense; Ys = sm_dense + n * n; diag = dg; }
+    else { M = gwork + gofs[sg]; Ys = M + (size_t)n * n; diag = Ys + (size_t)n * n; }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) { M[t] = 0.0; Ys[t] = 0.0; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int k = ptr[r0 + i]; k < ptr[r0 + i + 1]; ++k) {
+            const int j = col[k] - r0;
+            if (j >= 0 && j <= i) M[j * n + i] = val[k];
+        }
     __syncthreads();
     for (int j = 0; j < n; ++j) {
         double s = M[j * n + j];          // D_jj less l_jk^2 for every k < j
         if (!(s > 0.0)) { if (threadIdx.x == 0) *flag = 1; s = 1.0; }
         const double ljj = __dsqrt_rn(s);
-        if (threadIdx.x == 0) dg[j] = ljj;
+        if (threadIdx.x == 0) diag[j] = ljj;
         for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) M[j * n + i] = __ddiv_rn(M[j * n + i], ljj);
         __syncthreads();
         const int m = n - j - 1;          // trailing lower triangle, columns j+1..n-1
@@ -1545,7 +1566,7 @@ __global__ void k_dense_factor_sm(int n, const double* __restrict__ D, double* _
     }
     for (int k = 0; k < n; ++k) {
         for (int c = threadIdx.x; c <= k; c += blockDim.x)   // row k of every column c <= k is final
-            Ys[c * n + k] = c == k ? 1.0 / dg[k] : -Ys[c * n + k] / dg[k];
+            Ys[c * n + k] = c == k ? 1.0 / diag[k] : -Ys[c * n + k] / diag[k];
         __syncthreads();
         const int m = n - k - 1;
         for (int t = threadIdx.x; t < (k + 1) * m; t += blockDim.x) {
@@ -1554,10 +1575,13 @@ __global__ void k_dense_factor_sm(int n, const double* __restrict__ D, double* _
         }
         __syncthreads();
     }
+    double* Ai = Ainv + (segp ? blk[sg] : 0);
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-        const int c = t / n, i = t % n;
-        L[t] = i > c ? M[t] : (i == c ? dg[c] : 0.0);
-        Y[t] = Ys[t];
+        const int i = t / n, j = t % n;
+        double s = 0.0;
+        for (int k = max(i, j); k < n; ++k) s = fma(Ys[i * n + k], Ys[j * n + k], s);
+        Ai[t] = s;
+        if (Lout) Lout[t] = j > i ? M[t] : (j == i ? diag[i] : 0.0);   // t = column i, row j
     }
 }
 
@@ -2933,25 +2957,48 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         h->segL_blk = h->mem.alloc<long long>(nseg + 1);
         CUDA_CHECK(cudaMemcpyAsync(h->segL_ptr, sp.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, st));
         CUDA_CHECK(cudaMemcpyAsync(h->segL_blk, boff.data(), sizeof(long long) * (nseg + 1), cudaMemcpyHostToDevice, st));
-        int maxb = 0;
-        for (int s2 = 0; s2 < nseg; ++s2) maxb = std::max(maxb, sp[s2 + 1] - sp[s2]);
-        double* D = S.mem.alloc<double>((size_t)maxb * maxb + 1);
-        double* Lf = S.mem.alloc<double>((size_t)maxb * maxb + 1);
-        double* Y = S.mem.alloc<double>((size_t)maxb * maxb + 1);
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
+        // one CTA per block in a single launch; blocks above SM_DENSE rows work in
+        // global scratch, and when that scratch would pass 1 GiB the blocks are
+        // factored one after another instead
+        int maxb = 0, maxsm = 0;
+        std::vector<long long> gofs(nseg, 0);
+        long long gw = 0;
         for (int s2 = 0; s2 < nseg; ++s2) {
             const int ns = sp[s2 + 1] - sp[s2];
-            if (ns == 0) continue;
-            CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * ns * ns, st));
-            CUDA_CHECK(cudaMemsetAsync(Lf, 0, sizeof(double) * ns * ns, st));
-            k_dense_lower_block<<<grid_for(h, ns), TPB, 0, st>>>(ns, sp[s2], Lc.A.ptr, Lc.A.col, Lc.A.val, D);
+            maxb = std::max(maxb, ns);
+            if (ns <= SM_DENSE) maxsm = std::max(maxsm, ns);
+            else { gofs[s2] = gw; gw += 2LL * ns * ns + ns; }
+        }
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
+        if (gw <= (1LL << 27)) {
+            double* gwork = S.mem.alloc<double>(gw + 1);
+            long long* d_gofs = S.mem.alloc<long long>(nseg);
+            CUDA_CHECK(cudaMemcpyAsync(d_gofs, gofs.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice, st));
+            const int smd = (int)(2 * sizeof(double) * (size_t)maxsm * maxsm);
+            CUDA_CHECK(cudaFuncSetAttribute(k_coarse_inverse_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(2 * sizeof(double) * SM_DENSE * SM_DENSE)));
+            k_coarse_inverse_blocks<<<nseg, 1024, smd, st>>>(0, h->segL_ptr, h->segL_blk, d_gofs, Lc.A.ptr,
+                                                             Lc.A.col, Lc.A.val, gwork, h->coarse_inv, nullptr,
+                                                             S.cnt + 5);
             KERNEL_CHECK();
-            k_cholesky<<<1, 1024, 0, st>>>(ns, D, Lf, S.cnt + 5);
-            KERNEL_CHECK();
-            k_lower_inverse<<<(ns + 127) / 128, 128, 0, st>>>(ns, Lf, Y);
-            KERNEL_CHECK();
-            k_gram<<<(int)(((long long)ns * ns + 255) / 256), 256, 0, st>>>(ns, Y, h->coarse_inv + boff[s2]);
-            KERNEL_CHECK();
+        } else {
+            double* D = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+            double* Lf = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+            double* Y = S.mem.alloc<double>((size_t)maxb * maxb + 1);
+            for (int s2 = 0; s2 < nseg; ++s2) {
+                const int ns = sp[s2 + 1] - sp[s2];
+                if (ns == 0) continue;
+                CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * ns * ns, st));
+                CUDA_CHECK(cudaMemsetAsync(Lf, 0, sizeof(double) * ns * ns, st));
+                k_dense_lower_block<<<grid_for(h, ns), TPB, 0, st>>>(ns, sp[s2], Lc.A.ptr, Lc.A.col, Lc.A.val, D);
+                KERNEL_CHECK();
+                k_cholesky<<<1, 1024, 0, st>>>(ns, D, Lf, S.cnt + 5);
+                KERNEL_CHECK();
+                k_lower_inverse<<<(ns + 127) / 128, 128, 0, st>>>(ns, Lf, Y);
+                KERNEL_CHECK();
+                k_gram<<<(int)(((long long)ns * ns + 255) / 256), 256, 0, st>>>(ns, Y, h->coarse_inv + boff[s2]);
+                KERNEL_CHECK();
+            }
         }
         if (read_int(S.cnt + 5, S.host, st)) AMG_THROW(AMG_ERR_NOT_SPD, "a coarsest block hit a non-positive pivot");
     }
@@ -2959,33 +3006,34 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         Level& Lc = h->lev.back();
         const int nc = Lc.A.n;
         Scope sc_(&h->prof, st, S_COARSE, 0.0);
-        double* D = S.mem.alloc<double>((size_t)nc * nc);
-        double* Y = S.mem.alloc<double>((size_t)nc * nc);
         h->coarse_L = h->mem.alloc<double>((size_t)nc * nc);
         h->coarse_inv = h->mem.alloc<double>((size_t)nc * nc);
-        CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * nc * nc, st));
-        CUDA_CHECK(cudaMemsetAsync(h->coarse_L, 0, sizeof(double) * nc * nc, st));
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
-        k_dense_lower<<<grid_for(h, nc), TPB, 0, st>>>(nc, Lc.A.ptr, Lc.A.col, Lc.A.val, D);
-        KERNEL_CHECK();
         if (nc <= SM_DENSE) {
             const int smd = (int)(2 * sizeof(double) * (size_t)nc * nc);
-            CUDA_CHECK(cudaFuncSetAttribute(k_dense_factor_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            CUDA_CHECK(cudaFuncSetAttribute(k_coarse_inverse_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)(2 * sizeof(double) * SM_DENSE * SM_DENSE)));
-            k_dense_factor_sm<<<1, 1024, smd, st>>>(nc, D, h->coarse_L, Y, S.cnt + 5);
+            k_coarse_inverse_blocks<<<1, 1024, smd, st>>>(nc, nullptr, nullptr, nullptr, Lc.A.ptr, Lc.A.col,
+                                                          Lc.A.val, nullptr, h->coarse_inv, h->coarse_L, S.cnt + 5);
             KERNEL_CHECK();
             if (read_int(S.cnt + 5, S.host, st))
                 AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
         } else {
+            double* D = S.mem.alloc<double>((size_t)nc * nc);
+            double* Y = S.mem.alloc<double>((size_t)nc * nc);
+            CUDA_CHECK(cudaMemsetAsync(D, 0, sizeof(double) * nc * nc, st));
+            CUDA_CHECK(cudaMemsetAsync(h->coarse_L, 0, sizeof(double) * nc * nc, st));
+            k_dense_lower<<<grid_for(h, nc), TPB, 0, st>>>(nc, Lc.A.ptr, Lc.A.col, Lc.A.val, D);
+            KERNEL_CHECK();
             k_cholesky<<<1, 1024, 0, st>>>(nc, D, h->coarse_L, S.cnt + 5);
             KERNEL_CHECK();
             if (read_int(S.cnt + 5, S.host, st))
                 AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
             k_lower_inverse<<<(nc + 127) / 128, 128, 0, st>>>(nc, h->coarse_L, Y);
             KERNEL_CHECK();
+            k_gram<<<(int)(((long long)nc * nc + 255) / 256), 256, 0, st>>>(nc, Y, h->coarse_inv);
+            KERNEL_CHECK();
         }
-        k_gram<<<(int)(((long long)nc * nc + 255) / 256), 256, 0, st>>>(nc, Y, h->coarse_inv);
-        KERNEL_CHECK();
     }
     CUDA_CHECK(cudaStreamSynchronize(st));
     h->prof.flush();

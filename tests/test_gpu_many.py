@@ -178,3 +178,25 @@ def test_solve_many_fp32_vcycle():
         its[prec] = [i["iterations"] for i in infos]
         h.close()
     assert all(abs(a - c) <= 3 for a, c in zip(its[amg.AMG_FP64], its[amg.AMG_FP32_VCYCLE])), its
+
+
+def test_many_dense_coarsest_blocks(orc):
+    # every system is its own coarsest block (max_coarse above every size):
+    # blocks of at most 96 rows are factored in shared memory, larger ones in
+    # global scratch, all in one launch; the V-cycle is the block-diagonal
+    # dense solve and matches the oracle's per-block Cholesky
+    from paper_2006_16147_gb300 import amg
+    import torch
+    mats = [W.poisson3d(4), W.random_spd(150, 0.04, 3), W.poisson3d(5), W.poisson3d(2, 1, 1), W.varcoef3d(4, seed=2)]
+    U, offs = W.block_diagonal(mats)
+    H = orc.Hierarchy(U, seg=offs, max_coarse=1000)
+    h = _setup_many(mats, [np.ones(M.n) for M in mats], max_coarse=1000)
+    assert amg.amg_hierarchy_info(h)["n"] == [U.n]
+    r = np.random.default_rng(5).normal(size=U.n)
+    z = torch.empty(U.n, dtype=torch.float64, device="cuda:0")
+    amg.amg_vcycle(h, dev(r), z)
+    torch.cuda.synchronize()
+    zg, zo = z.cpu().numpy(), H.vcycle(r)
+    assert np.linalg.norm(zg - zo) <= 1e-13 * np.linalg.norm(zo)
+    assert np.linalg.norm(U.scipy() @ zg - r) <= 1e-11 * np.linalg.norm(r)
+    h.close()
