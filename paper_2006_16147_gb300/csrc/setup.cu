@@ -1156,18 +1156,24 @@ __global__ void __launch_bounds__(TPB) k_rows_warp_sm(const int* __restrict__ li
 }
 
 // Compacts the per-row results from scratch (row q at off[q]) into the CSR
-// arrays; a group of G lanes per row, lanes over the row's entries.
+// arrays; a group of G lanes per row, lanes over the row's entries. With dww
+// set (zeroed by the caller), also dww[q] = (c_qq w_q) w_q, the value k_diag
+// would compute for the new matrix and smooth vector w.
 template <int G>
 __global__ void __launch_bounds__(TPB) k_rap_copy(int nc, const int* __restrict__ off, const int* __restrict__ cptr,
                                                  const int* __restrict__ skey, const double* __restrict__ sval,
-                                                 int* __restrict__ ccol, double* __restrict__ cval) {
+                                                 int* __restrict__ ccol, double* __restrict__ cval,
+                                                 const double* __restrict__ w, double* __restrict__ dww) {
     const int gl = threadIdx.x & (G - 1);
     const int ng = (gridDim.x * blockDim.x) / G;
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) / G; q < nc; q += ng) {
         const int s = off[q], d = cptr[q], e = cptr[q + 1];
         for (int k = gl; k < e - d; k += G) {
-            ccol[d + k] = skey[s + k];
-            cval[d + k] = sval[s + k];
+            const int c = skey[s + k];
+            const double v = sval[s + k];
+            ccol[d + k] = c;
+            cval[d + k] = v;
+            if (dww && c == q) dww[q] = __dmul_rn(__dmul_rn(v, w[q]), w[q]);
         }
     }
 }
@@ -1309,12 +1315,14 @@ void launch_rows(amg_hierarchy* h, int G, int nrows, const int* heads, const int
 }
 
 void launch_copy(amg_hierarchy* h, long long nnz, int nrows, const int* off, const int* cptr, const int* skey,
-                 const double* sval, int* ccol, double* cval, cudaStream_t st) {
+                 const double* sval, int* ccol, double* cval, cudaStream_t st, const double* w = nullptr,
+                 double* dww = nullptr) {
     const int G = rows_group(nnz, nrows);
     const int blocks = blocks_for((long long)nrows * G, TPB, h->num_sms * 16);
-    if (G == 8) k_rap_copy<8><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
-    else if (G == 16) k_rap_copy<16><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
-    else k_rap_copy<32><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval);
+    if (dww) CUDA_CHECK(cudaMemsetAsync(dww, 0, sizeof(double) * nrows, st));
+    if (G == 8) k_rap_copy<8><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval, w, dww);
+    else if (G == 16) k_rap_copy<16><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval, w, dww);
+    else k_rap_copy<32><<<blocks, TPB, 0, st>>>(nrows, off, cptr, skey, sval, ccol, cval, w, dww);
     KERNEL_CHECK();
 }
 
@@ -1376,23 +1384,37 @@ __global__ void k_to_float(long long n, const double* __restrict__ a, float* __r
 
 // ------------------------------------------------------------ SELL-32 ------
 // width[s] = longest row of slice s.
-__global__ void k_sell_width(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ perm,
-                             int* __restrict__ width) {
+// Row i of the source starts at ptr[i]; it has len[i] entries when len is
+// set (rows written in place by a row product), else ptr[i + 1] - ptr[i].
+__device__ __forceinline__ int src_len(const int* __restrict__ ptr, const int* __restrict__ len, int i) {
+    return len ? len[i] : ptr[i + 1] - ptr[i];
+}
+
+// Slice widths; with nnz_out set, also the entry count (one atomic per block).
+__global__ void k_sell_width(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ len,
+                             const int* __restrict__ perm, int* __restrict__ width, int* __restrict__ nnz_out) {
     const int lane = threadIdx.x & 31;
+    int sum = 0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
          t += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(t >> 5);
         const int ip = (int)t;
         const int i = ip < n ? (perm ? perm[ip] : ip) : 0;
-        const int len = ip < n ? ptr[i + 1] - ptr[i] : 0;
-        const int m = warp_max_int(len);
+        const int l = ip < n ? src_len(ptr, len, i) : 0;
+        sum += l;
+        const int m = warp_max_int(l);
         if (lane == 0) width[s] = m;
+    }
+    if (nnz_out) {
+        sum = block_sum_int(sum);
+        if (threadIdx.x == 0 && sum) atomicAdd(nnz_out, sum);
     }
 }
 
-__global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ col,
-                            const double* __restrict__ val, const int* __restrict__ sptr,
-                            const int* __restrict__ perm, int* __restrict__ scol, double* __restrict__ sval) {
+__global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, const int* __restrict__ rlen,
+                            const int* __restrict__ col, const double* __restrict__ val,
+                            const int* __restrict__ sptr, const int* __restrict__ perm, int* __restrict__ scol,
+                            double* __restrict__ sval) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nslices * 32;
          t += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(t >> 5), lane = (int)(t & 31);
@@ -1403,7 +1425,7 @@ __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, con
         if (ip < n) {
             const int i = perm ? perm[ip] : ip;
             b = ptr[i];
-            len = ptr[i + 1] - b;
+            len = src_len(ptr, rlen, i);
         }
         // padding repeats the row's last column (a valid index of this
         // matrix's column space, also for rectangular A P) with value 0
@@ -1420,13 +1442,13 @@ __global__ void k_sell_fill(int n, int nslices, const int* __restrict__ ptr, con
 // length. One block of SIGMA threads per window, bitonic sort in shared memory.
 constexpr int SIGMA = 256;
 __global__ void __launch_bounds__(SIGMA) k_sort_window(int n, const int* __restrict__ rows, const int* __restrict__ ptr,
-                                                      int* __restrict__ perm) {
+                                                      const int* __restrict__ len, int* __restrict__ perm) {
     __shared__ long long key[SIGMA];
     const int t = threadIdx.x;
     const int it = blockIdx.x * SIGMA + t;
     const int i = it < n ? (rows ? rows[it] : it) : 0;
     // key: larger length first, then smaller row index; items past n sort last
-    key[t] = it < n ? ((long long)(0x7fffffff - (ptr[i + 1] - ptr[i])) << 32) | (unsigned)i : 0x7fffffffffffffffLL;
+    key[t] = it < n ? ((long long)(0x7fffffff - src_len(ptr, len, i)) << 32) | (unsigned)i : 0x7fffffffffffffffLL;
     __syncthreads();
     for (int k = 2; k <= SIGMA; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -2197,8 +2219,17 @@ void sort_edges(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* spos) {
     KERNEL_CHECK();
 }
 
+// The error word of the proposal matching (read by the caller together with
+// the aggregate count, one synchronisation).
+void check_suitor_error(int e) {
+    if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
+    if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
+    if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
+}
+
 // Proposals over the sorted rows in S.nq (suitor words reset), then mate.
-int suitor_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* err) {
+// Errors are left in *err for the caller.
+void suitor_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* err) {
     cudaStream_t st = h->stream;
     const int n = A.n;
     Scope sc_(&h->prof, st, S_MATCH, 0.0);
@@ -2208,19 +2239,17 @@ int suitor_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int* err) {
     }
     k_suitor_mate<<<grid_for(h, n), TPB, 0, st>>>(n, S.nq, S.suitor, S.mate, err);
     KERNEL_CHECK();
-    const int e = read_int(err, S.host, st);
-    if (e & 1) AMG_THROW(AMG_ERR_ARG, "matching: an edge has no mirror entry (pattern not symmetric)");
-    if (e & 8) AMG_THROW(AMG_ERR_ARG, "matching: a row without a diagonal entry");
-    if (e & 6) AMG_THROW(AMG_ERR_CUDA, "matching by proposals did not settle (internal error %d)", e);
-    return 0;
 }
 
 // The matching of one sweep into S.mate (partner, or < 0 unmatched).
 // Returns the number of locally-dominant rounds (0 for the proposal method,
 // which has none). match_kernel 0: proposals (k_suitor); 1: one launch pair
 // per round with a host check every 16 rounds; 2: all rounds in one
-// cooperative launch when the device allows it (else as 1).
-int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
+// cooperative launch when the device allows it (else as 1). For 0, *pending
+// is set to the device error word, which the caller must read and pass to
+// check_suitor_error before it uses the matching beyond a scan of it.
+int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int** pending) {
+    *pending = nullptr;
     cudaStream_t st = h->stream;
     const int n = A.n;
     CUDA_CHECK(cudaMemsetAsync(S.mate, 0xff, sizeof(int) * n, st));   // all -1
@@ -2243,7 +2272,9 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A) {
                 k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             KERNEL_CHECK();
         }
-        return suitor_match(h, S, A, err);
+        suitor_match(h, S, A, err);
+        *pending = err;
+        return 0;
     }
     if (h->opt.match_kernel == 2 && h->coop_blocks > 0) {
         int* nbr = S.skey;            // sorted neighbour lists (free until the Galerkin step)
@@ -2328,34 +2359,47 @@ DevCsr galerkin_pairwise(amg_hierarchy* h, Scratch& S, const DevCsr& A, const Sw
     finish_csr(h, S, C);
     C.col = owner.alloc<int>(C.nnz);
     C.val = owner.alloc<double>(C.nnz);
-    launch_copy(h, C.nnz, nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val, st);
+    // the weight denominators of the next sweep come with the copy
+    launch_copy(h, C.nnz, nc, S.off, C.ptr, S.skey, S.sval, C.col, C.val, st, sw.wc, S.diag);
     return C;
 }
 
-void build_sell(amg_hierarchy* h, const DevCsr& A, DevSell& E, Scratch& S, bool fp32) {
+// SELL of A. With len set, row i of the source starts at A.ptr[i] and has
+// len[i] entries (A.nnz is then counted here); wtmp is the slice-width
+// scratch (S.ub when null).
+void build_sell(amg_hierarchy* h, DevCsr A, DevSell& E, Scratch& S, bool fp32, const int* len = nullptr,
+                int* wtmp = nullptr, int64_t* nnz_out = nullptr) {
     cudaStream_t st = h->stream;
+    int* width = wtmp ? wtmp : S.ub;
     E.n = A.n;
     E.nslices = (A.n + SELL_C - 1) / SELL_C;
     E.sptr = h->mem.alloc<int>(E.nslices + 1);
     const int wgrid = blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16);
-    k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, nullptr, S.ub);
+    int* cnt = len ? S.cnt + 19 : nullptr;
+    if (cnt) CUDA_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, len, nullptr, width, cnt);
     KERNEL_CHECK();
-    scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
-    E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
+    scan_exclusive(width, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
+    CUDA_CHECK(cudaMemcpyAsync(S.host, E.sptr + E.nslices, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (cnt) CUDA_CHECK(cudaMemcpyAsync(S.host + 1, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    E.padded = (int64_t)S.host[0] * SELL_C;
+    if (cnt) A.nnz = S.host[1];
+    if (nnz_out) *nnz_out = A.nnz;
     if ((double)E.padded > 1.3 * (double)A.nnz) {
         // uneven rows: sort by length inside windows (SELL-C-sigma)
         E.perm = h->mem.alloc<int>(A.n);
-        k_sort_window<<<(A.n + SIGMA - 1) / SIGMA, SIGMA, 0, st>>>(A.n, nullptr, A.ptr, E.perm);
+        k_sort_window<<<(A.n + SIGMA - 1) / SIGMA, SIGMA, 0, st>>>(A.n, nullptr, A.ptr, len, E.perm);
         KERNEL_CHECK();
-        k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, E.perm, S.ub);
+        k_sell_width<<<wgrid, TPB, 0, st>>>(A.n, E.nslices, A.ptr, len, E.perm, width, nullptr);
         KERNEL_CHECK();
-        scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
+        scan_exclusive(width, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
         E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
     }
     E.col = h->mem.alloc<int>(E.padded);
     E.val = h->mem.alloc<double>(E.padded);
     k_sell_fill<<<blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-        A.n, E.nslices, A.ptr, A.col, A.val, E.sptr, E.perm, E.col, E.val);
+        A.n, E.nslices, A.ptr, len, A.col, A.val, E.sptr, E.perm, E.col, E.val);
     KERNEL_CHECK();
     if (fp32) {
         E.val32 = h->mem.alloc<float>(E.padded);
@@ -2386,18 +2430,18 @@ void build_sell_hybrid(amg_hierarchy* h, const DevCsr& A, DevSell& E, Scratch& S
     E.sptr = h->mem.alloc<int>(E.nslices + 1);
     E.perm = h->mem.alloc<int>(nshort > 0 ? nshort : 1);
     k_sort_window<<<(nshort + SIGMA - 1) / SIGMA > 0 ? (nshort + SIGMA - 1) / SIGMA : 1, SIGMA, 0, st>>>(
-        nshort, short_rows, A.ptr, E.perm);
+        nshort, short_rows, A.ptr, nullptr, E.perm);
     KERNEL_CHECK();
     const int wgrid = blocks_for((long long)E.nslices * 32, TPB, h->num_sms * 16);
-    k_sell_width<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, E.perm, S.ub);
+    k_sell_width<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, nullptr, E.perm, S.ub, nullptr);
     KERNEL_CHECK();
     scan_exclusive(S.ub, E.sptr, E.nslices, E.sptr + E.nslices, st, S.scan_tmp);
     E.padded = (int64_t)read_int(E.sptr + E.nslices, S.host, st) * SELL_C;
     E.col = h->mem.alloc<int>(E.padded);
     E.val = h->mem.alloc<double>(E.padded);
-    k_sell_fill<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, A.col, A.val, E.sptr, E.perm, E.col, E.val);
+    k_sell_fill<<<wgrid, TPB, 0, st>>>(nshort, E.nslices, A.ptr, nullptr, A.col, A.val, E.sptr, E.perm, E.col,
+                                       E.val);
     KERNEL_CHECK();
-    CUDA_CHECK(cudaStreamSynchronize(st));
     S.mem.release(short_rows);
 }
 
@@ -2424,20 +2468,14 @@ void build_ap(amg_hierarchy* h, Level& L, int nc, Scratch& S, bool fp32) {
     if (L.A.max_row == 0 || L.A.max_row > G)
         launch_rows_long<false>(h, S, n, S.list1, S.cnt + 8, nullptr, nullptr, L.A.ptr, L.A.col, L.A.val, L.agg,
                                 L.p, L.A.ptr, S.ub, L.wminv, st, G, L.A.max_row);
+    // SELL straight from the row products: row i at L.A.ptr[i] in (skey, sval),
+    // S.ub[i] entries (S.off holds the slice widths meanwhile)
     DevCsr AP;
     AP.n = n;
-    AP.ptr = S.mem.alloc<int>(n + 1);
-    scan_exclusive(S.ub, AP.ptr, n, AP.ptr + n, st, S.scan_tmp);
-    AP.nnz = read_int(AP.ptr + n, S.host, st);
-    AP.col = S.mem.alloc<int>(AP.nnz);
-    AP.val = S.mem.alloc<double>(AP.nnz);
-    launch_copy(h, AP.nnz, n, L.A.ptr, AP.ptr, S.skey, S.sval, AP.col, AP.val, st);
-    L.ap_nnz = AP.nnz;
-    build_sell(h, AP, L.AP, S, fp32);
-    CUDA_CHECK(cudaStreamSynchronize(st));
-    S.mem.release(AP.ptr);
-    S.mem.release(AP.col);
-    S.mem.release(AP.val);
+    AP.ptr = L.A.ptr;
+    AP.col = S.skey;
+    AP.val = S.sval;
+    build_sell(h, AP, L.AP, S, fp32, S.ub, S.off, &L.ap_nnz);
 }
 
 void build_members(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
@@ -2460,8 +2498,7 @@ void build_members(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
 // can give a coarse matrix with more entries than the finest one.
 void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     if (nnz <= S.cap_nnz) return;
-    CUDA_CHECK(cudaStreamSynchronize(st));
-    S.mem.release(S.c);
+    S.mem.release(S.c);                 // stream-ordered: no synchronisation
     S.mem.release(S.skey);
     S.mem.release(S.sval);
     S.mem.release(S.spos);
@@ -2787,19 +2824,35 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             const int n = A.n;
             {
                 Scope sc_(&h->prof, st, S_WEIGHTS, 20.0 * A.nnz + 24.0 * n);
-                k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
+                // S.diag: (a_ii w_i) w_i of the current A. Level 0 starts from the
+                // diagonal the validation wrote; after a pairwise sweep the
+                // Galerkin copy has written it; a level's first sweep recomputes
+                // it (the level's matrix may come from the smoothed product).
+                if (s == 0 && l == 0) k_dww<<<grid_for(h, n), TPB, 0, st>>>(n, S.diag, w);
+                else if (s == 0) k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
                 KERNEL_CHECK();
                 launch_weights(weights_group(A.nnz, n), h->num_sms * 16, st, n, A.ptr, A.col, A.val, S.diag, w,
                                S.c);
             }
-            const int rr = ld_match(h, S, A);
+            int* pending = nullptr;
+            const int rr = ld_match(h, S, A, &pending);
             int nc = 0;
             {
+                // head flags and their scan only compare mate values, so they
+                // may run before the matching's error word is checked
                 Scope sc_(&h->prof, st, S_AGGREGATE, 0.0);
                 k_head_flags<<<grid_for(h, n), TPB, 0, st>>>(n, S.mate, S.flag);
                 KERNEL_CHECK();
                 scan_exclusive(S.flag, S.qid, n, S.cnt + 6, st, S.scan_tmp);
-                nc = read_int(S.cnt + 6, S.host, st);
+                if (pending) {
+                    CUDA_CHECK(cudaMemcpyAsync(S.host, S.cnt + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    CUDA_CHECK(cudaMemcpyAsync(S.host + 1, pending, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    CUDA_CHECK(cudaStreamSynchronize(st));
+                    check_suitor_error(S.host[1]);
+                    nc = S.host[0];
+                } else {
+                    nc = read_int(S.cnt + 6, S.host, st);
+                }
             }
             if (nc == n) break;                                   // nothing matched: end the level
             if (nseg) {
@@ -2839,13 +2892,11 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 R.mate = mate_keep; R.agg = sw.agg; R.p = sw.p; R.wc = sw.wc;
                 recs.push_back(R);
             } else {
-                CUDA_CHECK(cudaStreamSynchronize(st));
-                h->mem.release(sw.agg);
+                h->mem.release(sw.agg);                   // stream-ordered frees: no synchronisation
                 h->mem.release(sw.p);
             }
             // the previous intermediate matrix and smooth vector are no longer needed
             if (A.ptr != h->lev[l].A.ptr) {
-                CUDA_CHECK(cudaStreamSynchronize(st));
                 h->mem.release(A.ptr); h->mem.release(A.col); h->mem.release(A.val);
                 if (!o.keep_sweeps) h->mem.release(w);
             }
