@@ -124,10 +124,13 @@ __global__ void k_dww(int n, double* __restrict__ diag, const double* __restrict
 // division and the subtraction (this GPU's FP64 pipe bounds this kernel).
 // A group of G lanes per row (G = 1, 8, 16 or 32 by the mean row length),
 // the row's entries strided over the group, so long rows are shared out.
+// With mir set, the mirror position found for every upper entry (j > i) is
+// kept in mir[k] (-1: none); lower entries are not written.
 template <int G>
 __global__ void __launch_bounds__(TPB) k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                                                  const double* __restrict__ val, const double* __restrict__ dww,
-                                                 const double* __restrict__ w, double* __restrict__ c) {
+                                                 const double* __restrict__ w, double* __restrict__ c,
+                                                 int* __restrict__ mir) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int gl = threadIdx.x & (G - 1);
     const int ng = (gridDim.x * blockDim.x) / G;
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(TPB) k_weights(int n, const int* __restrict__ 
             c[k] = cw;
             const int mirror = find_in_row(ptr, col, j, i);
             if (mirror >= 0) c[mirror] = cw;
+            if (mir) mir[k] = mirror;
         }
     }
 }
@@ -776,8 +780,8 @@ constexpr unsigned long long NO_SUITOR = ~0ull;
 template <int G>
 __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                                                     const double* __restrict__ c, const int* __restrict__ spos,
-                                                    int2* __restrict__ nq, unsigned long long* __restrict__ suitor,
-                                                    int* err) {
+                                                    const int* __restrict__ mir, int2* __restrict__ nq,
+                                                    unsigned long long* __restrict__ suitor, int* err) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -797,7 +801,7 @@ __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict
             if (!is_edge(c[k])) continue;           // not an edge (diagonal, zero pair)
             ++edges;
             const int u = col[k];
-            const int km = find_in_row(ptr, col, u, v);
+            const int km = mir && u > v ? mir[k] : find_in_row(ptr, col, u, v);   // mir: upper entries
             if (km < 0) {                            // no mirror entry: pattern not symmetric
                 nq[spos[k]] = make_int2(-1, -1);
                 atomicOr(err, 1);
@@ -870,24 +874,33 @@ __global__ void k_head_flags(int n, const int* __restrict__ mate, int* __restric
 
 // Aggregate q = number of heads (smallest members) before it. Pair columns
 // are w restricted to the pair and normalised; singletons sign(w_s).
-__global__ void k_aggregate(int n, const int* __restrict__ mate, const int* __restrict__ qid,
-                            const double* __restrict__ w, int* __restrict__ agg, double* __restrict__ p,
-                            double* __restrict__ wc, int* __restrict__ heads, int* __restrict__ mate_out) {
+// Heads: the smallest member of each aggregate, heads[qid[i]] = i (and the
+// kept copy of the matching with -1 for every unmatched vertex).
+__global__ void k_heads(int n, const int* __restrict__ mate, const int* __restrict__ qid, int* __restrict__ heads,
+                        int* __restrict__ mate_out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int j = mate[i];
         if (mate_out) mate_out[i] = j < 0 ? -1 : j;
-        if (j >= 0 && j < i) continue;
-        const int q = qid[i];
+        if (j < 0 || j > i) heads[qid[i]] = i;
+    }
+}
+
+// One thread per aggregate q (all lanes busy on the FP64 square root and
+// divisions, which bound this step): agg, the Eq. 4 column p and wc[q].
+__global__ void k_aggregate(int nc, const int* __restrict__ heads, const int* __restrict__ mate,
+                            const double* __restrict__ w, int* __restrict__ agg, double* __restrict__ p,
+                            double* __restrict__ wc) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int i = heads[q];
+        const int j = mate[i];
         const double wi = w[i];
-        heads[q] = i;
+        agg[i] = q;
         if (j < 0) {
-            agg[i] = q;
             p[i] = wi > 0.0 ? 1.0 : -1.0;
             wc[q] = fabs(wi);
         } else {
             const double wj = w[j];
             const double s = __dsqrt_rn(__dadd_rn(__dmul_rn(wi, wi), __dmul_rn(wj, wj)));
-            agg[i] = q;
             agg[j] = q;
             p[i] = __ddiv_rn(wi, s);
             p[j] = __ddiv_rn(wj, s);
@@ -1285,12 +1298,12 @@ int weights_group(long long nnz, long long n) {
 }
 
 void launch_weights(int G, int grid_cap, cudaStream_t st, int n, const int* ptr, const int* col, const double* val,
-                    const double* dww, const double* w, double* c) {
+                    const double* dww, const double* w, double* c, int* mir = nullptr) {
     const int blocks = blocks_for((long long)n * G, TPB, grid_cap);
-    if (G == 1) k_weights<1><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
-    else if (G == 8) k_weights<8><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
-    else if (G == 16) k_weights<16><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
-    else k_weights<32><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    if (G == 1) k_weights<1><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
+    else if (G == 8) k_weights<8><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
+    else if (G == 16) k_weights<16><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
+    else k_weights<32><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
     KERNEL_CHECK();
 }
 
@@ -1829,8 +1842,8 @@ __global__ void k_sort_pairs(int nrows, const int* __restrict__ list, const int*
 //              memory), at xoff[p] of (xcol, xval); rows whose count is above
 //              the capacity are left to a launch of larger capacity;
 //   SPG_ONE    one pass: write the sorted row into a scratch slot (at
-//              xoff[p] * stride, or t * stride for the t-th listed row) and
-//              its count to cnt[p].
+//              xoff[p] * stride, or without xoff t * stride for the t-th
+//              listed row) and its count to cnt[p].
 // In SPG_COUNT and SPG_ONE a row with more columns stops at once and is
 // appended to `longs` for a launch of larger capacity (its count set to
 // INT_MAX until then), or flags `overflow` when there is no such list.
@@ -1905,21 +1918,32 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
         int jn = eb < ee ? ycol[eb] : 0;
         double yn = eb < ee ? yval[eb] : 0.0;
         int fbn = eb < ee ? zptr[jn] : 0, fen = eb < ee ? zptr[jn + 1] : 0;
+        // a block's steps wait on the Z rows (DRAM-resident on large levels):
+        // the first chunk of the next step is loaded during the current one
+        int qn = BLOCK && fbn + tid < fen ? zcol[fbn + tid] : 0;
+        double zn = BLOCK && fbn + tid < fen ? zval[fbn + tid] : 0.0;
         for (int e = eb; e < ee && !full; ++e) {
             const double y = yn;
             const int fb = fbn, fe = fen;
+            const int q0 = qn;
+            const double z0 = zn;
             if (e + 1 < ee) {                              // the next step's row, loaded ahead
                 jn = ycol[e + 1];
                 yn = yval[e + 1];
                 fbn = zptr[jn];
                 fen = zptr[jn + 1];
+                if (BLOCK) {
+                    qn = fbn + tid < fen ? zcol[fbn + tid] : 0;
+                    zn = fbn + tid < fen ? zval[fbn + tid] : 0.0;
+                }
             }
             for (int f0 = fb; f0 < fe && !full; f0 += U) {
                 const int f = f0 + tid;
                 bool added = false;
                 if (f < fe) {
-                    const int q = zcol[f];
-                    const double term = __dmul_rn(y, zval[f]);
+                    const bool pre = BLOCK && f0 == fb;
+                    const int q = pre ? q0 : zcol[f];
+                    const double term = __dmul_rn(y, pre ? z0 : zval[f]);
                     unsigned hs = ((unsigned)q * 2654435769u) >> hshift;
                     // ends: a step starts with at most CAP / 2 columns and adds at
                     // most U <= CAP / 2, so the key or a free slot is always found
@@ -1944,10 +1968,10 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
                         hs = (hs + 1) & (unsigned)(CAP - 1);
                     }
                 }
-                used += count(added);
+                used += count(added);   // in a block also the barrier between steps (__syncthreads_count)
                 full = used > (CAP >> 1);
             }
-            sync();
+            if (!BLOCK) __syncwarp();   // a ballot does not order shared memory: the warp's step barrier
         }
         if (full) {
             if (tid == 0) {
@@ -2003,13 +2027,105 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
                 sync();
             }
         const long long c0 = MODE == SPG_FILL ? (long long)xoff[p]
-                                              : (list ? (long long)t * stride : (long long)xoff[p] * stride);
+                                              : (xoff ? (long long)xoff[p] * stride : (long long)t * stride);
         for (int s = tid; s < m; s += U) {
             xcol[c0 + s] = K[s];
             xval[c0 + s] = V[s];
         }
         if (MODE == SPG_ONE && tid == 0) cnt[p] = m;
         sync();
+    }
+}
+
+// Rows of X = Y Z with at most 32 terms, a warp each (expand, sort,
+// compress): lane t holds term t in the order of the hash kernel's steps
+// (entries of row p of Y in column order, then the entries of the Z row each
+// one reads), its stable rank by column comes from a shuffle sweep, the terms
+// are placed in rank order in shared memory, and the first lane of every run
+// of equal columns sums the run left to right from its first term: for every
+// column the same products added in the same order as the hash kernel (and
+// the oracle), bit for bit, without a table to clear and sweep. The sorted
+// row goes to the first tier's scratch slot (xoff[p] * 8 entries, which
+// holds min(terms, its capacity)) and its count to cnt[p]; a row of Y with
+// more than 32 entries or a row with more than 32 terms is appended to
+// longs for the hash kernel.
+__global__ void __launch_bounds__(TPB) k_spgemm_warp(int nrows, const int* __restrict__ yptr,
+                                                     const int* __restrict__ ycol, const double* __restrict__ yval,
+                                                     const int* __restrict__ zptr, const int* __restrict__ zcol,
+                                                     const double* __restrict__ zval, int* __restrict__ cnt,
+                                                     const int* __restrict__ xoff, int* __restrict__ xcol,
+                                                     double* __restrict__ xval, int* __restrict__ longs,
+                                                     int* __restrict__ nlongs) {
+    __shared__ int Ks[TPB];
+    __shared__ double Vs[TPB];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int* K = Ks + wid * 32;
+    double* V = Vs + wid * 32;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int warp_first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int p = warp_first; p < nrows; p += nw) {                 // p is uniform in the warp
+        const int eb = yptr[p], ly = yptr[p + 1] - eb;
+        if (ly > 32) {
+            if (lane == 0) longs[atomicAdd(nlongs, 1)] = p;
+            continue;
+        }
+        int zb = 0, len = 0;
+        double y = 0.0;
+        if (lane < ly) {
+            const int j = ycol[eb + lane];
+            y = yval[eb + lane];
+            zb = zptr[j];
+            len = zptr[j + 1] - zb;
+        }
+        int incl = len;                                              // inclusive scan of the Z row lengths
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int T = __shfl_sync(FULL_MASK, incl, 31);
+        if (T > 32) {
+            if (lane == 0) longs[atomicAdd(nlongs, 1)] = p;
+            continue;
+        }
+        const int start = incl - len;
+        for (int k = 0; k < len; ++k) K[start + k] = lane;          // owner entry of every term slot
+        __syncwarp();
+        const int e = lane < T ? K[lane] : 0;
+        const double ye = __shfl_sync(FULL_MASK, y, e);
+        const int zbe = __shfl_sync(FULL_MASK, zb, e);
+        const int se = __shfl_sync(FULL_MASK, start, e);
+        int q = 0x7fffffff;
+        double term = 0.0;
+        if (lane < T) {
+            const int f = zbe + (lane - se);
+            q = zcol[f];
+            term = __dmul_rn(ye, zval[f]);
+        }
+        int rank = 0;                                                // stable rank by column
+        for (int u = 0; u < T; ++u) {
+            const int qu = __shfl_sync(FULL_MASK, q, u);
+            rank += (qu < q || (qu == q && u < lane)) ? 1 : 0;
+        }
+        __syncwarp();
+        if (lane < T) {
+            K[rank] = q;
+            V[rank] = term;
+        }
+        __syncwarp();
+        const int kr = lane < T ? K[lane] : 0;
+        const bool head = lane < T && (lane == 0 || K[lane - 1] != kr);
+        const unsigned heads = __ballot_sync(FULL_MASK, head);
+        const long long c0 = (long long)xoff[p] * 8;
+        if (head) {
+            double sum = V[lane];
+            for (int k = lane + 1; k < T && K[k] == kr; ++k) sum = __dadd_rn(sum, V[k]);
+            const int idx = __popc(heads & ((1u << lane) - 1u));
+            xcol[c0 + idx] = kr;
+            xval[c0 + idx] = sum;
+        }
+        if (lane == 0) cnt[p] = __popc(heads);
+        __syncwarp();
     }
 }
 
@@ -2045,7 +2161,7 @@ __global__ void k_spgemm_copy(int nrows, const int* __restrict__ list, const int
         const int p = list ? list[t] : t;
         const int m = cnt[p];
         if (m > limit) continue;
-        const long long src = list ? (long long)t * stride : (long long)xoff[p] * stride;
+        const long long src = xoff ? (long long)xoff[p] * stride : (long long)t * stride;
         const int dst = xptr[p];
         for (int s = lane; s < m; s += 32) {
             xcol[dst + s] = scol[src + s];
@@ -2073,6 +2189,7 @@ struct Scratch {
     double* sval = nullptr;   // nnz
     int* spos = nullptr;      // nnz: sorted position of each entry (matching by proposals)
     int2* nq = nullptr;       // nnz: (neighbour, mirror's sorted position) per sorted entry
+    int* mir = nullptr;       // nnz: mirror position of each upper entry, -1 none (matching by proposals)
     unsigned long long* suitor = nullptr;   // n
     long long cap_nnz = 0;    // entries c, skey and sval hold
     int* scan_tmp = nullptr;
@@ -2265,11 +2382,14 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int** pending) {
             const int G = rows_group(A.nnz, n);
             const int mblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
             if (G == 8)
-                k_mirror_pos<8><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+                k_mirror_pos<8><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
+                                                          err);
             else if (G == 16)
-                k_mirror_pos<16><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+                k_mirror_pos<16><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
+                                                          err);
             else
-                k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
+                k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
+                                                          err);
             KERNEL_CHECK();
         }
         suitor_match(h, S, A, err);
@@ -2503,11 +2623,13 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.mem.release(S.sval);
     S.mem.release(S.spos);
     S.mem.release(S.nq);
+    S.mem.release(S.mir);
     S.c = S.mem.alloc<double>(nnz);
     S.skey = S.mem.alloc<int>(nnz);
     S.sval = S.mem.alloc<double>(nnz);
     S.spos = S.mem.alloc<int>(nnz);
     S.nq = S.mem.alloc<int2>(nnz);
+    S.mir = S.mem.alloc<int>(nnz);
     S.cap_nnz = nnz;
 }
 
@@ -2531,26 +2653,29 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
     auto smem = [&](int t) { return (size_t)SPG_UNITS[t] * cap(t) * (sizeof(double) + sizeof(int)); };
     const int smax = (int)smem(SPG_TIERS - 1);
     for (const void* f : {(const void*)k_spgemm_hash<SPG_COUNT, true>, (const void*)k_spgemm_hash<SPG_FILL, true>,
-                          (const void*)k_spgemm_hash<SPG_ONE, true>})
+                          (const void*)k_spgemm_hash<SPG_ONE, true>, (const void*)k_spgemm_hash<SPG_COUNT, false>,
+                          (const void*)k_spgemm_hash<SPG_FILL, false>, (const void*)k_spgemm_hash<SPG_ONE, false>})
         CUDA_CHECK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
     int rows[SPG_TIERS] = {n, 0, 0, 0};
+    const int* first_list = nullptr;                    // rows the warp pass left to the first hash tier
+    const int* first_count = nullptr;
     bool one[SPG_TIERS] = {false, false, false, false};   // tier done in one pass (scratch slots)
     int* scol[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
     double* sval[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
     auto blocks = [&](int t) {
-        const int cp = h->num_sms * (t == 0 ? 8 : (t == 1 ? 6 : 2));
+        const int cp = h->num_sms * (t == 0 ? 8 : (t == 1 ? 9 : 2));
         return std::max(1, std::min((rows[t] + SPG_UNITS[t] - 1) / SPG_UNITS[t], cp));
     };
     auto launch = [&](int mode, int t, const int* xoff, long long stride, int* xcol, double* xval) {
         const bool last = t == SPG_TIERS - 1;
         int* longs = (mode == SPG_FILL || last) ? nullptr : lists[t + 1];
         int* nlongs = (mode == SPG_FILL || last) ? nullptr : nl + t;
-        const int* lst = lists[t];
-        const int* nls = t ? nl + t - 1 : nullptr;
+        const int* lst = t ? lists[t] : first_list;
+        const int* nls = t ? nl + t - 1 : first_count;
         const dim3 g(blocks(t)), b(SPG_THREADS[t]);
         const size_t sm = smem(t);
 #define SPG_ARGS n, lst, nls, cap(t), Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, xoff, stride, xcol, xval, longs, nlongs, over
-        if (t == 0) {
+        if (SPG_UNITS[t] > 1) {                         // a warp per row
             if (mode == SPG_COUNT) k_spgemm_hash<SPG_COUNT, false><<<g, b, sm, st>>>(SPG_ARGS);
             else if (mode == SPG_FILL) k_spgemm_hash<SPG_FILL, false><<<g, b, sm, st>>>(SPG_ARGS);
             else k_spgemm_hash<SPG_ONE, false><<<g, b, sm, st>>>(SPG_ARGS);
@@ -2572,6 +2697,14 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
         const long long units = read_int(S.off + n, S.host, st);
         scol[0] = S.mem.alloc<int>(units * 8 + 1);
         sval[0] = S.mem.alloc<double>(units * 8 + 1);
+        // rows of at most 32 terms by the warp pass, the rest (listed in
+        // S.heads, counted in S.cnt[24]) by the first hash tier
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 24, 0, sizeof(int), st));
+        k_spgemm_warp<<<blocks_for((long long)n * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
+            n, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, scol[0], sval[0], S.heads, S.cnt + 24);
+        KERNEL_CHECK();
+        first_list = S.heads;
+        first_count = S.cnt + 24;
         launch(SPG_ONE, 0, S.off, 8, scol[0], sval[0]);
     } else {
         launch(SPG_COUNT, 0, nullptr, 0, nullptr, nullptr);
@@ -2608,7 +2741,8 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& 
         const int* lst = lists[t];
         const int* nls = t ? nl + t - 1 : nullptr;
         k_spgemm_copy<<<blocks_for((long long)rows[t] * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-            n, lst, nls, cap(t) / 2, S.ub, S.off, t ? cap(t) / 2 : 8, scol[t], sval[t], X.ptr, X.col, X.val);
+            n, lst, nls, cap(t) / 2, S.ub, t ? nullptr : S.off, t ? cap(t) / 2 : 8, scol[t], sval[t], X.ptr, X.col,
+            X.val);
         KERNEL_CHECK();
     }
     for (int t = 0; t < SPG_TIERS; ++t)
@@ -2741,6 +2875,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.sval = S.mem.alloc<double>(nnz0);
     S.spos = S.mem.alloc<int>(nnz0);
     S.nq = S.mem.alloc<int2>(nnz0);
+    S.mir = S.mem.alloc<int>(nnz0);
     S.suitor = S.mem.alloc<unsigned long long>(n0);
     S.cap_nnz = nnz0;
     S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
@@ -2831,8 +2966,9 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 if (s == 0 && l == 0) k_dww<<<grid_for(h, n), TPB, 0, st>>>(n, S.diag, w);
                 else if (s == 0) k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
                 KERNEL_CHECK();
+                int* mir = o.match_kernel == 0 ? S.mir : nullptr;
                 launch_weights(weights_group(A.nnz, n), h->num_sms * 16, st, n, A.ptr, A.col, A.val, S.diag, w,
-                               S.c);
+                               S.c, mir);
             }
             int* pending = nullptr;
             const int rr = ld_match(h, S, A, &pending);
@@ -2868,8 +3004,9 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             int* mate_keep = o.keep_sweeps ? h->mem.alloc<int>(n) : nullptr;
             {
                 Scope sc_(&h->prof, st, S_AGGREGATE, 0.0);
-                k_aggregate<<<grid_for(h, n), TPB, 0, st>>>(n, S.mate, S.qid, w, sw.agg, sw.p, sw.wc, S.heads,
-                                                            mate_keep);
+                k_heads<<<grid_for(h, n), TPB, 0, st>>>(n, S.mate, S.qid, S.heads, mate_keep);
+                KERNEL_CHECK();
+                k_aggregate<<<grid_for(h, nc), TPB, 0, st>>>(nc, S.heads, S.mate, w, sw.agg, sw.p, sw.wc);
                 KERNEL_CHECK();
             }
             DevCsr C;
