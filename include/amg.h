@@ -97,10 +97,12 @@ typedef struct {
     int smooth_p;      /* [0] 1: smoothed prolongator Pbar = (I - omega D^-1 A) P on every level, omega =
                           4 / (3 ||D^-1 A||_inf) (see omega_rule), coarse matrices Pbar^T A Pbar (Section 3.2;
                           the paper's VA3 setting; its GPU runs use l1-Jacobi with pre = post = 4). V-cycle
-                          (cycle = 0), any pre/post, single right-hand-side solves only. A row of A Pbar or
-                          of Pbar^T A Pbar may hold up to 8192 entries (else AMG_ERR_TOO_LARGE); the
+                          (cycle = 0), any pre/post, single right-hand-side solves only. When the next
+                          level has more than 12288 rows, a row of A Pbar or of Pbar^T A Pbar may hold up to
+                          8192 entries (else AMG_ERR_TOO_LARGE); narrower products have no row limit. The
                           environment variable AMG_SPGEMM_CAP_SHIFT = k (0..3) divides that limit and the
-                          product's internal capacity tiers by 2^k, so small tests reach every tier */
+                          product's internal capacity tiers by 2^k (a tier of a warp per row keeps at least
+                          64 slots) and turns the narrow-product path off, so small tests reach every tier */
     int autotune;      /* [0] 1: choose the launch shapes of the V-cycle kernels (grid per level and kernel; lanes
                           per row and columns per lane of block solves) by timing candidates once per shape;
                           results are cached per process (see amg_tune_save). 0: fixed heuristics */

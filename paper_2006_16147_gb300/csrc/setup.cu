@@ -1848,14 +1848,16 @@ __global__ void k_sort_pairs(int nrows, const int* __restrict__ list, const int*
 // appended to `longs` for a launch of larger capacity (its count set to
 // INT_MAX until then), or flags `overflow` when there is no such list.
 enum SpgMode : int { SPG_COUNT = 0, SPG_FILL = 1, SPG_ONE = 2 };
-constexpr int SPG_TIERS = 4;
-constexpr int SPG_CAP[SPG_TIERS] = {512, 2048, 8192, 16384};   // hash slots per row; at most half are used
-constexpr int SPG_UNITS[SPG_TIERS] = {4, 1, 1, 1};             // rows per block (warps, or one block)
-constexpr int SPG_THREADS[SPG_TIERS] = {128, 128, 256, 512};   // threads per block
+constexpr int SPG_TIERS = 5;
+constexpr int SPG_CAP[SPG_TIERS] = {128, 512, 2048, 8192, 16384};   // hash slots per row; at most half are used
+constexpr int SPG_UNITS[SPG_TIERS] = {4, 4, 1, 1, 1};               // rows per block (warps, or one block)
+constexpr int SPG_THREADS[SPG_TIERS] = {128, 128, 128, 256, 512};   // threads per block
+constexpr int SPG_WARP_MIN_CAP = 64;   // a warp tier's capacity stays >= 64 slots when divided for tests
 // a unit's threads per step (32, or the block) never exceed half the capacity,
 // also with the capacities divided by 8 for tests
-static_assert(32 <= (SPG_CAP[0] >> 3) / 2 && SPG_THREADS[1] <= (SPG_CAP[1] >> 3) / 2 &&
-                  SPG_THREADS[2] <= (SPG_CAP[2] >> 3) / 2 && SPG_THREADS[3] <= (SPG_CAP[3] >> 3) / 2,
+static_assert(32 <= SPG_WARP_MIN_CAP / 2 && SPG_UNITS[0] > 1 && SPG_UNITS[1] > 1 &&
+                  SPG_THREADS[2] <= (SPG_CAP[2] >> 3) / 2 && SPG_THREADS[3] <= (SPG_CAP[3] >> 3) / 2 &&
+                  SPG_THREADS[4] <= (SPG_CAP[4] >> 3) / 2,
               "probe loop needs a free slot");
 template <int MODE, bool BLOCK>
 __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
@@ -2126,6 +2128,104 @@ __global__ void __launch_bounds__(TPB) k_spgemm_warp(int nrows, const int* __res
         }
         if (lane == 0) cnt[p] = __popc(heads);
         __syncwarp();
+    }
+}
+
+// Rows of X = Y Z when X has at most SPG_DENSE_MAX columns, a block each: a
+// dense accumulator V[ncols] and an occupancy bitmap in shared memory. Step
+// e (entry y of row p of Y) adds y z for every entry z of the Z row it reads;
+// within a step the columns are distinct, a column's first term starts its
+// sum and later steps add in step order (a barrier between steps): the hash
+// kernel's and the oracle's order, bit for bit, with no probing and no sort
+// (the bitmap is read in column order). The row goes to its scratch slot at
+// xoff[p] * 8 (min(terms, ncols) entries) and its count to cnt[p].
+constexpr int SPG_DENSE_MAX = 12288;
+constexpr int SPG_DENSE_THREADS = 256;
+__global__ void __launch_bounds__(SPG_DENSE_THREADS) k_spgemm_dense(
+    int nrows, int ncols, const int* __restrict__ yptr, const int* __restrict__ ycol,
+    const double* __restrict__ yval, const int* __restrict__ zptr, const int* __restrict__ zcol,
+    const double* __restrict__ zval, int* __restrict__ cnt, const int* __restrict__ xoff, int* __restrict__ xcol,
+    double* __restrict__ xval) {
+    extern __shared__ double dsm[];
+    __shared__ int wtot[SPG_DENSE_THREADS / 32];
+    double* V = dsm;
+    unsigned* F = reinterpret_cast<unsigned*>(dsm + ncols);
+    const int nw = (ncols + 31) >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int U = SPG_DENSE_THREADS;
+    const int per = (nw + U - 1) / U;                       // bitmap words per thread in the read-out
+    for (int p = blockIdx.x; p < nrows; p += gridDim.x) {
+        for (int w = tid; w < nw; w += U) F[w] = 0u;
+        __syncthreads();
+        const int eb = yptr[p], ee = yptr[p + 1];
+        int jn = eb < ee ? ycol[eb] : 0;
+        double yn = eb < ee ? yval[eb] : 0.0;
+        int fbn = eb < ee ? zptr[jn] : 0, fen = eb < ee ? zptr[jn + 1] : 0;
+        int qn = fbn + tid < fen ? zcol[fbn + tid] : 0;        // first chunk of the next step, loaded ahead
+        double zn = fbn + tid < fen ? zval[fbn + tid] : 0.0;
+        for (int e = eb; e < ee; ++e) {
+            const double y = yn;
+            const int fb = fbn, fe = fen;
+            const int q0 = qn;
+            const double z0 = zn;
+            if (e + 1 < ee) {
+                jn = ycol[e + 1];
+                yn = yval[e + 1];
+                fbn = zptr[jn];
+                fen = zptr[jn + 1];
+                qn = fbn + tid < fen ? zcol[fbn + tid] : 0;
+                zn = fbn + tid < fen ? zval[fbn + tid] : 0.0;
+            }
+            for (int f = fb + tid; f < fe; f += U) {
+                const bool pre = f - fb < U;
+                const int q = pre ? q0 : zcol[f];
+                const double term = __dmul_rn(y, pre ? z0 : zval[f]);
+                const unsigned bit = 1u << (q & 31);
+                if (F[q >> 5] & bit) {
+                    V[q] = __dadd_rn(V[q], term);
+                } else {
+                    V[q] = term;
+                    atomicOr(&F[q >> 5], bit);
+                }
+            }
+            __syncthreads();                                    // the barrier between steps
+        }
+        // read-out in column order: thread t takes words [t * per, (t + 1) * per)
+        int mine = 0;
+        for (int k = 0; k < per; ++k) {
+            const int w = tid * per + k;
+            if (w < nw) mine += __popc(F[w]);
+        }
+        int incl = mine;                                        // block exclusive scan of the counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wtot[wid] = incl;
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < U / 32; ++w2) {
+            before += w2 < wid ? wtot[w2] : 0;
+            total += wtot[w2];
+        }
+        int pos = before + incl - mine;
+        const long long c0 = (long long)xoff[p] * 8;
+        for (int k = 0; k < per; ++k) {
+            const int w = tid * per + k;
+            if (w >= nw) break;
+            unsigned bits = F[w];
+            while (bits) {
+                const int q = (w << 5) + __ffs(bits) - 1;
+                bits &= bits - 1;
+                xcol[c0 + pos] = q;
+                xval[c0 + pos] = V[q];
+                ++pos;
+            }
+        }
+        if (tid == 0) cnt[p] = total;
+        __syncthreads();                                        // wtot and F are reused by the next row
     }
 }
 
@@ -2638,32 +2738,70 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
 // scratch slots (then the offsets and a copy into place), or, when the slots
 // would be too large, counts them and fills them after the offsets. The
 // result lives in the scratch arena when `scratch`, else in the hierarchy's.
-DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, Scratch& S, bool scratch) {
+// A product with at most SPG_DENSE_MAX columns (ncols) takes the dense
+// accumulator kernel instead, a block per row, into the same kind of slots.
+// AMG_SPGEMM_CAP_SHIFT = k (0..3) divides every hash capacity by 2^k and
+// turns the dense path off, so that small test matrices reach every tier.
+DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, int ncols, Scratch& S, bool scratch) {
     cudaStream_t st = h->stream;
     const int n = Y.n;
+    const char* shift_env = std::getenv("AMG_SPGEMM_CAP_SHIFT");
+    if (!shift_env && ncols <= SPG_DENSE_MAX && (long long)n * ((ncols + 7) / 8) <= 0x7fffffffLL) {
+        k_spgemm_units<<<grid_for(h, n), TPB, 0, st>>>(n, Y.ptr, Y.col, Z.ptr, ncols, S.flag);
+        KERNEL_CHECK();
+        scan_exclusive(S.flag, S.off, n, S.off + n, st, S.scan_tmp);
+        const long long units = read_int(S.off + n, S.host, st);
+        int* dcol = S.mem.alloc<int>(units * 8 + 1);
+        double* dval = S.mem.alloc<double>(units * 8 + 1);
+        const int smd = (int)(sizeof(double) * ncols + sizeof(unsigned) * ((ncols + 31) / 32));
+        CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * SPG_DENSE_MAX + sizeof(unsigned) * (SPG_DENSE_MAX / 32))));
+        const int per_sm = std::max(1, std::min(8, (200 * 1024) / std::max(smd, 1)));
+        if (n > 0) {
+            k_spgemm_dense<<<std::min(n, h->num_sms * per_sm), SPG_DENSE_THREADS, smd, st>>>(
+                n, ncols, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, dcol, dval);
+            KERNEL_CHECK();
+        }
+        DevCsr X;
+        X.n = n;
+        X.ptr = scratch ? S.mem.alloc<int>(n + 1) : h->mem.alloc<int>(n + 1);
+        scan_exclusive(S.ub, X.ptr, n, X.ptr + n, st, S.scan_tmp);
+        finish_csr(h, S, X);
+        X.col = scratch ? S.mem.alloc<int>(X.nnz) : h->mem.alloc<int>(X.nnz);
+        X.val = scratch ? S.mem.alloc<double>(X.nnz) : h->mem.alloc<double>(X.nnz);
+        if (n > 0) {
+            k_spgemm_copy<<<blocks_for((long long)n * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
+                n, nullptr, nullptr, ncols, S.ub, S.off, 8, dcol, dval, X.ptr, X.col, X.val);
+            KERNEL_CHECK();
+        }
+        S.mem.release(dcol);
+        S.mem.release(dval);
+        return X;
+    }
     int* over = S.cnt + 10;
-    int* nl = S.cnt + 11;                               // rows listed for tiers 1, 2 and 3
-    int* lists[SPG_TIERS] = {nullptr, S.list0, S.list1, S.qid};
-    CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 4 * sizeof(int), st));
-    // AMG_SPGEMM_CAP_SHIFT = k (0..3) divides every capacity by 2^k, so that
-    // small test matrices reach every tier
+    int* nl = S.cnt + 11;                               // rows listed for tiers 1 .. 4
+    int* lists[SPG_TIERS] = {nullptr, S.list0, S.list1, S.qid, S.spos};   // spos: free once the sweeps are done
+    CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 5 * sizeof(int), st));
     int cshift = 0;
-    if (const char* e = std::getenv("AMG_SPGEMM_CAP_SHIFT")) cshift = std::max(0, std::min(3, std::atoi(e)));
-    auto cap = [&](int t) { return SPG_CAP[t] >> cshift; };
+    if (shift_env) cshift = std::max(0, std::min(3, std::atoi(shift_env)));
+    auto cap = [&](int t) {
+        return SPG_UNITS[t] > 1 ? std::max(SPG_CAP[t] >> cshift, SPG_WARP_MIN_CAP) : SPG_CAP[t] >> cshift;
+    };
     auto smem = [&](int t) { return (size_t)SPG_UNITS[t] * cap(t) * (sizeof(double) + sizeof(int)); };
     const int smax = (int)smem(SPG_TIERS - 1);
     for (const void* f : {(const void*)k_spgemm_hash<SPG_COUNT, true>, (const void*)k_spgemm_hash<SPG_FILL, true>,
                           (const void*)k_spgemm_hash<SPG_ONE, true>, (const void*)k_spgemm_hash<SPG_COUNT, false>,
                           (const void*)k_spgemm_hash<SPG_FILL, false>, (const void*)k_spgemm_hash<SPG_ONE, false>})
         CUDA_CHECK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    int rows[SPG_TIERS] = {n, 0, 0, 0};
+    int rows[SPG_TIERS] = {n, 0, 0, 0, 0};
     const int* first_list = nullptr;                    // rows the warp pass left to the first hash tier
     const int* first_count = nullptr;
-    bool one[SPG_TIERS] = {false, false, false, false};   // tier done in one pass (scratch slots)
-    int* scol[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
-    double* sval[SPG_TIERS] = {nullptr, nullptr, nullptr, nullptr};
+    bool one[SPG_TIERS] = {};                           // tier done in one pass (scratch slots)
+    int* scol[SPG_TIERS] = {};
+    double* sval[SPG_TIERS] = {};
     auto blocks = [&](int t) {
-        const int cp = h->num_sms * (t == 0 ? 8 : (t == 1 ? 9 : 2));
+        static constexpr int per_sm[SPG_TIERS] = {16, 8, 9, 2, 2};   // blocks per SM (threads, shared memory)
+        const int cp = h->num_sms * per_sm[t];
         return std::max(1, std::min((rows[t] + SPG_UNITS[t] - 1) / SPG_UNITS[t], cp));
     };
     auto launch = [&](int mode, int t, const int* xoff, long long stride, int* xcol, double* xval) {
@@ -2832,8 +2970,8 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     }
 
     // C = Pbar^T (A Pbar): two sparse products in the oracle's order
-    DevCsr W = spgemm_hash(h, A, P, S, true);
-    DevCsr C = spgemm_hash(h, T, W, S, false);
+    DevCsr W = spgemm_hash(h, A, P, nc, S, true);
+    DevCsr C = spgemm_hash(h, T, W, nc, S, false);
     S.mem.release(W.val);
     S.mem.release(W.col);
     S.mem.release(W.ptr);

@@ -43,9 +43,16 @@ def orc():
     return oracle
 
 
+@pytest.mark.parametrize("path", ["default", "hash"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_smoothed_setup_bit_exact(orc, name):
+def test_smoothed_setup_bit_exact(orc, name, path, monkeypatch):
+    # default: products with at most 12288 columns take the dense-accumulator
+    # kernel (every product of these small cases); hash: AMG_SPGEMM_CAP_SHIFT
+    # = 0 turns that path off, so the same products go through the warp pass
+    # and the hash tiers at full capacity
     from paper_2006_16147_gb300 import amg
+    if path == "hash":
+        monkeypatch.setenv("AMG_SPGEMM_CAP_SHIFT", "0")
     mk, seed, mc = CASES[name]
     A = mk()
     w = _w(A, seed)
@@ -164,8 +171,9 @@ def test_smoothed_option_checks():
 
 
 def test_smoothed_setup_every_capacity_tier(orc, monkeypatch):
-    # capacities divided by 4 (tiers of 64, 256, 1024, 2048 columns): the
-    # wide coarse rows (up to 1134 columns) pass through every tier
+    # capacities divided by 4 (tiers of 32, 64, 256, 1024, 2048 columns; the
+    # dense path off): the wide coarse rows (up to 1134 columns) pass through
+    # every tier
     from paper_2006_16147_gb300 import amg
     monkeypatch.setenv("AMG_SPGEMM_CAP_SHIFT", "2")
     mk, seed, mc = CASES["spd_wide_coarse"]
