@@ -1767,6 +1767,43 @@ __global__ void k_col_fill(int n, const int* __restrict__ ptr, const int* __rest
 // block per listed row (BLOCK = true), bitonic sort in shared memory. A row
 // longer than CAP is appended to `longs` for the block launch, or flags
 // `overflow` when there is no such list.
+// Rows of at most 32 (key, value) pairs sorted by key in registers, a warp
+// each (a bitonic network over the lanes; the keys of a row are distinct row
+// indices); longer rows are appended to longs for k_sort_pairs.
+__global__ void __launch_bounds__(TPB) k_sort_pairs_warp(int nrows, const int* __restrict__ ptr,
+                                                         int* __restrict__ key, double* __restrict__ val,
+                                                         int* __restrict__ longs, int* __restrict__ nlongs) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {   // uniform in the warp
+        const int b = ptr[r], m = ptr[r + 1] - b;
+        if (m <= 1) continue;
+        if (m > 32) {
+            if (lane == 0) longs[atomicAdd(nlongs, 1)] = r;
+            continue;
+        }
+        int k = lane < m ? key[b + lane] : 0x7fffffff;
+        double v = lane < m ? val[b + lane] : 0.0;
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const int pk = __shfl_xor_sync(FULL_MASK, k, stride);
+                const double pv = __shfl_xor_sync(FULL_MASK, v, stride);
+                const bool up = (lane & size) == 0;              // ascending run (size 32: the whole warp)
+                const bool lower = (lane & stride) == 0;
+                if ((pk < k) == (lower == up) && pk != k) {     // lower lane of an ascending pair keeps the min
+                    k = pk;
+                    v = pv;
+                }
+            }
+        if (lane < m) {
+            key[b + lane] = k;
+            val[b + lane] = v;
+        }
+    }
+}
+
 template <bool BLOCK>
 __global__ void k_sort_pairs(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int CAP,
                              const int* __restrict__ ptr, int* __restrict__ key, double* __restrict__ val,
@@ -2050,8 +2087,9 @@ __global__ void k_spgemm_hash(int nrows, const int* __restrict__ list, const int
 // row goes to the first tier's scratch slot (xoff[p] * 8 entries, which
 // holds min(terms, its capacity)) and its count to cnt[p]; a row of Y with
 // more than 32 entries or a row with more than 32 terms is appended to
-// longs for the hash kernel.
-__global__ void __launch_bounds__(TPB) k_spgemm_warp(int nrows, const int* __restrict__ yptr,
+// longs for the hash kernel. The rows are list[0 .. *nlist).
+__global__ void __launch_bounds__(TPB) k_spgemm_warp(const int* __restrict__ list, const int* __restrict__ nlist,
+                                                     const int* __restrict__ yptr,
                                                      const int* __restrict__ ycol, const double* __restrict__ yval,
                                                      const int* __restrict__ zptr, const int* __restrict__ zcol,
                                                      const double* __restrict__ zval, int* __restrict__ cnt,
@@ -2065,7 +2103,9 @@ __global__ void __launch_bounds__(TPB) k_spgemm_warp(int nrows, const int* __res
     double* V = Vs + wid * 32;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int warp_first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int p = warp_first; p < nrows; p += nw) {                 // p is uniform in the warp
+    const int nr = *nlist;
+    for (int t = warp_first; t < nr; t += nw) {                   // t is uniform in the warp
+        const int p = list[t];
         const int eb = yptr[p], ly = yptr[p + 1] - eb;
         if (ly > 32) {
             if (lane == 0) longs[atomicAdd(nlongs, 1)] = p;
@@ -2131,65 +2171,103 @@ __global__ void __launch_bounds__(TPB) k_spgemm_warp(int nrows, const int* __res
     }
 }
 
-// Rows of X = Y Z when X has at most SPG_DENSE_MAX columns, a block each: a
-// dense accumulator V[ncols] and an occupancy bitmap in shared memory. Step
+// Rows of X = Y Z whose columns lie in a window of at most dcap columns
+// starting at base[p] (the listed rows list[0 .. *nlist)), a block each: a
+// dense accumulator V[dcap] and an occupancy bitmap in shared memory. Step
 // e (entry y of row p of Y) adds y z for every entry z of the Z row it reads;
 // within a step the columns are distinct, a column's first term starts its
 // sum and later steps add in step order (a barrier between steps): the hash
 // kernel's and the oracle's order, bit for bit, with no probing and no sort
 // (the bitmap is read in column order). The row goes to its scratch slot at
-// xoff[p] * 8 (min(terms, ncols) entries) and its count to cnt[p].
+// xoff[p] * 8 (min(terms, window) entries) and its count to cnt[p].
 constexpr int SPG_DENSE_MAX = 12288;
+constexpr int SPG_DENSE_MIN_TERMS = 8192;   // rows of a wider product that take the dense kernel
 constexpr int SPG_DENSE_THREADS = 256;
+constexpr int SPG_STAGE = 512;      // entries of a Y row staged at a time (value and Z row bounds)
+constexpr int SPG_PF = 4;           // steps whose first Z chunk is loaded one group ahead
+__host__ __device__ constexpr int spg_dense_smem(int dcap) {
+    return (int)(sizeof(double) * dcap + sizeof(unsigned) * ((dcap + 31) / 32) +
+                 SPG_STAGE * (sizeof(double) + 2 * sizeof(int)));
+}
 __global__ void __launch_bounds__(SPG_DENSE_THREADS) k_spgemm_dense(
-    int nrows, int ncols, const int* __restrict__ yptr, const int* __restrict__ ycol,
+    const int* __restrict__ list, const int* __restrict__ nlist, const int* __restrict__ base, int dcap,
+    const int* __restrict__ yptr, const int* __restrict__ ycol,
     const double* __restrict__ yval, const int* __restrict__ zptr, const int* __restrict__ zcol,
     const double* __restrict__ zval, int* __restrict__ cnt, const int* __restrict__ xoff, int* __restrict__ xcol,
     double* __restrict__ xval) {
     extern __shared__ double dsm[];
     __shared__ int wtot[SPG_DENSE_THREADS / 32];
+    const int nw = (dcap + 31) >> 5;
     double* V = dsm;
-    unsigned* F = reinterpret_cast<unsigned*>(dsm + ncols);
-    const int nw = (ncols + 31) >> 5;
+    double* sy = dsm + dcap;                                   // staged y values
+    int* sb = reinterpret_cast<int*>(sy + SPG_STAGE);           // staged Z row starts
+    int* se = sb + SPG_STAGE;                                   // staged Z row ends
+    unsigned* F = reinterpret_cast<unsigned*>(se + SPG_STAGE);  // occupancy bitmap
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int U = SPG_DENSE_THREADS;
     const int per = (nw + U - 1) / U;                       // bitmap words per thread in the read-out
-    for (int p = blockIdx.x; p < nrows; p += gridDim.x) {
+    const int nr = *nlist;
+    for (int t = blockIdx.x; t < nr; t += gridDim.x) {
+        const int p = list[t];
+        const int b = base[p];                                  // first column of the window
         for (int w = tid; w < nw; w += U) F[w] = 0u;
-        __syncthreads();
         const int eb = yptr[p], ee = yptr[p + 1];
-        int jn = eb < ee ? ycol[eb] : 0;
-        double yn = eb < ee ? yval[eb] : 0.0;
-        int fbn = eb < ee ? zptr[jn] : 0, fen = eb < ee ? zptr[jn + 1] : 0;
-        int qn = fbn + tid < fen ? zcol[fbn + tid] : 0;        // first chunk of the next step, loaded ahead
-        double zn = fbn + tid < fen ? zval[fbn + tid] : 0.0;
-        for (int e = eb; e < ee; ++e) {
-            const double y = yn;
-            const int fb = fbn, fe = fen;
-            const int q0 = qn;
-            const double z0 = zn;
-            if (e + 1 < ee) {
-                jn = ycol[e + 1];
-                yn = yval[e + 1];
-                fbn = zptr[jn];
-                fen = zptr[jn + 1];
-                qn = fbn + tid < fen ? zcol[fbn + tid] : 0;
-                zn = fbn + tid < fen ? zval[fbn + tid] : 0.0;
+        for (int b0 = eb; b0 < ee; b0 += SPG_STAGE) {
+            const int nb = min(SPG_STAGE, ee - b0);
+            __syncthreads();                                    // the previous batch's staged entries are done
+            for (int i = tid; i < nb; i += U) {
+                const int j = ycol[b0 + i];
+                sy[i] = yval[b0 + i];
+                sb[i] = zptr[j];
+                se[i] = zptr[j + 1];
             }
-            for (int f = fb + tid; f < fe; f += U) {
-                const bool pre = f - fb < U;
-                const int q = pre ? q0 : zcol[f];
-                const double term = __dmul_rn(y, pre ? z0 : zval[f]);
-                const unsigned bit = 1u << (q & 31);
-                if (F[q >> 5] & bit) {
-                    V[q] = __dadd_rn(V[q], term);
-                } else {
-                    V[q] = term;
-                    atomicOr(&F[q >> 5], bit);
+            __syncthreads();
+            int qa[SPG_PF];
+            double za[SPG_PF];
+#pragma unroll
+            for (int k = 0; k < SPG_PF; ++k) {
+                const bool ok = k < nb && sb[k] + tid < se[k];
+                qa[k] = ok ? zcol[sb[k] + tid] : 0;
+                za[k] = ok ? zval[sb[k] + tid] : 0.0;
+            }
+            for (int g = 0; g < nb; g += SPG_PF) {
+                int qb[SPG_PF];
+                double zb[SPG_PF];
+#pragma unroll
+                for (int k = 0; k < SPG_PF; ++k) {              // the next group's first chunks
+                    const int sn = g + SPG_PF + k;
+                    const bool ok = sn < nb && sb[sn] + tid < se[sn];
+                    qb[k] = ok ? zcol[sb[sn] + tid] : 0;
+                    zb[k] = ok ? zval[sb[sn] + tid] : 0.0;
+                }
+#pragma unroll
+                for (int k = 0; k < SPG_PF; ++k) {
+                    const int sk = g + k;
+                    if (sk >= nb) break;                        // uniform in the block
+                    const double y = sy[sk];
+                    const int fb = sb[sk], fe = se[sk];
+                    for (int f = fb + tid; f < fe; f += U) {
+                        const bool pre = f - fb < U;
+                        const int q = (pre ? qa[k] : zcol[f]) - b;
+                        const double term = __dmul_rn(y, pre ? za[k] : zval[f]);
+                        const unsigned bit = 1u << (q & 31);
+                        if (F[q >> 5] & bit) {
+                            V[q] = __dadd_rn(V[q], term);
+                        } else {
+                            V[q] = term;
+                            atomicOr(&F[q >> 5], bit);
+                        }
+                    }
+                    __syncthreads();                            // the barrier between steps
+                }
+#pragma unroll
+                for (int k = 0; k < SPG_PF; ++k) {
+                    qa[k] = qb[k];
+                    za[k] = zb[k];
                 }
             }
-            __syncthreads();                                    // the barrier between steps
         }
+        __syncthreads();                                        // the bitmap is complete (also for an empty row)
         // read-out in column order: thread t takes words [t * per, (t + 1) * per)
         int mine = 0;
         for (int k = 0; k < per; ++k) {
@@ -2219,7 +2297,7 @@ __global__ void __launch_bounds__(SPG_DENSE_THREADS) k_spgemm_dense(
             while (bits) {
                 const int q = (w << 5) + __ffs(bits) - 1;
                 bits &= bits - 1;
-                xcol[c0 + pos] = q;
+                xcol[c0 + pos] = b + q;
                 xval[c0 + pos] = V[q];
                 ++pos;
             }
@@ -2229,29 +2307,101 @@ __global__ void __launch_bounds__(SPG_DENSE_THREADS) k_spgemm_dense(
     }
 }
 
-// Scratch units (8 entries) a one-pass row needs: min(terms of the row,
-// cap) rounded up, terms = sum of the lengths of the Z rows it reads.
-__global__ void k_spgemm_units(int n, const int* __restrict__ yptr, const int* __restrict__ ycol,
-                               const int* __restrict__ zptr, int cap, int* __restrict__ units) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        int sum = 0;
-        for (int e = yptr[p]; e < yptr[p + 1]; ++e) {
+
+// Per row p of X = Y Z: its terms T (the lengths of the Z rows it reads) and
+// the window [lo, hi] between the first and the last column of those rows.
+// A row whose window has at most dcap columns and that has at least dmin
+// terms goes to the dense kernel (base[p] = lo, listed in dlist), any other
+// to the warp pass and the hash tiers (base[p] = -1, listed in olist): a
+// block with a dense window is the faster way for rows of many terms, warps
+// with small hash tables for rows of few. units[p] = the scratch units (8
+// entries) of its slot, min(T, window) or min(T, hcap). Lists are appended a
+// warp at a time (their order does not matter: every row has its own slot).
+__global__ void k_spgemm_classify(int n, const int* __restrict__ yptr, const int* __restrict__ ycol,
+                                  const int* __restrict__ zptr, const int* __restrict__ zcol, int hcap, int dcap,
+                                  int dmin, int* __restrict__ units, int* __restrict__ base, int* __restrict__ dlist,
+                                  int* __restrict__ ndl, int* __restrict__ olist, int* __restrict__ nol) {
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x + threadIdx.x - lane; p0 < n; p0 += stride) {   // uniform in the warp
+        const int p = p0 + lane;
+        const bool valid = p < n;
+        bool dense = false;
+        if (valid) {
+            int T = 0, lo = 0x7fffffff, hi = -1;
+            for (int e = yptr[p]; e < yptr[p + 1]; ++e) {
+                const int j = ycol[e];
+                const int zb = zptr[j], ze = zptr[j + 1];
+                if (ze > zb) {
+                    T += ze - zb;
+                    lo = min(lo, zcol[zb]);
+                    hi = max(hi, zcol[ze - 1]);
+                }
+            }
+            const int win = hi >= lo ? hi - lo + 1 : 0;
+            dense = win > 0 && win <= dcap && T >= dmin;
+            units[p] = ((dense ? min(T, win) : min(T, hcap)) + 7) >> 3;
+            base[p] = dense ? lo : -1;
+        }
+        const unsigned bd = __ballot_sync(FULL_MASK, valid && dense);
+        const unsigned bo = __ballot_sync(FULL_MASK, valid && !dense);
+        int d0 = 0, o0 = 0;
+        if (lane == 0) {
+            if (bd) d0 = atomicAdd(ndl, __popc(bd));
+            if (bo) o0 = atomicAdd(nol, __popc(bo));
+        }
+        d0 = __shfl_sync(FULL_MASK, d0, 0);
+        o0 = __shfl_sync(FULL_MASK, o0, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (valid && dense) dlist[d0 + __popc(bd & below)] = p;
+        else if (valid) olist[o0 + __popc(bo & below)] = p;
+    }
+}
+
+// k_spgemm_classify with a warp per row, for long rows of Y (the lanes
+// stride the row; one append per row).
+__global__ void k_spgemm_classify_warp(int n, const int* __restrict__ yptr, const int* __restrict__ ycol,
+                                       const int* __restrict__ zptr, const int* __restrict__ zcol, int hcap,
+                                       int dcap, int dmin, int* __restrict__ units, int* __restrict__ base,
+                                       int* __restrict__ dlist, int* __restrict__ ndl, int* __restrict__ olist,
+                                       int* __restrict__ nol) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {   // uniform in the warp
+        int T = 0, lo = 0x7fffffff, hi = -1;
+        for (int e = yptr[p] + lane; e < yptr[p + 1]; e += 32) {
             const int j = ycol[e];
-            sum += zptr[j + 1] - zptr[j];
-            if (sum >= cap) {
-                sum = cap;
-                break;
+            const int zb = zptr[j], ze = zptr[j + 1];
+            if (ze > zb) {
+                T += ze - zb;
+                lo = min(lo, zcol[zb]);
+                hi = max(hi, zcol[ze - 1]);
             }
         }
-        units[p] = (sum + 7) >> 3;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            T += __shfl_xor_sync(FULL_MASK, T, o);
+            lo = min(lo, __shfl_xor_sync(FULL_MASK, lo, o));
+            hi = max(hi, __shfl_xor_sync(FULL_MASK, hi, o));
+        }
+        if (lane == 0) {
+            const int win = hi >= lo ? hi - lo + 1 : 0;
+            const bool dense = win > 0 && win <= dcap && T >= dmin;
+            units[p] = ((dense ? min(T, win) : min(T, hcap)) + 7) >> 3;
+            base[p] = dense ? lo : -1;
+            if (dense) dlist[atomicAdd(ndl, 1)] = p;
+            else olist[atomicAdd(nol, 1)] = p;
+        }
     }
 }
 
 // Rows of a one-pass product from their scratch slots (as in SPG_ONE) to the
 // CSR arrays, a warp per row; rows with more than `limit` columns went on to
-// a launch of larger capacity and are copied from its slots.
+// a launch of larger capacity and are copied from its slots, except the rows
+// of the dense kernel (dense[p] >= 0), which are always in these slots.
 __global__ void k_spgemm_copy(int nrows, const int* __restrict__ list, const int* __restrict__ nlist, int limit,
-                              const int* __restrict__ cnt, const int* __restrict__ xoff, long long stride,
+                              const int* __restrict__ dense, const int* __restrict__ cnt,
+                              const int* __restrict__ xoff, long long stride,
                               const int* __restrict__ scol, const double* __restrict__ sval,
                               const int* __restrict__ xptr, int* __restrict__ xcol, double* __restrict__ xval) {
     const int lane = threadIdx.x & 31;
@@ -2260,7 +2410,7 @@ __global__ void k_spgemm_copy(int nrows, const int* __restrict__ list, const int
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nr; t += nw) {
         const int p = list ? list[t] : t;
         const int m = cnt[p];
-        if (m > limit) continue;
+        if (m > limit && !(dense && dense[p] >= 0)) continue;   // left to a tier of larger capacity
         const long long src = xoff ? (long long)xoff[p] * stride : (long long)t * stride;
         const int dst = xptr[p];
         for (int s = lane; s < m; s += 32) {
@@ -2746,38 +2896,6 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, int ncols
     cudaStream_t st = h->stream;
     const int n = Y.n;
     const char* shift_env = std::getenv("AMG_SPGEMM_CAP_SHIFT");
-    if (!shift_env && ncols <= SPG_DENSE_MAX && (long long)n * ((ncols + 7) / 8) <= 0x7fffffffLL) {
-        k_spgemm_units<<<grid_for(h, n), TPB, 0, st>>>(n, Y.ptr, Y.col, Z.ptr, ncols, S.flag);
-        KERNEL_CHECK();
-        scan_exclusive(S.flag, S.off, n, S.off + n, st, S.scan_tmp);
-        const long long units = read_int(S.off + n, S.host, st);
-        int* dcol = S.mem.alloc<int>(units * 8 + 1);
-        double* dval = S.mem.alloc<double>(units * 8 + 1);
-        const int smd = (int)(sizeof(double) * ncols + sizeof(unsigned) * ((ncols + 31) / 32));
-        CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * SPG_DENSE_MAX + sizeof(unsigned) * (SPG_DENSE_MAX / 32))));
-        const int per_sm = std::max(1, std::min(8, (200 * 1024) / std::max(smd, 1)));
-        if (n > 0) {
-            k_spgemm_dense<<<std::min(n, h->num_sms * per_sm), SPG_DENSE_THREADS, smd, st>>>(
-                n, ncols, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, dcol, dval);
-            KERNEL_CHECK();
-        }
-        DevCsr X;
-        X.n = n;
-        X.ptr = scratch ? S.mem.alloc<int>(n + 1) : h->mem.alloc<int>(n + 1);
-        scan_exclusive(S.ub, X.ptr, n, X.ptr + n, st, S.scan_tmp);
-        finish_csr(h, S, X);
-        X.col = scratch ? S.mem.alloc<int>(X.nnz) : h->mem.alloc<int>(X.nnz);
-        X.val = scratch ? S.mem.alloc<double>(X.nnz) : h->mem.alloc<double>(X.nnz);
-        if (n > 0) {
-            k_spgemm_copy<<<blocks_for((long long)n * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-                n, nullptr, nullptr, ncols, S.ub, S.off, 8, dcol, dval, X.ptr, X.col, X.val);
-            KERNEL_CHECK();
-        }
-        S.mem.release(dcol);
-        S.mem.release(dval);
-        return X;
-    }
     int* over = S.cnt + 10;
     int* nl = S.cnt + 11;                               // rows listed for tiers 1 .. 4
     int* lists[SPG_TIERS] = {nullptr, S.list0, S.list1, S.qid, S.spos};   // spos: free once the sweeps are done
@@ -2826,20 +2944,50 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, int ncols
         KERNEL_CHECK();
     };
     // first tier: one pass into scratch slots of min(terms, capacity) entries
-    // when their total fits int32 units, else count now and fill later
+    // when their total fits int32 units, else count now and fill later. Rows
+    // whose columns lie in a window of at most dcap columns take the dense
+    // kernel (when even its largest slots fit int32 units, and not when the
+    // capacities are divided for tests). A product with more columns than
+    // the dense kernel holds sends it only rows of SPG_DENSE_MIN_TERMS terms
+    // or more.
     one[0] = (long long)n * ((cap(0) / 2 + 7) / 8) <= 0x7fffffffLL;
+    const int dcap = shift_env ? 0 : std::min(ncols, SPG_DENSE_MAX);
+    const bool dense_on = dcap > 0 && (long long)n * ((dcap + 7) / 8) <= 0x7fffffffLL;
+    int* dense_base = nullptr;
     if (one[0]) {
-        k_spgemm_units<<<grid_for(h, n), TPB, 0, st>>>(n, Y.ptr, Y.col, Z.ptr, cap(0) / 2, S.flag);
+        int* dlist = reinterpret_cast<int*>(S.nq);        // S.nq and S.mir: free once the sweeps are done
+        int* olist = reinterpret_cast<int*>(S.nq) + n;
+        dense_base = S.mir;
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 24, 0, 3 * sizeof(int), st));   // [24] long, [25] dense, [26] other
+        const int dmin = ncols <= SPG_DENSE_MAX ? 0 : SPG_DENSE_MIN_TERMS;
+        if (Y.nnz >= 64LL * n)                            // long rows of Y: a warp each
+            k_spgemm_classify_warp<<<blocks_for((long long)n * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
+                n, Y.ptr, Y.col, Z.ptr, Z.col, cap(0) / 2, dense_on ? dcap : 0, dmin, S.flag, dense_base, dlist,
+                S.cnt + 25, olist, S.cnt + 26);
+        else
+            k_spgemm_classify<<<grid_for(h, n), TPB, 0, st>>>(n, Y.ptr, Y.col, Z.ptr, Z.col, cap(0) / 2,
+                                                              dense_on ? dcap : 0, dmin, S.flag, dense_base, dlist,
+                                                              S.cnt + 25, olist, S.cnt + 26);
         KERNEL_CHECK();
         scan_exclusive(S.flag, S.off, n, S.off + n, st, S.scan_tmp);
         const long long units = read_int(S.off + n, S.host, st);
         scol[0] = S.mem.alloc<int>(units * 8 + 1);
         sval[0] = S.mem.alloc<double>(units * 8 + 1);
-        // rows of at most 32 terms by the warp pass, the rest (listed in
-        // S.heads, counted in S.cnt[24]) by the first hash tier
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 24, 0, sizeof(int), st));
+        if (dense_on) {
+            const int smd = spg_dense_smem(dcap);
+            CUDA_CHECK(cudaFuncSetAttribute(k_spgemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            spg_dense_smem(SPG_DENSE_MAX)));
+            const int per_sm = std::max(1, std::min(8, (220 * 1024) / smd));
+            k_spgemm_dense<<<h->num_sms * per_sm, SPG_DENSE_THREADS, smd, st>>>(
+                dlist, S.cnt + 25, dense_base, dcap, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, scol[0],
+                sval[0]);
+            KERNEL_CHECK();
+        }
+        // the other rows: at most 32 terms by the warp pass, the rest (listed
+        // in S.heads, counted in S.cnt[24]) by the first hash tier
         k_spgemm_warp<<<blocks_for((long long)n * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-            n, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, scol[0], sval[0], S.heads, S.cnt + 24);
+            olist, S.cnt + 26, Y.ptr, Y.col, Y.val, Z.ptr, Z.col, Z.val, S.ub, S.off, scol[0], sval[0], S.heads,
+            S.cnt + 24);
         KERNEL_CHECK();
         first_list = S.heads;
         first_count = S.cnt + 24;
@@ -2879,8 +3027,8 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, int ncols
         const int* lst = lists[t];
         const int* nls = t ? nl + t - 1 : nullptr;
         k_spgemm_copy<<<blocks_for((long long)rows[t] * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(
-            n, lst, nls, cap(t) / 2, S.ub, t ? nullptr : S.off, t ? cap(t) / 2 : 8, scol[t], sval[t], X.ptr, X.col,
-            X.val);
+            n, lst, nls, cap(t) / 2, t ? nullptr : dense_base, S.ub, t ? nullptr : S.off, t ? cap(t) / 2 : 8,
+            scol[t], sval[t], X.ptr, X.col, X.val);
         KERNEL_CHECK();
     }
     for (int t = 0; t < SPG_TIERS; ++t)
@@ -2947,7 +3095,8 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
     k_col_fill<<<grid_for(h, n), TPB, 0, st>>>(n, P.ptr, P.col, P.val, T.ptr, S.ub, T.col, T.val);
     KERNEL_CHECK();
     {
-        // rows of up to 2048 pairs: a warp each; longer rows: a block each
+        // rows of up to 32 pairs: a warp each in registers; up to 2048: a warp
+        // each in shared memory; longer rows: a block each
         constexpr int WCAP = 2048, WPB = 4, BCAP = 16384;
         const size_t sm_w = (size_t)WPB * WCAP * (sizeof(double) + sizeof(int));
         const size_t sm_b = (size_t)BCAP * (sizeof(double) + sizeof(int));
@@ -2955,9 +3104,13 @@ DevCsr smooth_level(amg_hierarchy* h, Level& L, int nc, Scratch& S) {
         CUDA_CHECK(cudaFuncSetAttribute(k_sort_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_b));
         int* over = S.cnt + 10;
         int* nl = S.cnt + 11;
-        CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 2 * sizeof(int), st));
+        int* nm = S.cnt + 12;
+        CUDA_CHECK(cudaMemsetAsync(S.cnt + 10, 0, 3 * sizeof(int), st));
+        k_sort_pairs_warp<<<blocks_for((long long)nc * 32, TPB, h->num_sms * 16), TPB, 0, st>>>(nc, T.ptr, T.col,
+                                                                                              T.val, S.list1, nm);
+        KERNEL_CHECK();
         k_sort_pairs<false><<<blocks_for((long long)nc * 32, WPB * 32, h->num_sms * 8), WPB * 32, sm_w, st>>>(
-            nc, nullptr, nullptr, WCAP, T.ptr, T.col, T.val, S.list0, nl, over);
+            nc, S.list1, nm, WCAP, T.ptr, T.col, T.val, S.list0, nl, over);
         KERNEL_CHECK();
         const int nlong = read_int(nl, S.host, st);
         if (nlong > 0) {
