@@ -124,13 +124,10 @@ __global__ void k_dww(int n, double* __restrict__ diag, const double* __restrict
 // division and the subtraction (this GPU's FP64 pipe bounds this kernel).
 // A group of G lanes per row (G = 1, 8, 16 or 32 by the mean row length),
 // the row's entries strided over the group, so long rows are shared out.
-// With mir set, the mirror position found for every upper entry (j > i) is
-// kept in mir[k] (-1: none); lower entries are not written.
 template <int G>
 __global__ void __launch_bounds__(TPB) k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                                                  const double* __restrict__ val, const double* __restrict__ dww,
-                                                 const double* __restrict__ w, double* __restrict__ c,
-                                                 int* __restrict__ mir) {
+                                                 const double* __restrict__ w, double* __restrict__ c) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int gl = threadIdx.x & (G - 1);
     const int ng = (gridDim.x * blockDim.x) / G;
@@ -152,7 +149,6 @@ __global__ void __launch_bounds__(TPB) k_weights(int n, const int* __restrict__ 
             c[k] = cw;
             const int mirror = find_in_row(ptr, col, j, i);
             if (mirror >= 0) c[mirror] = cw;
-            if (mir) mir[k] = mirror;
         }
     }
 }
@@ -780,8 +776,8 @@ constexpr unsigned long long NO_SUITOR = ~0ull;
 template <int G>
 __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict__ ptr, const int* __restrict__ col,
                                                     const double* __restrict__ c, const int* __restrict__ spos,
-                                                    const int* __restrict__ mir, int2* __restrict__ nq,
-                                                    unsigned long long* __restrict__ suitor, int* err) {
+                                                    int2* __restrict__ nq, unsigned long long* __restrict__ suitor,
+                                                    int* err) {
     const double NEG_INF = -__longlong_as_double(0x7ff0000000000000LL);
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -801,7 +797,7 @@ __global__ void __launch_bounds__(TPB) k_mirror_pos(int n, const int* __restrict
             if (!is_edge(c[k])) continue;           // not an edge (diagonal, zero pair)
             ++edges;
             const int u = col[k];
-            const int km = mir && u > v ? mir[k] : find_in_row(ptr, col, u, v);   // mir: upper entries
+            const int km = find_in_row(ptr, col, u, v);
             if (km < 0) {                            // no mirror entry: pattern not symmetric
                 nq[spos[k]] = make_int2(-1, -1);
                 atomicOr(err, 1);
@@ -1298,12 +1294,12 @@ int weights_group(long long nnz, long long n) {
 }
 
 void launch_weights(int G, int grid_cap, cudaStream_t st, int n, const int* ptr, const int* col, const double* val,
-                    const double* dww, const double* w, double* c, int* mir = nullptr) {
+                    const double* dww, const double* w, double* c) {
     const int blocks = blocks_for((long long)n * G, TPB, grid_cap);
-    if (G == 1) k_weights<1><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
-    else if (G == 8) k_weights<8><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
-    else if (G == 16) k_weights<16><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
-    else k_weights<32><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c, mir);
+    if (G == 1) k_weights<1><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else if (G == 8) k_weights<8><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else if (G == 16) k_weights<16><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
+    else k_weights<32><<<blocks, TPB, 0, st>>>(n, ptr, col, val, dww, w, c);
     KERNEL_CHECK();
 }
 
@@ -1561,6 +1557,7 @@ __global__ void k_cholesky(int n, const double* __restrict__ D, double* __restri
 // memory, a larger one in gwork + gofs[s] (2 n^2 doubles). segp == nullptr
 // means a single block of rows [0, n0).
 constexpr int SM_DENSE = 96;
+constexpr int CTA_DENSE = 256;      // largest block one CTA factors (its n^3 FP64 work runs on one SM)
 __global__ void k_coarse_inverse_blocks(int n0, const int* __restrict__ segp, const long long* __restrict__ blk,
                                         const long long* __restrict__ gofs, const int* __restrict__ ptr,
                                         const int* __restrict__ col, const double* __restrict__ val,
@@ -2439,7 +2436,7 @@ struct Scratch {
     double* sval = nullptr;   // nnz
     int* spos = nullptr;      // nnz: sorted position of each entry (matching by proposals)
     int2* nq = nullptr;       // nnz: (neighbour, mirror's sorted position) per sorted entry
-    int* mir = nullptr;       // nnz: mirror position of each upper entry, -1 none (matching by proposals)
+    int* rowbase = nullptr;   // n: a sparse product row's column window base (-1: the hash path)
     unsigned long long* suitor = nullptr;   // n
     long long cap_nnz = 0;    // entries c, skey and sval hold
     int* scan_tmp = nullptr;
@@ -2632,14 +2629,11 @@ int ld_match(amg_hierarchy* h, Scratch& S, const DevCsr& A, int** pending) {
             const int G = rows_group(A.nnz, n);
             const int mblocks = blocks_for((long long)n * G, TPB, h->num_sms * 16);
             if (G == 8)
-                k_mirror_pos<8><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
-                                                          err);
+                k_mirror_pos<8><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             else if (G == 16)
-                k_mirror_pos<16><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
-                                                          err);
+                k_mirror_pos<16><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             else
-                k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.mir, S.nq, S.suitor,
-                                                          err);
+                k_mirror_pos<32><<<mblocks, TPB, 0, st>>>(n, A.ptr, A.col, S.c, S.spos, S.nq, S.suitor, err);
             KERNEL_CHECK();
         }
         suitor_match(h, S, A, err);
@@ -2873,13 +2867,11 @@ void ensure_entry_scratch(Scratch& S, long long nnz, cudaStream_t st) {
     S.mem.release(S.sval);
     S.mem.release(S.spos);
     S.mem.release(S.nq);
-    S.mem.release(S.mir);
     S.c = S.mem.alloc<double>(nnz);
     S.skey = S.mem.alloc<int>(nnz);
     S.sval = S.mem.alloc<double>(nnz);
     S.spos = S.mem.alloc<int>(nnz);
     S.nq = S.mem.alloc<int2>(nnz);
-    S.mir = S.mem.alloc<int>(nnz);
     S.cap_nnz = nnz;
 }
 
@@ -2955,9 +2947,9 @@ DevCsr spgemm_hash(amg_hierarchy* h, const DevCsr& Y, const DevCsr& Z, int ncols
     const bool dense_on = dcap > 0 && (long long)n * ((dcap + 7) / 8) <= 0x7fffffffLL;
     int* dense_base = nullptr;
     if (one[0]) {
-        int* dlist = reinterpret_cast<int*>(S.nq);        // S.nq and S.mir: free once the sweeps are done
+        int* dlist = reinterpret_cast<int*>(S.nq);        // S.nq: free once the sweeps are done
         int* olist = reinterpret_cast<int*>(S.nq) + n;
-        dense_base = S.mir;
+        dense_base = S.rowbase;
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 24, 0, 3 * sizeof(int), st));   // [24] long, [25] dense, [26] other
         const int dmin = ncols <= SPG_DENSE_MAX ? 0 : SPG_DENSE_MIN_TERMS;
         if (Y.nnz >= 64LL * n)                            // long rows of Y: a warp each
@@ -3166,7 +3158,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
     S.sval = S.mem.alloc<double>(nnz0);
     S.spos = S.mem.alloc<int>(nnz0);
     S.nq = S.mem.alloc<int2>(nnz0);
-    S.mir = S.mem.alloc<int>(nnz0);
+    S.rowbase = S.mem.alloc<int>(n0 + 1);
     S.suitor = S.mem.alloc<unsigned long long>(n0);
     S.cap_nnz = nnz0;
     S.scan_tmp = S.mem.alloc<int>(scan_scratch_ints(n0 + 2) + 64);
@@ -3257,9 +3249,8 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
                 if (s == 0 && l == 0) k_dww<<<grid_for(h, n), TPB, 0, st>>>(n, S.diag, w);
                 else if (s == 0) k_diag<<<grid_for(h, n), TPB, 0, st>>>(n, A.ptr, A.col, A.val, w, S.diag);
                 KERNEL_CHECK();
-                int* mir = o.match_kernel == 0 ? S.mir : nullptr;
                 launch_weights(weights_group(A.nnz, n), h->num_sms * 16, st, n, A.ptr, A.col, A.val, S.diag, w,
-                               S.c, mir);
+                               S.c);
             }
             int* pending = nullptr;
             const int rr = ld_match(h, S, A, &pending);
@@ -3436,9 +3427,10 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         h->segL_blk = h->mem.alloc<long long>(nseg + 1);
         CUDA_CHECK(cudaMemcpyAsync(h->segL_ptr, sp.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, st));
         CUDA_CHECK(cudaMemcpyAsync(h->segL_blk, boff.data(), sizeof(long long) * (nseg + 1), cudaMemcpyHostToDevice, st));
-        // one CTA per block in a single launch; blocks above SM_DENSE rows work in
-        // global scratch, and when that scratch would pass 1 GiB the blocks are
-        // factored one after another instead
+        // one CTA per block in a single launch (blocks above SM_DENSE rows work in
+        // global scratch); with a block above CTA_DENSE rows, or scratch above
+        // 1 GiB, the blocks are factored one after another by the multi-block
+        // kernels instead
         int maxb = 0, maxsm = 0;
         std::vector<long long> gofs(nseg, 0);
         long long gw = 0;
@@ -3449,7 +3441,7 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
             else { gofs[s2] = gw; gw += 2LL * ns * ns + ns; }
         }
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
-        if (gw <= (1LL << 27)) {
+        if (maxb <= CTA_DENSE && gw <= (1LL << 27)) {
             double* gwork = S.mem.alloc<double>(gw + 1);
             long long* d_gofs = S.mem.alloc<long long>(nseg);
             CUDA_CHECK(cudaMemcpyAsync(d_gofs, gofs.data(), sizeof(long long) * nseg, cudaMemcpyHostToDevice, st));
@@ -3488,12 +3480,15 @@ void setup_hierarchy(amg_hierarchy* h, const amg_csr* Ain, const double* w_in) {
         h->coarse_L = h->mem.alloc<double>((size_t)nc * nc);
         h->coarse_inv = h->mem.alloc<double>((size_t)nc * nc);
         CUDA_CHECK(cudaMemsetAsync(S.cnt + 5, 0, sizeof(int), st));
-        if (nc <= SM_DENSE) {
-            const int smd = (int)(2 * sizeof(double) * (size_t)nc * nc);
+        if (nc <= CTA_DENSE) {                            // one CTA: shared memory up to SM_DENSE rows
+            const int smd = nc <= SM_DENSE ? (int)(2 * sizeof(double) * (size_t)nc * nc) : 0;
+            double* gwork = nc <= SM_DENSE ? nullptr : S.mem.alloc<double>(2 * (size_t)nc * nc + nc);
+            long long* gofs = S.mem.alloc<long long>(1);
+            CUDA_CHECK(cudaMemsetAsync(gofs, 0, sizeof(long long), st));
             CUDA_CHECK(cudaFuncSetAttribute(k_coarse_inverse_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)(2 * sizeof(double) * SM_DENSE * SM_DENSE)));
-            k_coarse_inverse_blocks<<<1, 1024, smd, st>>>(nc, nullptr, nullptr, nullptr, Lc.A.ptr, Lc.A.col,
-                                                          Lc.A.val, nullptr, h->coarse_inv, h->coarse_L, S.cnt + 5);
+            k_coarse_inverse_blocks<<<1, 1024, smd, st>>>(nc, nullptr, nullptr, gofs, Lc.A.ptr, Lc.A.col,
+                                                          Lc.A.val, gwork, h->coarse_inv, h->coarse_L, S.cnt + 5);
             KERNEL_CHECK();
             if (read_int(S.cnt + 5, S.host, st))
                 AMG_THROW(AMG_ERR_NOT_SPD, "coarsest-level Cholesky hit a non-positive pivot");
