@@ -251,6 +251,7 @@ struct amg_hierarchy {
     std::vector<amg::Level> lev;
     int nc = 0;                 // coarsest size
     int coarse_cg = 0;          // 1: coarsest solved by CG (above max_dense)
+    bool r32_ready = false;     // the CG update wrote level 0's float r for the next V-cycle call
     amg::CoarseCg ccg;
     double* coarse_L = nullptr;  // dense Cholesky factor (column-major)
     double* coarse_inv = nullptr;// dense inverse A_L^{-1} (row-major)

@@ -700,15 +700,18 @@ __global__ void __launch_bounds__(TPB) k_spmv_dot(SellView S, const double* __re
 }
 
 // x += alpha p; r -= alpha q; ||r||^2.
+// With r32 set (FP32 V-cycle), also the float copy of the new r that the
+// V-cycle's level 0 reads (the conversion of k_to_f32, without its pass).
 __global__ void __launch_bounds__(TPB) k_update_xr(int n, const double* __restrict__ p, const double* __restrict__ q,
-                                                   double* __restrict__ x, double* __restrict__ r, Reducer red,
-                                                   PcgScalars* sc) {
+                                                   double* __restrict__ x, double* __restrict__ r,
+                                                   float* __restrict__ r32, Reducer red, PcgScalars* sc) {
     const double alpha = sc->alpha;
     double rr = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         rr = fma(ri, ri, rr);
     }
     reduce_and_finish(rr, 0.0, red, sc, FIN_RR);
@@ -856,7 +859,7 @@ void vcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
         const int g = Lv.grid_pre[f32] ? Lv.grid_pre[f32] : sell_grid(h, S.nslices);
         T *xa = vec(Lv, VX), *ra = vec(Lv, VR), *xb = vec(Lv, VT);
         const int Vb = l == 0 ? 8 : V;
-        if (l == 0 && f32) {
+        if (l == 0 && f32 && !h->r32_ready) {           // else the CG update already wrote it
             Scope sc_(&h->prof, st, K_CONVERT, 12.0 * Lv.A.n);
             k_to_f32<<<vec_grid(h, Lv.A.n), TPB, 0, st>>>(Lv.A.n, r, (float*)vec(Lv, VB));
             KERNEL_CHECK();
@@ -1179,7 +1182,7 @@ void kcycle_typed(amg_hierarchy* h, const double* r, double* z, int rz_mode) {
     T* xa = lvec<T>(L0, 1);
     T* ra = lvec<T>(L0, 2);
     const int g = L0.grid_pre[f32] ? L0.grid_pre[f32] : sell_grid(h, S.nslices);
-    if (f32) {
+    if (f32 && !h->r32_ready) {                         // else the CG update already wrote it
         Scope sc_(&h->prof, st, K_CONVERT, 12.0 * n0);
         k_to_f32<<<vec_grid(h, n0), TPB, 0, st>>>(n0, r, (float*)lvec<T>(L0, 0));
         KERNEL_CHECK();
@@ -1440,6 +1443,9 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
     bool have_true = true;          // r currently equals b - A x exactly
     int it = 0;
     bool restart = true;
+    // FP32 V-cycle: the CG update also writes level 0's float copy of r
+    float* r32 = h->opt.precision == AMG_FP32_VCYCLE ? h->lev[0].b32 : nullptr;
+    h->r32_ready = false;
     if (rel <= rtol) status = AMG_OK;
     while (status != AMG_OK && it < maxit) {
         if (restart) {
@@ -1453,8 +1459,8 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             KERNEL_CHECK();
         }
         {
-            Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n);
-            k_update_xr<<<red_grid(h), TPB, 0, st>>>(n, h->p, h->q, x, h->r, h->red, h->sc);
+            Scope sc_(&h->prof, st, K_UPDATE_XR, 48.0 * n + (r32 ? 4.0 * n : 0.0));
+            k_update_xr<<<red_grid(h), TPB, 0, st>>>(n, h->p, h->q, x, h->r, r32, h->red, h->sc);
             KERNEL_CHECK();
         }
         ++it;
@@ -1478,8 +1484,10 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             ++inf.restarts;
             continue;
         }
+        h->r32_ready = r32 != nullptr;                  // level 0's float r is the one k_update_xr wrote
         vcycle_dispatch(h, h->r, h->z,
                         h->opt.krylov == 1 || h->opt.cycle > 0 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
+        h->r32_ready = false;
         Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
         k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
         KERNEL_CHECK();
