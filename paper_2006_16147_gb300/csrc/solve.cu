@@ -1446,6 +1446,21 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
     // FP32 V-cycle: the CG update also writes level 0's float copy of r
     float* r32 = h->opt.precision == AMG_FP32_VCYCLE ? h->lev[0].b32 : nullptr;
     h->r32_ready = false;
+    struct Ev {
+        cudaEvent_t e = nullptr;
+        ~Ev() { if (e) cudaEventDestroy(e); }
+    } ev;
+    CUDA_CHECK(cudaEventCreateWithFlags(&ev.e, cudaEventDisableTiming));
+    // z = B r for the next iteration, then p = z + beta p
+    auto precondition = [&]() {
+        h->r32_ready = r32 != nullptr;                  // level 0's float r is the one k_update_xr wrote
+        vcycle_dispatch(h, h->r, h->z,
+                        h->opt.krylov == 1 || h->opt.cycle > 0 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
+        h->r32_ready = false;
+        Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
+        k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
+        KERNEL_CHECK();
+    };
     if (rel <= rtol) status = AMG_OK;
     while (status != AMG_OK && it < maxit) {
         if (restart) {
@@ -1464,7 +1479,18 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             KERNEL_CHECK();
         }
         ++it;
-        read_scalars(h);
+        // The scalars go to the host. While the residual is well above the
+        // tolerance, the next iteration's preconditioner and direction update
+        // (which write only z, p and the device scalars) are queued behind the
+        // copy before the host waits for it, so the round trip overlaps the
+        // V-cycle; if the check below ends the loop after all, x and r are
+        // final and that work goes unused, and a restart recomputes rho and p
+        // from the true residual. Near the tolerance the host checks first.
+        const bool ahead = rel > 4.0 * rtol;
+        CUDA_CHECK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        CUDA_CHECK(cudaEventRecord(ev.e, st));
+        if (ahead) precondition();
+        CUDA_CHECK(cudaEventSynchronize(ev.e));
         if (hs->breakdown) { status = AMG_ERR_BREAKDOWN; break; }
         rel = std::sqrt(hs->rr) / nb;
         have_true = false;
@@ -1484,13 +1510,7 @@ amg_status solve(amg_hierarchy* h, const double* b, double* x, double rtol, int 
             ++inf.restarts;
             continue;
         }
-        h->r32_ready = r32 != nullptr;                  // level 0's float r is the one k_update_xr wrote
-        vcycle_dispatch(h, h->r, h->z,
-                        h->opt.krylov == 1 || h->opt.cycle > 0 ? FIN_RHO_UPDATE_FCG : FIN_RHO_UPDATE);
-        h->r32_ready = false;
-        Scope sc_(&h->prof, st, K_UPDATE_P, 24.0 * n);
-        k_update_p<<<vec_grid(h, n), TPB, 0, st>>>(n, h->z, h->p, h->sc);
-        KERNEL_CHECK();
+        if (!ahead) precondition();
     }
     if (!have_true) {
         {
